@@ -1,0 +1,490 @@
+"""CPU oracle for hashed path space filtering (Binder, Fricke, Keller 2019).
+
+TEST INFRASTRUCTURE ONLY.  Nothing on the product path may import, call or
+execute this module: only the tests, the package's smoke check and the
+benchmark's CPU-baseline leg use it.  It shares no code with the CUDA library
+and imports nothing from the package.
+
+What it computes, and from which passage
+----------------------------------------
+* Key construction (Algorithm 1, Sec. 3.1.4 jittering in the tangent plane,
+  Sec. 3.1.2 key components position + normal): level of detail from the
+  camera distance, a tangent-plane jitter scaled by the voxel edge of that
+  level, a second level of detail at the jittered point, the quantized
+  position, and the two hashes: the home index i = hash(x~, ...) mod T and the
+  32-bit fingerprint f = hash2(x~, n, ...) with the sentinel 0 excluded
+  (Sec. 3.2, Sec. 3.2.1).
+* Voxel membership (Eq. 7, with the transitivity argument right after it):
+  two vertices share a cell iff their full quantized tuples are equal.  The
+  oracle therefore groups vertices by the tuple (x~x, x~y, x~z, l', qx, qy, qz)
+  in an ordered (sorted) map, which is the "gather per voxel" form that opens
+  Sec. 3.2, and averages with weight w = 1 (Eq. 8/9): the cell value is the sum
+  of the members' contributions divided by their count.  This is the plain
+  definition the GPU's scatter form (atomic sums and counters, Sec. 3.2 and
+  Sec. 3.3.1) reaches up to summation order.
+* Temporal blending (Sec. 3.4.1): c = alpha c_old + (1 - alpha) c_new, or the
+  integrating weight alpha = N_old / (N_old + N_new).
+* Overflow audit (Sec. 3.2: the probe limit, after which a vertex keeps its
+  own unfiltered contribution): a helper that checks a table dump.
+
+Readings where the paper is silent (all listed in the design doc):
+* LOD: l(d) = floor(log2(s * theta_px * d)) read from the exponent bits of the
+  FP32 product, clamped to [lod_min, lod_max]; the voxel edge is 2^l, i.e. the
+  "s * 2^l" of Algorithm 1 with the projected-pixel footprint folded in, so the
+  voxel is always a power of two (Sec. 3.1.1 and Sec. 4).
+* Jitter: (u, w) in [-0.5, 0.5) from Philox4x32-10 (Salmon et al., SC'11) keyed
+  by (seed, frame), counter (vertex id, stream id, 0, 0); tangent frame from
+  Duff et al., "Building an Orthonormal Basis, Revisited" (JCGT 2017).
+* Hashes: MurmurHash3_x86_32 (Appleby) over the key's 32-bit words, with two
+  different seeds for hash and hash2.
+* Normal quantization: q(c) = clamp(floor((c + 1) * 128), 0, 255).
+* All key arithmetic is FP32 with round-to-nearest-even per operation, in the
+  order written below (numpy never fuses multiply-add), so the integer keys are
+  reproducible bit for bit.
+
+Sums are FP64 (the reference value) and, separately, fixed point
+(round-to-nearest of v * 2^24 into int64), which is exact and order-free.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+from typing import Dict, Optional, Sequence, Tuple
+
+import numpy as np
+
+F32 = np.float32
+U32 = np.uint32
+MASK32 = np.uint64(0xFFFFFFFF)
+
+# ----------------------------------------------------------------------------
+# Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel Random Numbers: As Easy
+# as 1, 2, 3", SC'11): a 10-round counter-based generator.  Each round takes
+# two 32x32->64 products of counter words with fixed multipliers, swaps and
+# xors the halves with the key, and the key is bumped by two Weyl constants
+# between rounds.
+# ----------------------------------------------------------------------------
+PHILOX_M0 = np.uint64(0xD2511F53)
+PHILOX_M1 = np.uint64(0xCD9E8D57)
+PHILOX_W0 = np.uint64(0x9E3779B9)
+PHILOX_W1 = np.uint64(0xBB67AE85)
+
+
+def philox4x32_10(c0, c1, c2, c3, k0, k1):
+    """Philox4x32 with 10 rounds; all arguments uint32 arrays (broadcastable)."""
+    c0, c1, c2, c3 = (np.asarray(x, dtype=np.uint64) & MASK32 for x in (c0, c1, c2, c3))
+    k0 = np.asarray(k0, dtype=np.uint64) & MASK32
+    k1 = np.asarray(k1, dtype=np.uint64) & MASK32
+    for rnd in range(10):
+        if rnd > 0:
+            k0 = (k0 + PHILOX_W0) & MASK32
+            k1 = (k1 + PHILOX_W1) & MASK32
+        p0 = PHILOX_M0 * c0
+        p1 = PHILOX_M1 * c2
+        hi0, lo0 = p0 >> np.uint64(32), p0 & MASK32
+        hi1, lo1 = p1 >> np.uint64(32), p1 & MASK32
+        c0, c1, c2, c3 = hi1 ^ c1 ^ k0, lo1, hi0 ^ c3 ^ k1, lo0
+    return tuple(x.astype(U32) for x in (c0, c1, c2, c3))
+
+
+# ----------------------------------------------------------------------------
+# MurmurHash3_x86_32 (Austin Appleby, public-domain reference algorithm) over
+# a message made of whole little-endian 32-bit words, so there is no tail.
+# ----------------------------------------------------------------------------
+_MM_C1 = np.uint64(0xCC9E2D51)
+_MM_C2 = np.uint64(0x1B873593)
+
+
+def _rotl32(x, r):
+    return ((x << np.uint64(r)) | (x >> np.uint64(32 - r))) & MASK32
+
+
+def murmur3_32(words: Sequence, seed: int) -> np.ndarray:
+    """MurmurHash3_x86_32 of the words (each a uint32 array) with `seed`."""
+    words = [np.asarray(w).astype(np.uint64) & MASK32 for w in words]
+    shape = np.broadcast(*words).shape if words else ()
+    h = np.zeros(shape, dtype=np.uint64) + np.uint64(seed & 0xFFFFFFFF)
+    for k in words:
+        k = (k * _MM_C1) & MASK32
+        k = _rotl32(k, 15)
+        k = (k * _MM_C2) & MASK32
+        h = h ^ k
+        h = _rotl32(h, 13)
+        h = (h * np.uint64(5) + np.uint64(0xE6546B64)) & MASK32
+    h = h ^ np.uint64(4 * len(words))
+    h = h ^ (h >> np.uint64(16))
+    h = (h * np.uint64(0x85EBCA6B)) & MASK32
+    h = h ^ (h >> np.uint64(13))
+    h = (h * np.uint64(0xC2B2AE35)) & MASK32
+    h = h ^ (h >> np.uint64(16))
+    return h.astype(U32)
+
+
+# ----------------------------------------------------------------------------
+# Key construction, Algorithm 1.
+# ----------------------------------------------------------------------------
+@dataclass(frozen=True)
+class KeyParams:
+    """Parameters of key construction and of the table (Alg. 1, Sec. 3.2)."""
+
+    log2_slots: int
+    max_probes: int
+    voxel_scale: float  # s: voxel edge in multiples of the projected pixel (Sec. 4)
+    pixel_angle: float  # theta_px = 2 tan(fov_y / 2) / height
+    jitter: bool = True
+    seed: int = 0x0051F15E
+    hash_seed_home: int = 0x9747B28C
+    hash_seed_fp: int = 0x2F0F1D3B
+    normal_in_home_hash: bool = False
+    lod_min: int = -24
+    lod_max: int = 24
+
+
+def pow2_f32(l) -> np.ndarray:
+    """2^l as float32, exact for integer l in [-126, 127] (built from the bits)."""
+    l = np.asarray(l, dtype=np.int64)
+    return ((l + 127) << 23).astype(U32).view(F32)
+
+
+def footprint_scale(p: KeyParams) -> np.float32:
+    """k = fl32(s * theta_px): world size of the voxel at unit distance."""
+    return F32(p.voxel_scale) * F32(p.pixel_angle)
+
+
+def level_of_detail(cx, cy, cz, x, y, z, k, lod_min, lod_max) -> np.ndarray:
+    """Alg. 1 level_of_detail(|p_cam - x|) = floor(log2(k * d)), clamped.
+
+    d = sqrt(((dx*dx) + (dy*dy)) + (dz*dz)) with d = p_cam - x, each FP32 op
+    rounded to nearest; floor(log2 F) of the positive FP32 F = k * d is its
+    unbiased exponent field (0 and subnormals read as -127 and clamp to
+    lod_min; inf/NaN read as 128 and clamp to lod_max)."""
+    dx = F32(cx) - x
+    dy = F32(cy) - y
+    dz = F32(cz) - z
+    d2 = (dx * dx + dy * dy) + dz * dz
+    d = np.sqrt(d2)
+    F = F32(k) * d
+    e = ((F.view(U32) >> U32(23)) & U32(0xFF)).astype(np.int32) - 127
+    return np.clip(e, lod_min, lod_max).astype(np.int32)
+
+
+def orthonormal_basis(nx, ny, nz):
+    """Tangent frame (t, b) of a unit normal n, after Duff et al. (JCGT 2017).
+
+    s = sign(nz) (copysign, so -0 gives -1); a = -1 / (s + nz);
+    q = (nx * ny) * a;  t = (1 + s*((nx*nx)*a), s*q, -(s*nx));
+    b = (q, s + (ny*ny)*a, -ny)."""
+    s = np.copysign(F32(1.0), nz).astype(F32)
+    a = F32(-1.0) / (s + nz)
+    q = (nx * ny) * a
+    tx = F32(1.0) + s * ((nx * nx) * a)
+    ty = s * q
+    tz = -(s * nx)
+    bx = q
+    by = s + (ny * ny) * a
+    bz = -ny
+    return (tx, ty, tz), (bx, by, bz)
+
+
+def jitter_uw(ids, stream, seed, frame):
+    """(u, w) in [-0.5, 0.5): top 24 bits of the first two Philox words."""
+    ids = np.asarray(ids, dtype=U32)
+    zero = np.zeros_like(ids)
+    x0, x1, _, _ = philox4x32_10(ids, np.full_like(ids, stream), zero, zero,
+                                 np.full_like(ids, seed), np.full_like(ids, frame))
+    u = (x0 >> U32(8)).astype(F32) * F32(2.0 ** -24) - F32(0.5)
+    w = (x1 >> U32(8)).astype(F32) * F32(2.0 ** -24) - F32(0.5)
+    return u, w
+
+
+def quantize_normal(c) -> np.ndarray:
+    """q(c) = clamp(floor((c + 1) * 128), 0, 255): 8 bits per normal axis."""
+    q = np.floor((c + F32(1.0)) * F32(128.0))
+    q = np.fmin(np.fmax(q, F32(0.0)), F32(255.0))
+    return q.astype(np.int32)
+
+
+_QMIN = F32(-2147483648.0)
+_QMAX = F32(2147483520.0)  # largest float32 below 2^31
+
+
+@dataclass
+class Keys:
+    xq: np.ndarray  # (N, 3) int32 quantized position x~
+    lod: np.ndarray  # (N,) int32 l' (level at the jittered point)
+    lod0: np.ndarray  # (N,) int32 l (level before jittering)
+    nq: np.ndarray  # (N, 3) int32 quantized normal
+    home: np.ndarray  # (N,) uint32 i = hash & (T - 1)
+    fp: np.ndarray  # (N,) uint32 fingerprint, never 0
+    xj: np.ndarray  # (N, 3) float32 jittered position x'
+
+    def tuples(self) -> np.ndarray:
+        """Full quantized tuple (x~x, x~y, x~z, l', qx, qy, qz) per vertex."""
+        return np.column_stack([self.xq.astype(np.int64), self.lod.astype(np.int64),
+                                self.nq.astype(np.int64)])
+
+
+def vertex_keys(p: KeyParams, cam, frame: int, px, py, pz, nx, ny, nz,
+                ids=None, stream: int = 0) -> Keys:
+    """Algorithm 1 for every vertex.
+
+    l  <- level_of_detail(|p_cam - x|)
+    x' <- x + jitter(n) * 2^l          (tangent plane of n; skipped if no jitter)
+    l' <- level_of_detail(|p_cam - x'|)
+    x~ <- floor(x' * 2^-l')            (exact scaling by a power of two)
+    i  <- hash(x~, l') mod T,   f <- hash2(x~, l', q(n)), 0 replaced by 1."""
+    px, py, pz, nx, ny, nz = (np.asarray(a, dtype=F32) for a in (px, py, pz, nx, ny, nz))
+    n = px.shape[0]
+    if ids is None:
+        ids = np.arange(n, dtype=np.uint64).astype(U32)
+    cx, cy, cz = (F32(c) for c in cam)
+    k = footprint_scale(p)
+    l0 = level_of_detail(cx, cy, cz, px, py, pz, k, p.lod_min, p.lod_max)
+    if p.jitter:
+        u, w = jitter_uw(ids, stream, p.seed, frame)
+        (tx, ty, tz), (bx, by, bz) = orthonormal_basis(nx, ny, nz)
+        E = pow2_f32(l0)
+        jx = u * tx + w * bx
+        jy = u * ty + w * by
+        jz = u * tz + w * bz
+        xj = px + jx * E
+        yj = py + jy * E
+        zj = pz + jz * E
+        l1 = level_of_detail(cx, cy, cz, xj, yj, zj, k, p.lod_min, p.lod_max)
+    else:
+        xj, yj, zj = px, py, pz
+        l1 = l0
+    inv = pow2_f32(-l1.astype(np.int64))
+    q = [np.fmin(np.fmax(np.floor(c * inv), _QMIN), _QMAX).astype(np.int32)
+         for c in (xj, yj, zj)]
+    xq = np.column_stack(q)
+    nq = np.column_stack([quantize_normal(c) for c in (nx, ny, nz)])
+    X, Y, Z = (c.view(U32) for c in q)
+    L = l1.astype(np.int32).view(U32)
+    NQ = (nq[:, 0] | (nq[:, 1] << 8) | (nq[:, 2] << 16)).astype(U32)
+    home_words = [X, Y, Z, L] + ([NQ] if p.normal_in_home_hash else [])
+    h1 = murmur3_32(home_words, p.hash_seed_home)
+    home = h1 & U32((1 << p.log2_slots) - 1)
+    f = murmur3_32([X, Y, Z, L, NQ], p.hash_seed_fp)
+    f = np.where(f == 0, U32(1), f).astype(U32)
+    return Keys(xq, l1, l0, nq, home.astype(U32), f, np.column_stack([xj, yj, zj]))
+
+
+# ----------------------------------------------------------------------------
+# Exact conversions used by the fixed-point mode.
+# ----------------------------------------------------------------------------
+FIXED_SHIFT = 24
+
+
+def to_fixed(v) -> np.ndarray:
+    """Round-to-nearest-even of v * 2^24 into int64 (v * 2^24 is exact)."""
+    v = np.asarray(v, dtype=F32).astype(np.float64) * float(2 ** FIXED_SHIFT)
+    return np.rint(v).astype(np.int64)
+
+
+def _bit_length_u64(a: np.ndarray) -> np.ndarray:
+    a = a.astype(np.uint64)
+    bl = np.zeros(a.shape, dtype=np.int64)
+    for s in (32, 16, 8, 4, 2, 1):
+        m = a >= (np.uint64(1) << np.uint64(s))
+        bl += np.where(m, s, 0)
+        a = np.where(m, a >> np.uint64(s), a)
+    return bl + (a > 0)
+
+
+def int64_to_f32_rn(v) -> np.ndarray:
+    """Correctly rounded (nearest, ties to even) int64 -> float32.
+
+    Keep the top 24 significant bits of |v|; round up when the dropped part
+    exceeds half a unit of the kept part, or equals it and the kept part is odd."""
+    v = np.asarray(v, dtype=np.int64)
+    neg = v < 0
+    a = np.where(neg, -(v + 1), v).astype(np.uint64) + neg.astype(np.uint64)  # |v|
+    bl = _bit_length_u64(a)
+    shift = np.maximum(bl - 24, 0).astype(np.uint64)
+    q = a >> shift
+    rem = a - (q << shift)
+    sm1 = np.where(shift > 0, shift - np.uint64(1), np.uint64(0))
+    half = np.where(shift > 0, np.uint64(1) << sm1, np.uint64(0))
+    up = (shift > 0) & ((rem > half) | ((rem == half) & ((q & np.uint64(1)) == 1)))
+    q = q + up.astype(np.uint64)
+    mag = q.astype(np.float64) * np.exp2(shift.astype(np.float64))
+    return np.where(neg, -mag, mag).astype(F32)
+
+
+# ----------------------------------------------------------------------------
+# Accumulation and lookup, Eq. 8/9 with w = 1, in the gather form.
+# ----------------------------------------------------------------------------
+@dataclass
+class FrameResult:
+    keys: Keys
+    cell: np.ndarray  # (N,) cell index into the sorted tuple list
+    tuples: np.ndarray  # (C, 7) sorted distinct tuples
+    count: np.ndarray  # (N,) int64 members of the vertex's cell
+    mean64: np.ndarray  # (N, 3) float64 cell average (reference value)
+    mean_fixed: np.ndarray  # (N, 3) float32 average from fixed-point sums
+    cell_count: np.ndarray  # (C,)
+    cell_sum64: np.ndarray  # (C, 3)
+    cell_fixed: np.ndarray  # (C, 3) int64
+    cell_home: np.ndarray  # (C,) uint32
+    cell_fp: np.ndarray  # (C,) uint32
+
+
+def group_cells(tuples: np.ndarray):
+    """Ordered-map group-by over the full tuple: (sorted tuples, inverse, counts)."""
+    uniq, inv, cnt = np.unique(tuples, axis=0, return_inverse=True, return_counts=True)
+    return uniq, inv.reshape(-1), cnt
+
+
+def fixed_mean_f32(sum_fixed: np.ndarray, count: np.ndarray) -> np.ndarray:
+    """fl32(fl32(sum) * 2^-24) / fl32(n): the fixed-point mode's cell average.
+
+    `sum_fixed` is (C, 3) int64 and `count` (C,); the product by 2^-24 is exact
+    and the division is one FP32 round-to-nearest."""
+    s = int64_to_f32_rn(sum_fixed) * F32(2.0 ** -FIXED_SHIFT)
+    return (s / count.astype(F32)[:, None]).astype(F32)
+
+
+def filter_frame(p: KeyParams, cam, frame: int, v: Dict[str, np.ndarray],
+                 ids=None, stream: int = 0) -> FrameResult:
+    """One frame of hashed path space filtering over the vertex arrays `v`."""
+    keys = vertex_keys(p, cam, frame, v["px"], v["py"], v["pz"], v["nx"], v["ny"], v["nz"],
+                       ids=ids, stream=stream)
+    tuples = keys.tuples()
+    uniq, inv, cnt = group_cells(tuples)
+    C = uniq.shape[0]
+    rgb = np.column_stack([np.asarray(v[c], dtype=F32) for c in ("r", "g", "b")])
+    sum64 = np.column_stack([np.bincount(inv, weights=rgb[:, j].astype(np.float64), minlength=C)
+                             for j in range(3)])
+    fx = to_fixed(rgb)
+    sumfx = np.zeros((C, 3), dtype=np.int64)
+    np.add.at(sumfx, inv, fx)
+    count = cnt[inv].astype(np.int64)
+    mean64 = sum64[inv] / count[:, None]
+    mean_fixed = fixed_mean_f32(sumfx, cnt)[inv]
+    # one representative vertex per cell gives the cell's home and fingerprint
+    rep = np.zeros(C, dtype=np.int64)
+    rep[inv] = np.arange(inv.shape[0])
+    return FrameResult(keys, inv, uniq, count, mean64, mean_fixed, cnt.astype(np.int64),
+                       sum64, sumfx, keys.home[rep], keys.fp[rep])
+
+
+# ----------------------------------------------------------------------------
+# Temporal filtering / integration, Sec. 3.4.1.
+# ----------------------------------------------------------------------------
+@dataclass
+class History:
+    """Per-cell history: sorted tuples, blended averages c and sample counts N."""
+
+    tuples: np.ndarray
+    c: np.ndarray
+    n: np.ndarray
+
+    @staticmethod
+    def empty() -> "History":
+        return History(np.zeros((0, 7), dtype=np.int64), np.zeros((0, 3)),
+                       np.zeros(0, dtype=np.int64))
+
+
+def blend(history: History, fr: FrameResult, alpha: float, fp16: bool = False,
+          n_cap: Optional[int] = None) -> Tuple[History, np.ndarray, np.ndarray]:
+    """c = alpha c_old + (1 - alpha) c_new per cell present in this frame.
+
+    alpha < 0 selects the integrating weight N_old / (N_old + N_new).  A cell
+    without history takes c_new; cells absent this frame keep their history.
+    N <- N_old + N_new (capped at `n_cap` if given).  With `fp16` the stored
+    average is rounded to binary16, as a half-precision history store does.
+    Returns (new history, blended value per vertex (N, 3), count per vertex)."""
+    H = history.tuples.shape[0]
+    allk = np.concatenate([history.tuples, fr.tuples]) if H else fr.tuples
+    uniq, inv = np.unique(allk, axis=0, return_inverse=True)[:2]
+    inv = inv.reshape(-1)
+    U = uniq.shape[0]
+    io, inw = inv[:H], inv[H:]
+    has_old = np.zeros(U, dtype=bool)
+    has_old[io] = True
+    c = np.zeros((U, 3))
+    N = np.zeros(U, dtype=np.int64)
+    c[io] = history.c
+    N[io] = history.n
+    c_new = fr.cell_sum64 / fr.cell_count[:, None]
+    n_new = fr.cell_count
+    c_old = c[inw]
+    n_old = N[inw]
+    had = has_old[inw]
+    if alpha < 0:
+        a = (n_old / np.maximum(n_old + n_new, 1))[:, None]
+    else:
+        a = float(alpha)
+    out = np.where(had[:, None], a * c_old + (1.0 - a) * c_new, c_new)
+    if fp16:
+        out = out.astype(np.float16).astype(np.float64)
+    c[inw] = out
+    N[inw] = n_old + n_new
+    if n_cap is not None:
+        N = np.minimum(N, n_cap)
+    new = History(uniq, c, N)
+    return new, out[fr.cell], N[inw][fr.cell]
+
+
+# ----------------------------------------------------------------------------
+# Table audit: fingerprint ambiguity and probe-limit overflow (Sec. 3.2, 3.2.1).
+# ----------------------------------------------------------------------------
+def ambiguous_cells(cell_home: np.ndarray, cell_fp: np.ndarray, log2_slots: int,
+                    max_probes: int) -> np.ndarray:
+    """Cells whose fingerprint equals another cell's while their homes lie
+    closer than P slots (mod T), so that their probe windows overlap.  The
+    table may merge such cells, which the paper accepts as the price of
+    fingerprints (Sec. 3.2.1); cells further apart can never meet."""
+    T = 1 << log2_slots
+    order = np.argsort(cell_fp, kind="stable")
+    fs = cell_fp[order]
+    starts = np.nonzero(np.r_[True, fs[1:] != fs[:-1]])[0]
+    ends = np.r_[starts[1:], fs.shape[0]]
+    amb = np.zeros(cell_fp.shape[0], dtype=bool)
+    for s, e in zip(starts[ends - starts > 1], ends[ends - starts > 1]):
+        members = order[s:e]
+        hs = cell_home[members].astype(np.int64)
+        for a in range(members.shape[0]):
+            for b in range(a + 1, members.shape[0]):
+                d = (hs[b] - hs[a]) % T
+                if min(d, T - d) < max_probes:
+                    amb[members[a]] = amb[members[b]] = True
+    return amb
+
+
+def overflow_window_full(fp_table: np.ndarray, home: int, f: int, max_probes: int) -> bool:
+    """True iff slots home .. home+P-1 (mod T) are all occupied by fingerprints
+    other than f: the only state in which an insert may legally give up."""
+    T = fp_table.shape[0]
+    idx = (home + np.arange(max_probes)) % T
+    w = fp_table[idx]
+    return bool(np.all((w != 0) & (w != f)))
+
+
+def simulate_linear_probing(home: np.ndarray, fp: np.ndarray, log2_slots: int,
+                            max_probes: int):
+    """Sequential insert-only linear probing of distinct keys in the given order.
+
+    Returns (slot per key or -1 on overflow, probes used per key, final table)."""
+    T = 1 << log2_slots
+    table = np.zeros(T, dtype=U32)
+    slot = np.full(home.shape[0], -1, dtype=np.int64)
+    probes = np.zeros(home.shape[0], dtype=np.int64)
+    for j in range(home.shape[0]):
+        h = int(home[j])
+        f = int(fp[j])
+        for s in range(max_probes):
+            q = (h + s) & (T - 1)
+            cur = int(table[q])
+            if cur == 0:
+                table[q] = f
+                slot[j] = q
+                probes[j] = s + 1
+                break
+            if cur == f:
+                slot[j] = q
+                probes[j] = s + 1
+                break
+        else:
+            probes[j] = max_probes
+    return slot, probes, table
