@@ -1,0 +1,377 @@
+"""Throughput of hashed path space filtering on synthetic HD frames.
+
+One step = one frame of the whole hot path through the library's fused launch
+(pps_filter): key construction (Alg. 1), probing insert with atomic
+accumulation (Sec. 3.2), temporal blend (Sec. 3.4.1), one lookup per vertex,
+and the per-frame clear.  The workload is the HD configuration: 1920x1080, one
+path per pixel, 3 bounces with Russian roulette 0.8 (about 5.06 M vertices per
+frame), table 2^23 slots, FP32 history of 2^25 slots, alpha = 0.2, 16 frames
+with the camera moving 0.01 in x per frame; frames are generated once on the
+GPU and stay resident in HBM (182 MB of input per frame, larger than L2, and
+the steps cycle through the 16 frames).
+
+Multi-GPU (torchrun): every rank filters its own independent stream of frames
+(different path seeds) with its own table; no collective touches the data
+path (weak scaling).  `value` is all ranks' vertices / the slowest rank's time.
+
+`--impl reference` times the CPU oracle (the plain numpy implementation the
+tests compare against) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "filtered path vertices/sec (insert+query) and ms/frame at 1080p×3 bounces vs plain"
+UNIT = "vertices/s"
+FRAMES = 16
+CSRC = os.path.join(ROOT, "paper_1902_05942_gb300", "csrc")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_fused_hd_traffic.json")
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _source_hash() -> str:
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(CSRC)):
+        with open(os.path.join(CSRC, f), "rb") as fh:
+            h.update(f.encode())
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _traffic_per_launch():
+    """DRAM bytes of one k_fused launch from the committed ncu summary, or None
+    when the kernel sources changed since those counters were taken."""
+    try:
+        with open(TRAFFIC_FILE) as fh:
+            d = json.load(fh)
+        if d.get("source_sha") == _source_hash():
+            return float(d["dram_bytes_per_launch"])
+    except Exception:
+        pass
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 7:
+                self.rows.append(parts)
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4)
+                          if r[3 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.rows)}
+
+
+def make_frames(rank: int, device):
+    import torch
+    from paper_1902_05942_gb300 import configs, scene
+    w = configs.hd(FRAMES)
+    frames = []
+    for f in range(FRAMES):
+        spec = configs.frame_spec(w, 0, f)
+        spec.path_seed += 1000 * rank
+        spec.radiance_seed += 1000 * rank
+        v = scene.trace_stream(spec, f, device)
+        frames.append(({k: v[k] for k in scene.STREAMS}, tuple(spec.view.eye)))
+    torch.cuda.synchronize()
+    return w, frames
+
+
+def algorithmic_bytes(n: int, cells: int) -> int:
+    """Per frame: 36 B of vertex input + 12 B of output + 1 B status per vertex;
+    per occupied cell 20 B (accumulator and fingerprint written back once) and
+    32 B for the FP32 history cell read and written by the blend."""
+    return 49 * n + 52 * cells
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    from paper_1902_05942_gb300 import build, pps
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    build.build()
+    dev = torch.device("cuda", local)
+    w, frames = make_frames(rank, dev)
+    cfg = w.filters[0]
+    tab = pps.Table(cfg)
+    n_max = max(fr[0]["px"].numel() for fr in frames)
+    out = pps.empty_output(n_max, dev, count=False, status=True)
+    stream = torch.cuda.current_stream()
+    # argument blocks built once per frame; the timed loop only calls the C ABI
+    import ctypes
+    L = pps.lib()
+    sptr = stream.cuda_stream
+    calls = []
+    for v, eye in frames:
+        n = v["px"].numel()
+        calls.append((pps.camera(eye), pps.make_vertices(v, n), n,
+                      pps.make_output({k: t[:n] for k, t in out.items()}, n)))
+
+    def step(i):
+        cam, vs, n, os_ = calls[i % FRAMES]
+        rc = L.pps_filter(tab.handle, ctypes.byref(cam), i, ctypes.byref(vs), n, 1, cfg.alpha,
+                          ctypes.byref(os_), sptr)
+        if rc:
+            raise pps.PPSError(rc, pps.last_error())
+        return n
+
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize()
+    st = tab.stats()
+    total_n = sum(frames[(args.warmup + i) % FRAMES][0]["px"].numel() for i in range(args.steps))
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    cells = []
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        for i in range(args.steps):
+            step(args.warmup + i)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    st = tab.stats()  # cells of the last frame (deterministic per frame)
+    # cells per frame: one extra untimed pass per distinct frame for the byte count
+    for i in range(min(args.steps, FRAMES)):
+        step(args.warmup + i)
+        cells.append(tab.stats()["frame_cells"])
+    if ws > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        tn = torch.tensor([total_n], device=dev, dtype=torch.float64)
+        dist.all_reduce(tn)
+        job_n = float(tn.item())
+    else:
+        job_n = float(total_n)
+    value = job_n / (ms / 1e3)
+    ms_step = ms / args.steps
+    # roofline of the dominant (only) kernel: k_fused, one launch per step
+    mean_n = total_n / args.steps
+    mean_c = sum(cells) / len(cells)
+    alg = algorithmic_bytes(int(mean_n), int(mean_c))
+    achieved = alg / (ms_step / 1e3) / 1e9
+    peak, peak_kind = _peaks()
+    traffic = _traffic_per_launch()
+
+    # end to end through the host-buffer entry point: H2D of the inputs, the
+    # filter, D2H of r, g, b and status, inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        hv = [{k: t.cpu().pin_memory() for k, t in fr[0].items()} for fr in frames[:4]]
+        ho = pps.empty_output(n_max, "cpu", count=False, status=True)
+        ho = {k: t.pin_memory() for k, t in ho.items()}
+        tab_h = pps.Table(cfg)
+
+        def hstep(i):
+            v = hv[i % len(hv)]
+            n = v["px"].numel()
+            o = {k: t[:n] for k, t in ho.items()}
+            pps.pps_filter_host(tab_h.handle, pps.camera(frames[i % len(hv)][1]), i,
+                                pps.make_vertices(v, n, device=False), n, True, cfg.alpha,
+                                pps.make_output(o, n, device=False), stream)
+            return n
+
+        for i in range(args.warmup):
+            hstep(i)
+        torch.cuda.synchronize()
+        if ws > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        hn = sum(hstep(args.warmup + i) for i in range(args.steps))
+        dt = time.perf_counter() - t0
+        if ws > 1:
+            t = torch.tensor([dt], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = float(t.item())
+            tn = torch.tensor([hn], device=dev, dtype=torch.float64)
+            dist.all_reduce(tn)
+            hn = float(tn.item())
+        e2e = {"value": hn / dt, "unit": UNIT,
+               "h2d_bytes_per_step": int(36 * mean_n), "d2h_bytes_per_step": int(13 * mean_n),
+               "ms_per_step": 1e3 * dt / args.steps}
+        tab_h.close()
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "hd: 1920x1080 x 3 bounces (RR 0.8), ~5.06M vertices/frame, "
+                                   "T=2^23, P=16, FP32 history 2^25, alpha=0.2, 16 frames, "
+                                   "camera +0.01/frame",
+                       "vertices_per_frame": mean_n, "cells_per_frame": mean_c,
+                       "l2": "inputs larger than L2 (182 MB per frame, 16 frames cycled)",
+                       "parallelism": f"replicas x{ws} (independent frame streams)"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "peak_source": peak_kind, "kernel": "k_fused",
+                         "algorithmic_bytes_per_launch": alg},
+            "gpu_launches": args.steps,
+            "clocks": clk.summary(),
+            "e2e": e2e,
+        }
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(frames[0], w, args.cpu_sample)
+        print(json.dumps(line), flush=True)
+    tab.close()
+    if ws > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def _oracle_step(v_np, w, frame, eye, hist):
+    from oracle import pps_oracle as O
+    cfg = w.filters[0]
+    fr = O.filter_frame(O.KeyParams(**cfg.oracle_kwargs()), eye, frame, v_np)
+    hist, val, cnt = O.blend(hist, fr, cfg.alpha)
+    return hist
+
+
+def cpu_baseline(frame, w, sample):
+    """The CPU oracle as it stands, single-threaded numpy, on the first `sample`
+    vertices of one HD frame (a bounded sample: the full frame takes ~15 s)."""
+    from oracle import pps_oracle as O
+    v, eye = frame
+    v_np = {k: t[:sample].cpu().numpy() for k, t in v.items()}
+    t0 = time.perf_counter()
+    _oracle_step(v_np, w, 0, eye, O.History.empty())
+    dt = time.perf_counter() - t0
+    return {"value": sample / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"first {sample} vertices of HD frame 0, filter + blend, numpy FP64"}
+
+
+def run_reference(args):
+    """The oracle on the host cores, same workload/metric, bounded samples."""
+    ws, rank, local = _dist()
+    if rank != 0:
+        return
+    import torch
+    from oracle import pps_oracle as O
+    from paper_1902_05942_gb300 import configs, scene
+    w = configs.hd(FRAMES)
+    # bounded: about 30 M oracle vertices in total keeps the run to a few minutes
+    sample = max(50_000, min(args.cpu_sample, int(30e6 / (args.steps + args.warmup))))
+    hist = O.History.empty()
+    data = []
+    for f in range(FRAMES if args.steps + args.warmup > FRAMES else args.steps + args.warmup):
+        spec = configs.frame_spec(w, 0, f)
+        v = scene.trace_stream(spec, f, "cpu")
+        data.append(({k: v[k][:sample].numpy() for k in scene.STREAMS}, tuple(spec.view.eye)))
+    for i in range(args.warmup):
+        v, eye = data[i % len(data)]
+        hist = _oracle_step(v, w, i, eye, hist)
+    t0 = time.perf_counter()
+    n = 0
+    for i in range(args.steps):
+        v, eye = data[(args.warmup + i) % len(data)]
+        hist = _oracle_step(v, w, args.warmup + i, eye, hist)
+        n += v["px"].shape[0]
+    dt = time.perf_counter() - t0
+    value = n / dt
+    desc = f"first {sample} vertices of each HD frame, filter + blend, numpy FP64"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "hd (CPU oracle on a bounded sample of each frame)",
+                   "sample_vertices": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": desc},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=48)
+    ap.add_argument("--warmup", type=int, default=8)
+    ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
+    ap.add_argument("--cpu-sample", type=int, default=1_500_000)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

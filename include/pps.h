@@ -1,0 +1,275 @@
+/*
+ * pps.h -- C ABI of the GB300 hashed path space filtering library.
+ *
+ * The operation is the second phase of the method of Binder, Fricke and Keller,
+ * "Massively Parallel Path Space Filtering" (2019), Sec. 3: the input is a set
+ * of path vertices with their descriptors (position, normal) and their
+ * contributions L_i f_i cos (Eq. 9); every vertex receives the average of the
+ * contributions of all vertices whose quantized key equals its own (Eq. 7,
+ * Eq. 8/9 with w = 1), optionally blended across frames (Sec. 3.4.1).
+ *
+ * Conventions (all entry points):
+ *  - Every function is extern "C", returns int: PPS_OK (0) or a PPS_E* code;
+ *    pps_last_error() returns the message of the calling thread's last error.
+ *    No C++ exception crosses this boundary.
+ *  - Array arguments are DEVICE pointers owned by the caller unless the name
+ *    says _host.  The library owns only what pps_create allocates (the table,
+ *    its control block and, on demand, its scratch buffers) and frees it in
+ *    pps_destroy.
+ *  - Work is enqueued on the cudaStream_t passed as `void* stream` (NULL = the
+ *    legacy default stream) and runs asynchronously; only pps_stats,
+ *    pps_table_dump and pps_filter_host synchronize that stream.
+ *  - A table is bound to the device that was current at pps_create; call it
+ *    with that device current.  A table must not be used from two host threads
+ *    at once, and calls on one table must be ordered (same stream, or streams
+ *    ordered by events).
+ *  - Float inputs must be finite; normals must be unit length.
+ */
+#ifndef PPS_H
+#define PPS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes ------------------------------------------------------ */
+#define PPS_OK 0
+#define PPS_EINVAL 1  /* bad argument (NULL, size, alignment, range)          */
+#define PPS_ENOMEM 2  /* device or host allocation failed                      */
+#define PPS_ECUDA 3   /* a CUDA runtime call failed (message has the name)     */
+#define PPS_EDEVICE 4 /* a kernel raised the table's device error word         */
+#define PPS_ESTATE 5  /* call out of order for the table's frame state         */
+
+/* ---- per-vertex status written by pps_query / pps_filter ---------------- */
+#define PPS_STATUS_OK 0       /* cell average returned                         */
+#define PPS_STATUS_LOWCOUNT 1 /* average returned, count < lowcount_threshold  */
+#define PPS_STATUS_OVERFLOW 2 /* probe limit exceeded: the vertex's own,       */
+                              /* unfiltered contribution returned (Sec. 3.2)   */
+
+/* ---- modes -------------------------------------------------------------- */
+#define PPS_ACCUM_FP32 0  /* FP32 sums, FP32 count lane: red.add.v4.f32         */
+#define PPS_ACCUM_FIXED 1 /* int64 sums of round(v * 2^24): order-free, exact   */
+#define PPS_HIST_NONE 0   /* no temporal state: every frame starts empty        */
+#define PPS_HIST_FP32 1   /* history average FP32, count uint32                 */
+#define PPS_HIST_FP16 2   /* history average binary16, count uint16 saturating  */
+
+/*
+ * Table and key parameters (Algorithm 1; Sec. 3.1.1, 3.2, 3.2.1; Sec. 4).
+ *
+ *  log2_slots         T = 2^log2_slots cells, 4 <= log2_slots <= 30.  The index
+ *                     is hash & (T - 1) ("modulo", Sec. 3.2).
+ *  max_probes         P, linear-probing limit, 1 <= P <= min(T, 4096).  A vertex
+ *                     that finds neither its fingerprint nor an empty cell in
+ *                     P steps keeps its own contribution (Sec. 3.2).
+ *  voxel_scale        s > 0: the voxel edge is s times the projected size of a
+ *                     pixel at the vertex's camera distance (Sec. 4), snapped
+ *                     down to a power of two: 2^floor(log2(s * pixel_angle * d)).
+ *  pixel_angle        theta_px > 0 = 2 tan(fov_y / 2) / image height.
+ *  jitter             1: jitter positions in the tangent plane before
+ *                     quantization (Sec. 3.1.4, Alg. 1); 0: plain quantization.
+ *  seed               jitter key word 0 (word 1 is the frame number).
+ *  hash_seed_home     seed of hash  (MurmurHash3_x86_32) -> home index i.
+ *  hash_seed_fp       seed of hash2 (MurmurHash3_x86_32) -> fingerprint f; the
+ *                     sentinel 0 marks an empty cell and is remapped to 1
+ *                     (Sec. 3.2.1).
+ *  normal_in_home_hash 0: the quantized normal enters only hash2, exactly as
+ *                     Algorithm 1 prints it; 1: it enters both hashes
+ *                     ("the arguments ... may be extended", Alg. 1 caption).
+ *                     Cell membership is the same either way.
+ *  lod_min, lod_max   clamp of the level of detail, -126 < lod_min <= lod_max < 127.
+ *  accum_mode         PPS_ACCUM_FP32 or PPS_ACCUM_FIXED.
+ *  hist_mode          PPS_HIST_NONE, PPS_HIST_FP32 or PPS_HIST_FP16: the
+ *                     temporal state of Sec. 3.4.1 in a second open-addressed
+ *                     table whose fingerprints persist across frames.
+ *  lowcount_threshold a returned count below it is flagged LOWCOUNT (Sec. 3.3).
+ *  log2_hist_slots    history table size Th = 2^log2_hist_slots (0: same as T),
+ *                     4..30; probed with the same limit P.
+ *  reserved           must be zero.
+ */
+typedef struct pps_params {
+  uint32_t log2_slots;
+  uint32_t max_probes;
+  float voxel_scale;
+  float pixel_angle;
+  uint32_t jitter;
+  uint32_t seed;
+  uint32_t hash_seed_home;
+  uint32_t hash_seed_fp;
+  uint32_t normal_in_home_hash;
+  int32_t lod_min;
+  int32_t lod_max;
+  uint32_t accum_mode;
+  uint32_t hist_mode;
+  uint32_t lowcount_threshold;
+  uint32_t log2_hist_slots;
+  uint32_t reserved[3];
+} pps_params;
+
+/* Camera position p_cam of Algorithm 1 (world space). */
+typedef struct pps_camera {
+  float pos[3];
+} pps_camera;
+
+/*
+ * One batch of path vertices, structure of arrays, n entries each (device).
+ *  px,py,pz   position x;  nx,ny,nz unit normal n;  r,g,b contribution.
+ *  id         optional per-vertex jitter counter (NULL: id_base + index).
+ *  stream_id  second jitter counter word (e.g. a view index).
+ * All nine float arrays are required.  16-byte-aligned arrays are read with
+ * 128-bit loads; other alignments take a scalar path.
+ */
+typedef struct pps_vertices {
+  const float *px, *py, *pz;
+  const float *nx, *ny, *nz;
+  const float *r, *g, *b;
+  const uint32_t *id;
+  uint32_t id_base;
+  uint32_t stream_id;
+} pps_vertices;
+
+/*
+ * Per-vertex results (device), n entries each.
+ *  r,g,b   filtered contribution: the cell average (or the blended history
+ *          value with a history), or the own contribution on OVERFLOW.
+ *  count   optional: vertices behind the returned value (this frame's cell
+ *          count; N_old + N_new with a history; 0 on OVERFLOW).
+ *  status  optional: PPS_STATUS_* per vertex.
+ */
+typedef struct pps_output {
+  float *r, *g, *b;
+  uint32_t *count;
+  uint8_t *status;
+} pps_output;
+
+/* Counters of the last frame (filled by pps_stats). */
+typedef struct pps_stats_t {
+  uint64_t frame_cells;       /* cells claimed this frame                      */
+  uint64_t overflow_vertices; /* vertices that hit the probe limit this frame  */
+  uint64_t occupied_slots;    /* frame-table slots holding a fingerprint now   */
+  uint64_t vertices;          /* vertices inserted this frame                  */
+  uint64_t hist_overflow;     /* cells whose history window was full           */
+  uint64_t hist_occupied;     /* history slots holding a fingerprint           */
+  uint32_t device_error;      /* device error word (0 = none)                  */
+  uint32_t frame;             /* frame number of the last pps_build/pps_filter */
+} pps_stats_t;
+
+typedef struct pps_table pps_table;
+
+/* Library version string (static storage). */
+const char *pps_version(void);
+
+/* Copies the calling thread's last error message into buf (NUL-terminated,
+ * truncated to len).  Returns PPS_OK. */
+int pps_last_error(char *buf, size_t len);
+
+/*
+ * pps_create: allocate a table for `p` on the current device and clear it.
+ * The frame table's cells (Sec. 3.2) are separate arrays: fingerprints (4 B
+ * per cell) and accumulators (16 B FP32 / 32 B fixed).  With a history, a
+ * second table holds fingerprints (4 B) and history values (16 B FP32 / 8 B
+ * FP16) per history cell, plus 4 B per frame cell linking it to its history
+ * cell.  *out receives the handle.
+ * Errors: PPS_EINVAL (bad parameters), PPS_ENOMEM, PPS_ECUDA.
+ */
+int pps_create(pps_table **out, const pps_params *p);
+
+/* pps_destroy: synchronize the device and free everything pps_create and
+ * later calls allocated.  NULL is accepted. */
+int pps_destroy(pps_table *t);
+
+/*
+ * pps_build: begin a frame (Sec. 3, second phase): record the camera and the
+ * frame number (jitter key word 1) and empty the frame-table cells of the
+ * previous frame (the history is kept).
+ * Errors: PPS_EINVAL.
+ */
+int pps_build(pps_table *t, const pps_camera *cam, uint32_t frame, void *stream);
+
+/*
+ * pps_insert: for each of the n vertices compute its key (Algorithm 1), find
+ * or claim its cell by linear probing on the fingerprint word (Sec. 3.2,
+ * 3.2.1) and add its contribution and a count of one atomically (Sec. 3.2,
+ * Sec. 3.3.1).  The vertex that claims a cell also finds or claims the key's
+ * history cell when the table keeps a history.  slot_out (nullable, n entries): the vertex's cell index, or 0xFFFFFFFF when
+ * the probe limit was exceeded; pass it to pps_query to skip re-probing.
+ * May be called several times per frame.  Errors: PPS_EINVAL, PPS_ESTATE
+ * (no pps_build since the last pps_blend).
+ */
+int pps_insert(pps_table *t, const pps_vertices *v, size_t n, uint32_t *slot_out,
+               void *stream);
+
+/*
+ * pps_blend: temporal filtering / integration (Sec. 3.4.1) over every cell
+ * touched this frame: c = alpha * c_old + (1 - alpha) * c_new, where c_new is
+ * the cell's average this frame and c_old its history; alpha < 0 selects
+ * alpha = N_old / (N_old + N_new), which integrates exactly.  A cell without
+ * history takes c_new.  N <- N_old + N_new.  Requires hist_mode != NONE.
+ * After it, pps_query returns the blended value.  Errors: PPS_EINVAL, PPS_ESTATE.
+ */
+int pps_blend(pps_table *t, float alpha, void *stream);
+
+/*
+ * pps_query: one lookup per vertex (Sec. 3.3.1): the cell average sum / count
+ * (FP32 round-to-nearest division), or the blended history value after
+ * pps_blend.  slot_in (nullable) must come from pps_insert of the same vertices
+ * this frame; without it the key is recomputed and the cell found by
+ * read-only probing.  Errors: PPS_EINVAL.
+ */
+int pps_query(pps_table *t, const pps_vertices *v, size_t n, const uint32_t *slot_in,
+              const pps_output *out, void *stream);
+
+/*
+ * pps_filter: the whole frame in one persistent cooperative launch: build,
+ * insert, [blend if blend != 0], query and the per-frame clear, separated by
+ * grid-wide barriers, with each vertex's cell index kept on chip (shared
+ * memory) or, for large n, in a library-owned scratch buffer.  Results equal
+ * pps_build + pps_insert + [pps_blend] + pps_query.  The table is left ready
+ * for the next frame.  Errors: PPS_EINVAL, PPS_ENOMEM, PPS_ECUDA.
+ */
+int pps_filter(pps_table *t, const pps_camera *cam, uint32_t frame, const pps_vertices *v,
+               size_t n, int blend, float alpha, const pps_output *out, void *stream);
+
+/*
+ * pps_filter_host: pps_filter on HOST arrays (pinned or pageable): copies the
+ * nine input arrays to library-owned device buffers, filters, copies r, g, b
+ * (and count / status when non-NULL) back, and synchronizes `stream`.
+ * `v->id` must be NULL.  Errors: as pps_filter.
+ */
+int pps_filter_host(pps_table *t, const pps_camera *cam, uint32_t frame,
+                    const pps_vertices *v_host, size_t n, int blend, float alpha,
+                    const pps_output *out_host, void *stream);
+
+/*
+ * pps_keys: Algorithm 1 alone, for inspection: for each vertex write the full
+ * 32-bit home hash h (the home cell is h & (T - 1)) and the fingerprint f
+ * (never 0), using the camera and frame of the last pps_build / pps_filter.
+ * The table is not touched.  h_out and f_out: n entries each (device).
+ * Errors: PPS_EINVAL.
+ */
+int pps_keys(pps_table *t, const pps_vertices *v, size_t n, uint32_t *h_out, uint32_t *f_out,
+             void *stream);
+
+/*
+ * pps_stats: synchronize `stream` and read the table's counters.  Returns
+ * PPS_EDEVICE if a kernel raised the device error word (the word is then
+ * cleared).
+ */
+int pps_stats(pps_table *t, pps_stats_t *out, void *stream);
+
+/*
+ * pps_table_dump: synchronize `stream` and copy the table to host memory:
+ * fp_host[T] fingerprints (0 = empty); acc_host (nullable) the accumulators as
+ * 4 floats per cell {sum r, sum g, sum b, count} (FP32 mode) or 4 int64
+ * {sum r, sum g, sum b, count} (fixed mode).  T = 2^log2_slots.  Used to audit
+ * probe overflow and for inspection.  Errors: PPS_EINVAL, PPS_ECUDA.
+ */
+int pps_table_dump(pps_table *t, uint32_t *fp_host, void *acc_host, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PPS_H */

@@ -1,0 +1,444 @@
+// C ABI of the hashed path space filter (see include/pps.h for the contract).
+//
+// Host-side responsibilities only: argument checks, the per-table frame state
+// machine (clean -> open -> blended -> clean), device allocations owned by the
+// table, and kernel launches.  Every step of the filter itself runs in the
+// kernels of pps_kernels.cu.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "pps.h"
+#include "pps_internal.h"
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+
+int cuda_fail(const char* what, cudaError_t e) {
+  return fail(PPS_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define PPS_CUDA(call)                                \
+  do {                                                \
+    cudaError_t e_ = (call);                          \
+    if (e_ != cudaSuccess) return cuda_fail(#call, e_); \
+  } while (0)
+
+enum FrameState { kClean = 0, kOpen = 1, kBlended = 2 };
+
+}  // namespace
+
+struct pps_table {
+  pps_params p{};
+  int device = 0;
+  uint32_t T = 0;
+  uint32_t Th = 0;
+  pps::TableDev dev{};
+  pps::KeyConst kc{};
+  int state = kClean;
+  uint32_t* gstash = nullptr;
+  size_t gstash_cap = 0;
+  void* stage = nullptr;  // pps_filter_host device staging
+  size_t stage_cap = 0;
+  unsigned long long* scratch_u64 = nullptr;  // 1 word for occupancy counting
+};
+
+namespace {
+
+int check_params(const pps_params* p) {
+  if (!p) return fail(PPS_EINVAL, "params is NULL");
+  if (p->log2_slots < 4 || p->log2_slots > 30) return fail(PPS_EINVAL, "log2_slots must be in [4, 30]");
+  const uint64_t T = 1ull << p->log2_slots;
+  if (p->max_probes < 1 || p->max_probes > T || p->max_probes > 4096)
+    return fail(PPS_EINVAL, "max_probes must be in [1, min(T, 4096)]");
+  if (!(p->voxel_scale > 0.0f) || !std::isfinite(p->voxel_scale))
+    return fail(PPS_EINVAL, "voxel_scale must be finite and > 0");
+  if (!(p->pixel_angle > 0.0f) || !std::isfinite(p->pixel_angle))
+    return fail(PPS_EINVAL, "pixel_angle must be finite and > 0");
+  if (p->lod_min <= -126 || p->lod_max >= 127 || p->lod_min > p->lod_max)
+    return fail(PPS_EINVAL, "need -126 < lod_min <= lod_max < 127");
+  if (p->accum_mode > PPS_ACCUM_FIXED) return fail(PPS_EINVAL, "bad accum_mode");
+  if (p->hist_mode > PPS_HIST_FP16) return fail(PPS_EINVAL, "bad hist_mode");
+  if (p->jitter > 1 || p->normal_in_home_hash > 1) return fail(PPS_EINVAL, "flags must be 0 or 1");
+  if (p->log2_hist_slots != 0 && (p->log2_hist_slots < 4 || p->log2_hist_slots > 30))
+    return fail(PPS_EINVAL, "log2_hist_slots must be 0 or in [4, 30]");
+  if (p->log2_hist_slots != 0 && p->max_probes > (1ull << p->log2_hist_slots))
+    return fail(PPS_EINVAL, "max_probes exceeds the history table size");
+  for (uint32_t r : p->reserved)
+    if (r) return fail(PPS_EINVAL, "reserved fields must be zero");
+  return PPS_OK;
+}
+
+int check_table(pps_table* t) {
+  if (!t) return fail(PPS_EINVAL, "table is NULL");
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev != t->device)
+    return fail(PPS_EINVAL, "the table's device is not the current device");
+  return PPS_OK;
+}
+
+int check_vertices(const pps_vertices* v, size_t n) {
+  if (!v) return fail(PPS_EINVAL, "vertices is NULL");
+  if (n == 0) return PPS_OK;
+  if (!v->px || !v->py || !v->pz || !v->nx || !v->ny || !v->nz || !v->r || !v->g || !v->b)
+    return fail(PPS_EINVAL, "all nine vertex arrays are required");
+  if (n > (1ull << 40)) return fail(PPS_EINVAL, "n too large");
+  return PPS_OK;
+}
+
+int check_output(const pps_output* o, size_t n) {
+  if (!o) return fail(PPS_EINVAL, "output is NULL");
+  if (n && (!o->r || !o->g || !o->b)) return fail(PPS_EINVAL, "output r, g, b are required");
+  return PPS_OK;
+}
+
+pps::VertexPtrs to_dev(const pps_vertices* v) {
+  pps::VertexPtrs d;
+  d.px = v->px;
+  d.py = v->py;
+  d.pz = v->pz;
+  d.nx = v->nx;
+  d.ny = v->ny;
+  d.nz = v->nz;
+  d.r = v->r;
+  d.g = v->g;
+  d.b = v->b;
+  d.id = v->id;
+  d.id_base = v->id_base;
+  d.stream_id = v->stream_id;
+  return d;
+}
+
+pps::OutPtrs to_dev(const pps_output* o) {
+  pps::OutPtrs d;
+  d.r = o->r;
+  d.g = o->g;
+  d.b = o->b;
+  d.count = o->count;
+  d.status = o->status;
+  return d;
+}
+
+bool temporal(const pps_table* t) { return t->p.hist_mode != PPS_HIST_NONE; }
+
+// Empty the cells touched since the last clear (dirty list) and reset the
+// frame counters.
+int reset_frame(pps_table* t, cudaStream_t st) {
+  if (t->state != kClean) {
+    PPS_CUDA(pps::launch_clear_dirty(t->dev, st));
+    PPS_CUDA(cudaMemsetAsync(&t->dev.ctrl->dirty_count, 0, sizeof(unsigned int), st));
+    t->state = kClean;
+  }
+  PPS_CUDA(cudaMemsetAsync(t->dev.ctrl, 0, pps::kCtrlFrameBytes, st));
+  return PPS_OK;
+}
+
+void set_camera(pps_table* t, const pps_camera* cam, uint32_t frame) {
+  t->kc.cam[0] = cam->pos[0];
+  t->kc.cam[1] = cam->pos[1];
+  t->kc.cam[2] = cam->pos[2];
+  t->kc.frame = frame;
+}
+
+void free_all(pps_table* t) {
+  cudaFree(t->dev.fp);
+  cudaFree(t->dev.acc);
+  cudaFree(t->dev.acc64);
+  cudaFree(t->dev.hist);
+  cudaFree(t->dev.hist16);
+  cudaFree(t->dev.hfp);
+  cudaFree(t->dev.hslot);
+  cudaFree(t->dev.dirty);
+  cudaFree(t->dev.ctrl);
+  cudaFree(t->gstash);
+  cudaFree(t->stage);
+  cudaFree(t->scratch_u64);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* pps_version(void) { return "pps-gb300 0.1 (sm_103a)"; }
+
+int pps_last_error(char* buf, size_t len) {
+  if (buf && len) {
+    std::strncpy(buf, g_err.c_str(), len - 1);
+    buf[len - 1] = '\0';
+  }
+  return PPS_OK;
+}
+
+int pps_create(pps_table** out, const pps_params* p) {
+  if (!out) return fail(PPS_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (int rc = check_params(p)) return rc;
+  pps_table* t = new (std::nothrow) pps_table();
+  if (!t) return fail(PPS_ENOMEM, "host allocation failed");
+  t->p = *p;
+  t->T = 1u << p->log2_slots;
+  t->Th = 1u << (p->log2_hist_slots ? p->log2_hist_slots : p->log2_slots);
+  cudaGetDevice(&t->device);
+  const size_t T = t->T;
+  const size_t Th = t->Th;
+  auto alloc = [&](void** ptr, size_t bytes) -> cudaError_t {
+    cudaError_t e = cudaMalloc(ptr, bytes);
+    if (e == cudaSuccess) e = cudaMemset(*ptr, 0, bytes);
+    return e;
+  };
+  cudaError_t e = alloc(reinterpret_cast<void**>(&t->dev.fp), T * sizeof(uint32_t));
+  if (e == cudaSuccess) {
+    if (p->accum_mode == PPS_ACCUM_FP32)
+      e = alloc(reinterpret_cast<void**>(&t->dev.acc), T * sizeof(float4));
+    else
+      e = alloc(reinterpret_cast<void**>(&t->dev.acc64), T * sizeof(pps::AccFixed));
+  }
+  if (e == cudaSuccess && p->hist_mode != PPS_HIST_NONE) {
+    e = alloc(reinterpret_cast<void**>(&t->dev.hfp), Th * sizeof(uint32_t));
+    if (e == cudaSuccess) e = alloc(reinterpret_cast<void**>(&t->dev.hslot), T * sizeof(uint32_t));
+  }
+  if (e == cudaSuccess && p->hist_mode == PPS_HIST_FP32)
+    e = alloc(reinterpret_cast<void**>(&t->dev.hist), Th * sizeof(float4));
+  if (e == cudaSuccess && p->hist_mode == PPS_HIST_FP16)
+    e = alloc(reinterpret_cast<void**>(&t->dev.hist16), Th * sizeof(uint2));
+  if (e == cudaSuccess) e = alloc(reinterpret_cast<void**>(&t->dev.dirty), T * sizeof(uint32_t));
+  if (e == cudaSuccess) e = alloc(reinterpret_cast<void**>(&t->dev.ctrl), sizeof(pps::Ctrl));
+  if (e == cudaSuccess) e = alloc(reinterpret_cast<void**>(&t->scratch_u64), 2 * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    free_all(t);
+    delete t;
+    cudaGetLastError();
+    return fail(e == cudaErrorMemoryAllocation ? PPS_ENOMEM : PPS_ECUDA,
+                std::string("pps_create: ") + cudaGetErrorString(e));
+  }
+  t->dev.mask = t->T - 1;
+  t->dev.hmask = t->Th - 1;
+  t->dev.max_probes = p->max_probes;
+  t->dev.lowcount = p->lowcount_threshold;
+  t->dev.fixed = p->accum_mode == PPS_ACCUM_FIXED;
+  t->dev.hist_mode = static_cast<int>(p->hist_mode);
+  t->kc.k = p->voxel_scale * p->pixel_angle;  // fl32(s * theta_px)
+  t->kc.seed = p->seed;
+  t->kc.hseed_home = p->hash_seed_home;
+  t->kc.hseed_fp = p->hash_seed_fp;
+  t->kc.mask = t->T - 1;
+  t->kc.max_probes = p->max_probes;
+  t->kc.lod_min = p->lod_min;
+  t->kc.lod_max = p->lod_max;
+  t->kc.jitter = p->jitter;
+  t->kc.nih = p->normal_in_home_hash;
+  *out = t;
+  return PPS_OK;
+}
+
+int pps_destroy(pps_table* t) {
+  if (!t) return PPS_OK;
+  int prev = -1;
+  cudaGetDevice(&prev);
+  cudaSetDevice(t->device);
+  cudaDeviceSynchronize();
+  free_all(t);
+  delete t;
+  if (prev >= 0) cudaSetDevice(prev);
+  return PPS_OK;
+}
+
+int pps_build(pps_table* t, const pps_camera* cam, uint32_t frame, void* stream) {
+  if (int rc = check_table(t)) return rc;
+  if (!cam) return fail(PPS_EINVAL, "camera is NULL");
+  const cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (int rc = reset_frame(t, st)) return rc;
+  set_camera(t, cam, frame);
+  t->state = kOpen;
+  return PPS_OK;
+}
+
+int pps_insert(pps_table* t, const pps_vertices* v, size_t n, uint32_t* slot_out, void* stream) {
+  if (int rc = check_table(t)) return rc;
+  if (int rc = check_vertices(v, n)) return rc;
+  if (t->state != kOpen) return fail(PPS_ESTATE, "pps_insert needs pps_build first (and no pps_blend since)");
+  PPS_CUDA(pps::launch_insert(t->kc, t->dev, to_dev(v), n, slot_out,
+                              static_cast<cudaStream_t>(stream)));
+  return PPS_OK;
+}
+
+int pps_blend(pps_table* t, float alpha, void* stream) {
+  if (int rc = check_table(t)) return rc;
+  if (!temporal(t)) return fail(PPS_EINVAL, "pps_blend needs a table with hist_mode != NONE");
+  if (!std::isfinite(alpha) || alpha > 1.0f) return fail(PPS_EINVAL, "alpha must be finite and <= 1");
+  if (t->state != kOpen) return fail(PPS_ESTATE, "pps_blend needs an open frame (pps_build, pps_insert)");
+  PPS_CUDA(pps::launch_blend(t->dev, alpha, static_cast<cudaStream_t>(stream)));
+  t->state = kBlended;
+  return PPS_OK;
+}
+
+int pps_query(pps_table* t, const pps_vertices* v, size_t n, const uint32_t* slot_in,
+              const pps_output* out, void* stream) {
+  if (int rc = check_table(t)) return rc;
+  if (int rc = check_vertices(v, n)) return rc;
+  if (int rc = check_output(out, n)) return rc;
+  if (t->state == kClean) return fail(PPS_ESTATE, "pps_query needs an open frame");
+  PPS_CUDA(pps::launch_query(t->kc, t->dev, to_dev(v), n, slot_in, to_dev(out),
+                             t->state == kBlended, static_cast<cudaStream_t>(stream)));
+  return PPS_OK;
+}
+
+int pps_filter(pps_table* t, const pps_camera* cam, uint32_t frame, const pps_vertices* v,
+               size_t n, int blend, float alpha, const pps_output* out, void* stream) {
+  if (int rc = check_table(t)) return rc;
+  if (!cam) return fail(PPS_EINVAL, "camera is NULL");
+  if (int rc = check_vertices(v, n)) return rc;
+  if (int rc = check_output(out, n)) return rc;
+  if (blend && !temporal(t)) return fail(PPS_EINVAL, "blend needs a table with hist_mode != NONE");
+  if (blend && (!std::isfinite(alpha) || alpha > 1.0f))
+    return fail(PPS_EINVAL, "alpha must be finite and <= 1");
+  const cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (int rc = reset_frame(t, st)) return rc;
+  set_camera(t, cam, frame);
+  if (n == 0) return PPS_OK;
+  pps::FusedPlan plan;
+  PPS_CUDA(pps::plan_fused(n, temporal(t), &plan));
+  // the kernel writes stash words [0, chunk * grid): CTA b owns [b * chunk, (b + 1) * chunk)
+  const size_t stash_need = plan.chunk * static_cast<size_t>(plan.grid);
+  if (plan.global_stash && t->gstash_cap < stash_need) {
+    cudaFree(t->gstash);
+    t->gstash = nullptr;
+    t->gstash_cap = 0;
+    const size_t cap = stash_need;
+    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&t->gstash), cap * sizeof(uint32_t));
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(PPS_ENOMEM, "pps_filter: scratch stash allocation failed");
+    }
+    t->gstash_cap = cap;
+  }
+  PPS_CUDA(pps::launch_fused(t->kc, t->dev, to_dev(v), n, to_dev(out), temporal(t), blend != 0,
+                             alpha, plan, t->gstash, st));
+  t->state = kClean;
+  return PPS_OK;
+}
+
+int pps_filter_host(pps_table* t, const pps_camera* cam, uint32_t frame, const pps_vertices* vh,
+                    size_t n, int blend, float alpha, const pps_output* oh, void* stream) {
+  if (int rc = check_table(t)) return rc;
+  if (int rc = check_vertices(vh, n)) return rc;
+  if (int rc = check_output(oh, n)) return rc;
+  if (vh->id) return fail(PPS_EINVAL, "pps_filter_host takes no id array");
+  const cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // staging: 9 input floats, 3 output floats, 1 count word, status bytes (rounded)
+  const size_t nn = (n + 3) & ~static_cast<size_t>(3);
+  const size_t need = nn * (9 + 3 + 1) * sizeof(float) + nn;
+  if (t->stage_cap < need) {
+    cudaFree(t->stage);
+    t->stage = nullptr;
+    t->stage_cap = 0;
+    cudaError_t e = cudaMalloc(&t->stage, need);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(PPS_ENOMEM, "pps_filter_host: staging allocation failed");
+    }
+    t->stage_cap = need;
+  }
+  float* base = static_cast<float*>(t->stage);
+  const float* src[9] = {vh->px, vh->py, vh->pz, vh->nx, vh->ny, vh->nz, vh->r, vh->g, vh->b};
+  float* dst[9];
+  for (int i = 0; i < 9; ++i) {
+    dst[i] = base + static_cast<size_t>(i) * nn;
+    PPS_CUDA(cudaMemcpyAsync(dst[i], src[i], n * sizeof(float), cudaMemcpyHostToDevice, st));
+  }
+  pps_vertices vd{};
+  vd.px = dst[0];
+  vd.py = dst[1];
+  vd.pz = dst[2];
+  vd.nx = dst[3];
+  vd.ny = dst[4];
+  vd.nz = dst[5];
+  vd.r = dst[6];
+  vd.g = dst[7];
+  vd.b = dst[8];
+  vd.id_base = vh->id_base;
+  vd.stream_id = vh->stream_id;
+  pps_output od{};
+  od.r = base + 9 * nn;
+  od.g = base + 10 * nn;
+  od.b = base + 11 * nn;
+  od.count = oh->count ? reinterpret_cast<uint32_t*>(base + 12 * nn) : nullptr;
+  od.status = oh->status ? reinterpret_cast<uint8_t*>(base + 13 * nn) : nullptr;
+  if (int rc = pps_filter(t, cam, frame, &vd, n, blend, alpha, &od, stream)) return rc;
+  PPS_CUDA(cudaMemcpyAsync(oh->r, od.r, n * sizeof(float), cudaMemcpyDeviceToHost, st));
+  PPS_CUDA(cudaMemcpyAsync(oh->g, od.g, n * sizeof(float), cudaMemcpyDeviceToHost, st));
+  PPS_CUDA(cudaMemcpyAsync(oh->b, od.b, n * sizeof(float), cudaMemcpyDeviceToHost, st));
+  if (oh->count)
+    PPS_CUDA(cudaMemcpyAsync(oh->count, od.count, n * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+  if (oh->status)
+    PPS_CUDA(cudaMemcpyAsync(oh->status, od.status, n, cudaMemcpyDeviceToHost, st));
+  PPS_CUDA(cudaStreamSynchronize(st));
+  return PPS_OK;
+}
+
+int pps_keys(pps_table* t, const pps_vertices* v, size_t n, uint32_t* h_out, uint32_t* f_out,
+             void* stream) {
+  if (int rc = check_table(t)) return rc;
+  if (int rc = check_vertices(v, n)) return rc;
+  if (n && (!h_out || !f_out)) return fail(PPS_EINVAL, "h_out and f_out are required");
+  PPS_CUDA(pps::launch_keys(t->kc, to_dev(v), n, h_out, f_out, static_cast<cudaStream_t>(stream)));
+  return PPS_OK;
+}
+
+int pps_stats(pps_table* t, pps_stats_t* out, void* stream) {
+  if (int rc = check_table(t)) return rc;
+  if (!out) return fail(PPS_EINVAL, "out is NULL");
+  const cudaStream_t st = static_cast<cudaStream_t>(stream);
+  PPS_CUDA(cudaMemsetAsync(t->scratch_u64, 0, 2 * sizeof(unsigned long long), st));
+  PPS_CUDA(pps::launch_count_occupied(t->dev.fp, t->T, t->scratch_u64, st));
+  if (t->dev.hfp) PPS_CUDA(pps::launch_count_occupied(t->dev.hfp, t->Th, t->scratch_u64 + 1, st));
+  pps::Ctrl c;
+  unsigned long long occ[2] = {0, 0};
+  PPS_CUDA(cudaMemcpyAsync(&c, t->dev.ctrl, sizeof(c), cudaMemcpyDeviceToHost, st));
+  PPS_CUDA(cudaMemcpyAsync(occ, t->scratch_u64, sizeof(occ), cudaMemcpyDeviceToHost, st));
+  PPS_CUDA(cudaStreamSynchronize(st));
+  std::memset(out, 0, sizeof(*out));
+  out->frame_cells = c.frame_cells;
+  out->overflow_vertices = c.overflow_vertices;
+  out->vertices = c.vertices;
+  out->occupied_slots = occ[0];
+  out->hist_occupied = occ[1];
+  out->hist_overflow = c.hist_overflow;
+  out->device_error = c.error;
+  out->frame = t->kc.frame;
+  if (c.error) {
+    // clear the error word and the barrier state so the table stays usable
+    PPS_CUDA(cudaMemsetAsync(&t->dev.ctrl->error, 0, 3 * sizeof(unsigned int), st));
+    PPS_CUDA(cudaStreamSynchronize(st));
+    char buf[96];
+    std::snprintf(buf, sizeof(buf), "device error word 0x%x", c.error);
+    return fail(PPS_EDEVICE, buf);
+  }
+  return PPS_OK;
+}
+
+int pps_table_dump(pps_table* t, uint32_t* fp_host, void* acc_host, void* stream) {
+  if (int rc = check_table(t)) return rc;
+  if (!fp_host) return fail(PPS_EINVAL, "fp_host is NULL");
+  const cudaStream_t st = static_cast<cudaStream_t>(stream);
+  PPS_CUDA(cudaMemcpyAsync(fp_host, t->dev.fp, t->T * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+  if (acc_host) {
+    if (t->dev.fixed)
+      PPS_CUDA(cudaMemcpyAsync(acc_host, t->dev.acc64, t->T * sizeof(pps::AccFixed),
+                               cudaMemcpyDeviceToHost, st));
+    else
+      PPS_CUDA(cudaMemcpyAsync(acc_host, t->dev.acc, t->T * sizeof(float4), cudaMemcpyDeviceToHost, st));
+  }
+  PPS_CUDA(cudaStreamSynchronize(st));
+  return PPS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,312 @@
+"""Python binding of the C ABI in include/pps.h (argument marshalling only).
+
+The functions carry the C names (``pps_create``, ``pps_build``, ``pps_insert``,
+``pps_blend``, ``pps_query``, ``pps_filter``, ...) and take torch tensors,
+whose device pointers are handed to the library unchanged; every step of the
+filter runs in the CUDA library.  ``Table`` is a small convenience wrapper.
+
+The library is ``libpps.so`` next to this file (built by ``build.py``).  If it
+is missing, loading raises: there is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Dict, Optional, Sequence
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpps.so")
+
+PPS_OK, PPS_EINVAL, PPS_ENOMEM, PPS_ECUDA, PPS_EDEVICE, PPS_ESTATE = range(6)
+STATUS_OK, STATUS_LOWCOUNT, STATUS_OVERFLOW = 0, 1, 2
+ACCUM_FP32, ACCUM_FIXED = 0, 1
+HIST_NONE, HIST_FP32, HIST_FP16 = 0, 1, 2
+OVERFLOW_SLOT = 0xFFFFFFFF
+
+_u32, _i32, _f32 = ctypes.c_uint32, ctypes.c_int32, ctypes.c_float
+_vp = ctypes.c_void_p
+
+
+class pps_params(ctypes.Structure):
+    _fields_ = [("log2_slots", _u32), ("max_probes", _u32), ("voxel_scale", _f32),
+                ("pixel_angle", _f32), ("jitter", _u32), ("seed", _u32),
+                ("hash_seed_home", _u32), ("hash_seed_fp", _u32),
+                ("normal_in_home_hash", _u32), ("lod_min", _i32), ("lod_max", _i32),
+                ("accum_mode", _u32), ("hist_mode", _u32), ("lowcount_threshold", _u32),
+                ("log2_hist_slots", _u32), ("reserved", _u32 * 3)]
+
+
+class pps_camera(ctypes.Structure):
+    _fields_ = [("pos", _f32 * 3)]
+
+
+class pps_vertices(ctypes.Structure):
+    _fields_ = [("px", _vp), ("py", _vp), ("pz", _vp), ("nx", _vp), ("ny", _vp), ("nz", _vp),
+                ("r", _vp), ("g", _vp), ("b", _vp), ("id", _vp), ("id_base", _u32),
+                ("stream_id", _u32)]
+
+
+class pps_output(ctypes.Structure):
+    _fields_ = [("r", _vp), ("g", _vp), ("b", _vp), ("count", _vp), ("status", _vp)]
+
+
+class pps_stats_t(ctypes.Structure):
+    _fields_ = [("frame_cells", ctypes.c_uint64), ("overflow_vertices", ctypes.c_uint64),
+                ("occupied_slots", ctypes.c_uint64), ("vertices", ctypes.c_uint64),
+                ("hist_overflow", ctypes.c_uint64), ("hist_occupied", ctypes.c_uint64),
+                ("device_error", _u32), ("frame", _u32)]
+
+
+# Every exported function and its argument types.
+SIGNATURES = {
+    "pps_version": ([], ctypes.c_char_p),
+    "pps_last_error": ([ctypes.c_char_p, ctypes.c_size_t], ctypes.c_int),
+    "pps_create": ([ctypes.POINTER(_vp), ctypes.POINTER(pps_params)], ctypes.c_int),
+    "pps_destroy": ([_vp], ctypes.c_int),
+    "pps_build": ([_vp, ctypes.POINTER(pps_camera), _u32, _vp], ctypes.c_int),
+    "pps_insert": ([_vp, ctypes.POINTER(pps_vertices), ctypes.c_size_t, _vp, _vp], ctypes.c_int),
+    "pps_blend": ([_vp, _f32, _vp], ctypes.c_int),
+    "pps_query": ([_vp, ctypes.POINTER(pps_vertices), ctypes.c_size_t, _vp,
+                   ctypes.POINTER(pps_output), _vp], ctypes.c_int),
+    "pps_filter": ([_vp, ctypes.POINTER(pps_camera), _u32, ctypes.POINTER(pps_vertices),
+                    ctypes.c_size_t, ctypes.c_int, _f32, ctypes.POINTER(pps_output), _vp],
+                   ctypes.c_int),
+    "pps_filter_host": ([_vp, ctypes.POINTER(pps_camera), _u32, ctypes.POINTER(pps_vertices),
+                         ctypes.c_size_t, ctypes.c_int, _f32, ctypes.POINTER(pps_output), _vp],
+                        ctypes.c_int),
+    "pps_keys": ([_vp, ctypes.POINTER(pps_vertices), ctypes.c_size_t, _vp, _vp, _vp],
+                 ctypes.c_int),
+    "pps_stats": ([_vp, ctypes.POINTER(pps_stats_t), _vp], ctypes.c_int),
+    "pps_table_dump": ([_vp, _vp, _vp, _vp], ctypes.c_int),
+}
+
+_lib: Optional[ctypes.CDLL] = None
+
+
+class PPSError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"pps error {code}: {msg}")
+        self.code = code
+
+
+def lib() -> ctypes.CDLL:
+    """Load libpps.so (raises when it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "`python -m paper_1902_05942_gb300.build`")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (args, res) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = L
+    return _lib
+
+
+def last_error() -> str:
+    buf = ctypes.create_string_buffer(512)
+    lib().pps_last_error(buf, 512)
+    return buf.value.decode(errors="replace")
+
+
+def _check(rc: int):
+    if rc != PPS_OK:
+        raise PPSError(rc, last_error())
+
+
+def _stream(stream) -> Optional[int]:
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, torch.cuda.Stream):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def _ptr(t: Optional[torch.Tensor], n: int, dtype, name: str, device=True) -> Optional[int]:
+    if t is None:
+        return None
+    if t.dtype != dtype or not t.is_contiguous() or t.numel() < n:
+        raise ValueError(f"{name}: need a contiguous {dtype} tensor of >= {n} elements")
+    if device and not t.is_cuda:
+        raise ValueError(f"{name}: need a CUDA tensor")
+    if not device and t.is_cuda:
+        raise ValueError(f"{name}: need a host tensor")
+    return t.data_ptr()
+
+
+STREAM_NAMES = ("px", "py", "pz", "nx", "ny", "nz", "r", "g", "b")
+
+
+def make_vertices(v: Dict[str, torch.Tensor], n: Optional[int] = None, ids=None, id_base=0,
+                  stream_id=0, device=True) -> pps_vertices:
+    n = v["px"].numel() if n is None else n
+    ptrs = [_ptr(v[k], n, torch.float32, k, device) for k in STREAM_NAMES]
+    return pps_vertices(*ptrs, _ptr(ids, n, torch.int32, "id", device) if ids is not None
+                        else None, id_base & 0xFFFFFFFF, stream_id & 0xFFFFFFFF)
+
+
+def make_output(out: Dict[str, torch.Tensor], n: int, device=True) -> pps_output:
+    return pps_output(_ptr(out["r"], n, torch.float32, "r", device),
+                      _ptr(out["g"], n, torch.float32, "g", device),
+                      _ptr(out["b"], n, torch.float32, "b", device),
+                      _ptr(out.get("count"), n, torch.int32, "count", device),
+                      _ptr(out.get("status"), n, torch.uint8, "status", device))
+
+
+def make_params(cfg, hist_mode: Optional[int] = None, accum_fixed: Optional[bool] = None,
+                log2_hist_slots: Optional[int] = None) -> pps_params:
+    """pps_params from a FilterConfig-like object (attribute names as in configs.py)."""
+    hm = cfg.hist_mode if hist_mode is None else hist_mode
+    fx = cfg.accum_fixed if accum_fixed is None else accum_fixed
+    lh = cfg.log2_hist_slots if log2_hist_slots is None else log2_hist_slots
+    return pps_params(cfg.log2_slots, cfg.max_probes, cfg.voxel_scale, cfg.pixel_angle,
+                      int(cfg.jitter), cfg.seed & 0xFFFFFFFF, cfg.hash_seed_home & 0xFFFFFFFF,
+                      cfg.hash_seed_fp & 0xFFFFFFFF, int(cfg.normal_in_home_hash), cfg.lod_min,
+                      cfg.lod_max, ACCUM_FIXED if fx else ACCUM_FP32, hm,
+                      cfg.lowcount_threshold, lh, (_u32 * 3)(0, 0, 0))
+
+
+def camera(pos: Sequence[float]) -> pps_camera:
+    return pps_camera((_f32 * 3)(*[float(x) for x in pos]))
+
+
+# ---------------------------------------------------------------- C-named calls
+def pps_version() -> str:
+    return lib().pps_version().decode()
+
+
+def pps_create(params: pps_params) -> int:
+    h = _vp()
+    _check(lib().pps_create(ctypes.byref(h), ctypes.byref(params)))
+    return h.value
+
+
+def pps_destroy(handle: int):
+    _check(lib().pps_destroy(handle))
+
+
+def pps_build(handle, cam: pps_camera, frame: int, stream=None):
+    _check(lib().pps_build(handle, ctypes.byref(cam), frame & 0xFFFFFFFF, _stream(stream)))
+
+
+def pps_insert(handle, v: pps_vertices, n: int, slot_out: Optional[torch.Tensor] = None,
+               stream=None):
+    _check(lib().pps_insert(handle, ctypes.byref(v), n,
+                            _ptr(slot_out, n, torch.int32, "slot_out"), _stream(stream)))
+
+
+def pps_blend(handle, alpha: float, stream=None):
+    _check(lib().pps_blend(handle, float(alpha), _stream(stream)))
+
+
+def pps_query(handle, v: pps_vertices, n: int, slot_in: Optional[torch.Tensor],
+              out: pps_output, stream=None):
+    _check(lib().pps_query(handle, ctypes.byref(v), n, _ptr(slot_in, n, torch.int32, "slot_in"),
+                           ctypes.byref(out), _stream(stream)))
+
+
+def pps_filter(handle, cam: pps_camera, frame: int, v: pps_vertices, n: int, blend: bool,
+               alpha: float, out: pps_output, stream=None):
+    _check(lib().pps_filter(handle, ctypes.byref(cam), frame & 0xFFFFFFFF, ctypes.byref(v), n,
+                            1 if blend else 0, float(alpha), ctypes.byref(out), _stream(stream)))
+
+
+def pps_filter_host(handle, cam: pps_camera, frame: int, v: pps_vertices, n: int, blend: bool,
+                    alpha: float, out: pps_output, stream=None):
+    _check(lib().pps_filter_host(handle, ctypes.byref(cam), frame & 0xFFFFFFFF, ctypes.byref(v),
+                                 n, 1 if blend else 0, float(alpha), ctypes.byref(out),
+                                 _stream(stream)))
+
+
+def pps_keys(handle, v: pps_vertices, n: int, h_out: torch.Tensor, f_out: torch.Tensor,
+             stream=None):
+    _check(lib().pps_keys(handle, ctypes.byref(v), n, _ptr(h_out, n, torch.int32, "h_out"),
+                          _ptr(f_out, n, torch.int32, "f_out"), _stream(stream)))
+
+
+def pps_stats(handle, stream=None) -> dict:
+    s = pps_stats_t()
+    _check(lib().pps_stats(handle, ctypes.byref(s), _stream(stream)))
+    return {k: getattr(s, k) for k, _ in pps_stats_t._fields_}
+
+
+def pps_table_dump(handle, T: int, fixed: bool, stream=None):
+    fp = np.zeros(T, dtype=np.uint32)
+    acc = np.zeros((T, 4), dtype=np.int64 if fixed else np.float32)
+    _check(lib().pps_table_dump(handle, fp.ctypes.data, acc.ctypes.data, _stream(stream)))
+    return fp, acc
+
+
+# ---------------------------------------------------------------- convenience
+def empty_output(n: int, device="cuda", count=True, status=True) -> Dict[str, torch.Tensor]:
+    o = {c: torch.empty(n, dtype=torch.float32, device=device) for c in ("r", "g", "b")}
+    if count:
+        o["count"] = torch.empty(n, dtype=torch.int32, device=device)
+    if status:
+        o["status"] = torch.empty(n, dtype=torch.uint8, device=device)
+    return o
+
+
+class Table:
+    """One filter table (frame table plus optional history) on the current device."""
+
+    def __init__(self, cfg, hist_mode: Optional[int] = None, accum_fixed: Optional[bool] = None,
+                 log2_hist_slots: Optional[int] = None):
+        self.params = make_params(cfg, hist_mode, accum_fixed, log2_hist_slots)
+        self.handle = pps_create(self.params)
+        self.T = 1 << self.params.log2_slots
+        self.fixed = self.params.accum_mode == ACCUM_FIXED
+
+    def close(self):
+        if self.handle:
+            pps_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def filter(self, v, cam, frame, blend=False, alpha=0.2, out=None, stream=None, ids=None,
+               id_base=0, stream_id=0):
+        n = v["px"].numel()
+        out = empty_output(n, v["px"].device) if out is None else out
+        pps_filter(self.handle, camera(cam), frame, make_vertices(v, n, ids, id_base, stream_id),
+                   n, blend, alpha, make_output(out, n), stream)
+        return out
+
+    def build(self, cam, frame, stream=None):
+        pps_build(self.handle, camera(cam), frame, stream)
+
+    def insert(self, v, slot_out=None, stream=None, ids=None, id_base=0, stream_id=0):
+        n = v["px"].numel()
+        pps_insert(self.handle, make_vertices(v, n, ids, id_base, stream_id), n, slot_out, stream)
+
+    def blend(self, alpha, stream=None):
+        pps_blend(self.handle, alpha, stream)
+
+    def query(self, v, slot_in=None, out=None, stream=None, ids=None, id_base=0, stream_id=0):
+        n = v["px"].numel()
+        out = empty_output(n, v["px"].device) if out is None else out
+        pps_query(self.handle, make_vertices(v, n, ids, id_base, stream_id), n, slot_in,
+                  make_output(out, n), stream)
+        return out
+
+    def keys(self, v, stream=None, ids=None, id_base=0, stream_id=0):
+        n = v["px"].numel()
+        h = torch.empty(n, dtype=torch.int32, device=v["px"].device)
+        f = torch.empty(n, dtype=torch.int32, device=v["px"].device)
+        pps_keys(self.handle, make_vertices(v, n, ids, id_base, stream_id), n, h, f, stream)
+        return h, f
+
+    def stats(self, stream=None) -> dict:
+        return pps_stats(self.handle, stream)
+
+    def dump(self, stream=None):
+        return pps_table_dump(self.handle, self.T, self.fixed, stream)

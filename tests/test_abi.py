@@ -1,0 +1,109 @@
+"""The C-ABI library loads, exports every function include/pps.h declares, and
+its host-side argument checks answer without a GPU.  The ctypes layouts of the
+binding are checked against a C program compiled from the header."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+from conftest import ROOT
+
+HEADER = os.path.join(ROOT, "include", "pps.h")
+
+
+def _lib():
+    from paper_1902_05942_gb300 import build, pps
+    build.build()
+    return pps, pps.lib()
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(pps_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary_calls():
+    names = declared_functions()
+    for n in ("pps_build", "pps_insert", "pps_query", "pps_blend", "pps_create", "pps_destroy",
+              "pps_filter", "pps_stats"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol():
+    pps, L = _lib()
+    out = subprocess.run(["nm", "-D", "--defined-only", pps.LIB_PATH], capture_output=True,
+                         text=True, check=True).stdout
+    exported = set(re.findall(r" T (pps_\w+)", out))
+    missing = [n for n in declared_functions() if n not in exported]
+    assert not missing, missing
+    for n in declared_functions():
+        assert n in pps.SIGNATURES, f"binding lacks {n}"
+        getattr(L, n)
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    pps, _ = _lib()
+    prog = tmp_path / "sizes.c"
+    prog.write_text(
+        '#include <stdio.h>\n#include <stddef.h>\n#include "pps.h"\n'
+        "int main(void){printf(\"%zu %zu %zu %zu %zu %zu %zu\\n\", sizeof(pps_params),"
+        " sizeof(pps_camera), sizeof(pps_vertices), sizeof(pps_output), sizeof(pps_stats_t),"
+        " offsetof(pps_params, log2_hist_slots), offsetof(pps_vertices, id_base));return 0;}\n")
+    exe = tmp_path / "sizes"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)],
+                   check=True)
+    got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True,
+                                          check=True).stdout.split()]
+    want = [ctypes.sizeof(pps.pps_params), ctypes.sizeof(pps.pps_camera),
+            ctypes.sizeof(pps.pps_vertices), ctypes.sizeof(pps.pps_output),
+            ctypes.sizeof(pps.pps_stats_t), pps.pps_params.log2_hist_slots.offset,
+            pps.pps_vertices.id_base.offset]
+    assert got == want
+
+
+def _params(pps, **kw):
+    from paper_1902_05942_gb300 import configs
+    cfg = configs.small().filters[0]
+    p = pps.make_params(cfg)
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+@pytest.mark.parametrize("field,value", [("log2_slots", 3), ("log2_slots", 31),
+                                         ("max_probes", 0), ("max_probes", 5000),
+                                         ("voxel_scale", 0.0), ("voxel_scale", float("nan")),
+                                         ("pixel_angle", -1.0), ("lod_min", -126),
+                                         ("lod_max", 127), ("accum_mode", 2), ("hist_mode", 3),
+                                         ("jitter", 2), ("log2_hist_slots", 2)])
+def test_create_rejects_bad_parameters_without_touching_the_gpu(field, value):
+    pps, L = _lib()
+    p = _params(pps, **{field: value})
+    h = ctypes.c_void_p()
+    rc = L.pps_create(ctypes.byref(h), ctypes.byref(p))
+    assert rc == pps.PPS_EINVAL
+    assert h.value is None
+    assert pps.last_error()
+
+
+def test_reserved_fields_must_be_zero():
+    pps, L = _lib()
+    p = _params(pps)
+    p.reserved[1] = 7
+    h = ctypes.c_void_p()
+    assert L.pps_create(ctypes.byref(h), ctypes.byref(p)) == pps.PPS_EINVAL
+    assert "reserved" in pps.last_error()
+
+
+def test_null_arguments_are_rejected():
+    pps, L = _lib()
+    assert L.pps_create(None, None) == pps.PPS_EINVAL
+    assert L.pps_build(None, None, 0, None) == pps.PPS_EINVAL
+    assert L.pps_insert(None, None, 0, None, None) == pps.PPS_EINVAL
+    assert L.pps_query(None, None, 0, None, None, None) == pps.PPS_EINVAL
+    assert L.pps_blend(None, 0.2, None) == pps.PPS_EINVAL
+    assert L.pps_destroy(None) == pps.PPS_OK
+    assert pps.pps_version().startswith("pps-gb300")

@@ -1,0 +1,383 @@
+"""GPU parity: the CUDA library through its C ABI against the CPU oracle.
+
+Bars (per vertex):
+* keys (home hash, fingerprint), cell membership and counts: bit-exact;
+* FP32 accumulation: |gpu - fp64| <= max(1e-5, (n + 1) 2^-24) * |fp64|.  The GPU
+  adds n non-negative FP32 values in some order and divides once; the recursive
+  summation bound for non-negative terms gives a relative error of at most
+  (n - 1) u plus u for the division (u = 2^-24), so 1e-5 holds for n <= 166 and
+  the bound itself above that;
+* fixed-point accumulation: bit-exact;
+* temporal blend: the frame bar plus 8 u per blended frame (FP32 history), or
+  one binary16 rounding step (FP16 history).
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import pps_oracle as O
+from paper_1902_05942_gb300 import configs, pps, scene
+
+pytestmark = pytest.mark.gpu
+
+U = 2.0 ** -24
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1902_05942_gb300 import build
+    build.build()
+    torch.cuda.set_device(0)
+    yield
+
+
+def _small(width=128, height=128, bounces=1, **fkw):
+    w = configs.small()
+    spec = configs.frame_spec(w, 0, 0)
+    spec.view.width, spec.view.height = width, height
+    spec.bounces = bounces
+    cfg = w.filters[0]
+    cfg.pixel_angle = spec.view.pixel_angle()
+    for k, v in fkw.items():
+        setattr(cfg, k, v)
+    return spec, cfg
+
+
+def _gen(spec, frame=0):
+    v = scene.trace_stream(spec, frame, "cpu")
+    return {k: v[k] for k in scene.STREAMS}
+
+
+def _dev(v, n=None):
+    return {k: (v[k][:n] if n is not None else v[k]).to("cuda").contiguous() for k in scene.STREAMS}
+
+
+def _np(v, n=None):
+    return {k: (v[k][:n] if n is not None else v[k]).cpu().numpy() for k in scene.STREAMS}
+
+
+def _oracle(cfg, cam, frame, v_np, ids=None):
+    return O.filter_frame(O.KeyParams(**cfg.oracle_kwargs()), cam, frame, v_np, ids=ids)
+
+
+def _rgb(out):
+    return torch.stack([out[c] for c in "rgb"], 1).cpu().numpy()
+
+
+def _check_values(got, ref64, count, extra=0.0):
+    tol = np.maximum(1e-5, (count + 1) * U)[:, None] + extra
+    rel = np.abs(got.astype(np.float64) - ref64) / np.abs(ref64)
+    bad = rel > tol
+    assert not bad.any(), f"{bad.sum()} values off, max rel {rel.max():.3e}"
+    return rel.max()
+
+
+def _check_frame(out, fr, fixed=False):
+    cnt = out["count"].cpu().numpy().astype(np.int64)
+    st = out["status"].cpu().numpy()
+    assert np.array_equal(cnt, fr.count)
+    assert np.array_equal(st, np.where(fr.count < 4, 1, 0))
+    got = _rgb(out)
+    if fixed:
+        assert np.array_equal(got, fr.mean_fixed)
+    else:
+        _check_values(got, fr.mean64, fr.count)
+
+
+# ------------------------------------------------------------------ keys
+@pytest.mark.parametrize("jitter,nih", [(True, True), (True, False), (False, True)])
+def test_keys_bit_exact(jitter, nih):
+    spec, cfg = _small(jitter=jitter, normal_in_home_hash=nih)
+    v = _gen(spec)
+    n = v["px"].numel() - 5  # ragged tail
+    tab = pps.Table(cfg)
+    tab.build(spec.view.eye, 7)
+    h, f = tab.keys(_dev(v, n))
+    kw = cfg.oracle_kwargs()
+    kw["log2_slots"] = 32  # full 32-bit home hash
+    k = O.vertex_keys(O.KeyParams(**kw), spec.view.eye, 7,
+                      *(v[c][:n].numpy() for c in ("px", "py", "pz", "nx", "ny", "nz")))
+    assert np.array_equal(h.cpu().numpy().view(np.uint32), k.home)
+    assert np.array_equal(f.cpu().numpy().view(np.uint32), k.fp)
+    tab.close()
+
+
+def test_keys_degenerate_inputs():
+    # a vertex at the camera (distance 0), normals along -z and +z, -0.0 components
+    cam = (0.5, 2.0, -3.0)
+    px = np.array([0.5, 0.5, 1.0, -2.0, 3.0], np.float32)
+    py = np.array([2.0, 1.0, 0.0, 0.25, 1e-6], np.float32)
+    pz = np.array([-3.0, -1.0, 0.0, 4.0, -0.0], np.float32)
+    nx = np.array([0.0, 0.0, -0.0, 0.6, 1.0], np.float32)
+    ny = np.array([0.0, 1.0, 0.0, 0.8, 0.0], np.float32)
+    nz = np.array([-1.0, -0.0, 1.0, 0.0, -0.0], np.float32)
+    rgb = np.ones(5, np.float32)
+    v = {k: torch.from_numpy(a) for k, a in zip(scene.STREAMS, (px, py, pz, nx, ny, nz, rgb, rgb, rgb))}
+    _, cfg = _small()
+    tab = pps.Table(cfg)
+    tab.build(cam, 3)
+    h, f = tab.keys(_dev(v))
+    kw = cfg.oracle_kwargs()
+    kw["log2_slots"] = 32
+    k = O.vertex_keys(O.KeyParams(**kw), cam, 3, px, py, pz, nx, ny, nz)
+    assert np.array_equal(h.cpu().numpy().view(np.uint32), k.home)
+    assert np.array_equal(f.cpu().numpy().view(np.uint32), k.fp)
+    tab.close()
+
+
+# ------------------------------------------------------------------ one frame
+@pytest.mark.parametrize("fixed", [False, True])
+def test_fused_filter_matches_oracle(fixed):
+    spec, cfg = _small(width=160, height=120, bounces=3, accum_fixed=fixed)
+    v = _gen(spec, 2)
+    n = v["px"].numel() - 3
+    tab = pps.Table(cfg)
+    out = tab.filter(_dev(v, n), spec.view.eye, 2)
+    fr = _oracle(cfg, spec.view.eye, 2, _np(v, n))
+    _check_frame(out, fr, fixed)
+    st = tab.stats()
+    assert st["frame_cells"] == fr.tuples.shape[0]
+    assert st["overflow_vertices"] == 0 and st["device_error"] == 0
+    assert st["occupied_slots"] == 0  # the frame table is left empty
+    tab.close()
+
+
+@pytest.mark.parametrize("fixed", [False, True])
+def test_split_path_matches_oracle_and_audit(fixed):
+    spec, cfg = _small(width=160, height=120, bounces=2, accum_fixed=fixed)
+    v = _gen(spec, 1)
+    n = v["px"].numel()
+    d = _dev(v)
+    tab = pps.Table(cfg)
+    tab.build(spec.view.eye, 1)
+    slots = torch.empty(n, dtype=torch.int32, device="cuda")
+    half = n // 2  # two inserts into one frame
+    tab.insert({k: d[k][:half] for k in d}, slots[:half])
+    tab.insert({k: d[k][half:] for k in d}, slots[half:], id_base=half)
+    out1 = tab.query(d, slots)
+    out2 = tab.query(d)  # re-probing lookup
+    fr = _oracle(cfg, spec.view.eye, 1, _np(v))
+    _check_frame(out1, fr, fixed)
+    _check_frame(out2, fr, fixed)
+    if fixed:
+        assert all(torch.equal(out1[c], out2[c]) for c in "rgb")
+    # table audit: slots hold the oracle's fingerprints inside the probe window
+    fp, acc = tab.dump()
+    s = slots.cpu().numpy().view(np.uint32).astype(np.int64)
+    T = 1 << cfg.log2_slots
+    assert np.array_equal(fp[s], fr.keys.fp)
+    dist = (s - fr.keys.home.astype(np.int64)) % T
+    assert dist.max() < cfg.max_probes
+    assert set(fp[fp != 0].tolist()) == set(fr.cell_fp.tolist())
+    cnt = acc[s, 3].astype(np.int64)
+    assert np.array_equal(cnt, fr.count)
+    st = tab.stats()
+    assert st["occupied_slots"] == fr.tuples.shape[0] == st["frame_cells"]
+    tab.build(spec.view.eye, 2)  # empties the frame through the dirty list
+    fp2, acc2 = tab.dump()
+    assert not fp2.any() and not acc2.any()
+    tab.close()
+
+
+def test_constant_field_and_single_cell():
+    spec, cfg = _small(width=96, height=96, bounces=2)
+    v = _gen(spec)
+    for c in "rgb":
+        v[c] = torch.full_like(v[c], 0.75)
+    tab = pps.Table(cfg)
+    out = tab.filter(_dev(v), spec.view.eye, 0)
+    assert all(torch.all(out[c] == 0.75) for c in "rgb")
+    tab.close()
+    # one voxel covering everything (constant level 2^10, no jitter, one normal)
+    rng = np.random.default_rng(4)
+    N = 20000
+    p = rng.uniform(0, 900, (N, 3)).astype(np.float32)
+    rgb = rng.lognormal(-1, 1.5, (N, 3)).astype(np.float32)
+    arrs = [p[:, 0], p[:, 1], p[:, 2], np.zeros(N, np.float32), np.ones(N, np.float32),
+            np.zeros(N, np.float32), rgb[:, 0], rgb[:, 1], rgb[:, 2]]
+    vv = {k: torch.from_numpy(np.ascontiguousarray(a)) for k, a in zip(scene.STREAMS, arrs)}
+    _, cfg2 = _small(jitter=False, lod_min=10, lod_max=10, accum_fixed=True)
+    tab = pps.Table(cfg2)
+    out = tab.filter(_dev(vv), (0, 3, -12), 0)
+    fr = _oracle(cfg2, (0, 3, -12), 0, {k: vv[k].numpy() for k in scene.STREAMS})
+    assert fr.tuples.shape[0] == 1
+    assert torch.all(out["count"] == N)
+    assert np.array_equal(_rgb(out), fr.mean_fixed)
+    tab.close()
+
+
+def test_zero_and_one_vertex():
+    spec, cfg = _small()
+    v = _gen(spec)
+    tab = pps.Table(cfg)
+    out = tab.filter(_dev(v, 1), spec.view.eye, 0)
+    assert out["count"].item() == 1
+    assert np.array_equal(_rgb(out)[0], np.array([v[c][0].item() for c in "rgb"], np.float32))
+    e = {k: torch.empty(0, device="cuda") for k in scene.STREAMS}
+    tab.filter(e, spec.view.eye, 1)
+    assert tab.stats()["vertices"] == 0
+    tab.close()
+
+
+def test_overflow_all_or_none_and_window_audit():
+    spec, cfg = _small(width=64, height=48, bounces=2, log2_slots=7, max_probes=4)
+    v = _gen(spec)
+    n = v["px"].numel()
+    d = _dev(v)
+    fr = _oracle(cfg, spec.view.eye, 0, _np(v))
+    assert fr.tuples.shape[0] > 128  # more cells than slots: overflow is certain
+    tab = pps.Table(cfg)
+    tab.build(spec.view.eye, 0)
+    slots = torch.empty(n, dtype=torch.int32, device="cuda")
+    tab.insert(d, slots)
+    out = tab.query(d, slots)
+    fp, _ = tab.dump()
+    st = out["status"].cpu().numpy()
+    cnt = out["count"].cpu().numpy().astype(np.int64)
+    ovf = st == 2
+    assert ovf.any() and (~ovf).any()
+    # all vertices of a cell share the outcome
+    for c in np.unique(fr.cell[ovf]):
+        assert np.all(ovf[fr.cell == c])
+    # an overflowed key's window is full of other fingerprints
+    for j in np.nonzero(ovf)[0][:200]:
+        assert O.overflow_window_full(fp, int(fr.keys.home[j]), int(fr.keys.fp[j]), 4)
+    own = np.column_stack([v[c].numpy() for c in "rgb"])
+    assert np.array_equal(_rgb(out)[ovf], own[ovf])
+    assert np.all(cnt[ovf] == 0)
+    assert np.array_equal(cnt[~ovf], fr.count[~ovf])
+    _check_values(_rgb(out)[~ovf], fr.mean64[~ovf], fr.count[~ovf])
+    assert tab.stats()["overflow_vertices"] == ovf.sum()
+    tab.close()
+    # the fused path shows the same all-or-none behaviour
+    tab = pps.Table(cfg)
+    out = tab.filter(d, spec.view.eye, 0)
+    st = out["status"].cpu().numpy()
+    ovf = st == 2
+    for c in np.unique(fr.cell[ovf]):
+        assert np.all(ovf[fr.cell == c])
+    assert np.array_equal(out["count"].cpu().numpy().astype(np.int64)[~ovf], fr.count[~ovf])
+    tab.close()
+
+
+# ------------------------------------------------------------------ temporal
+@pytest.mark.parametrize("hist_mode,alpha,fused", [(1, 0.2, True), (1, -1.0, True),
+                                                   (1, 0.2, False), (2, 0.2, True),
+                                                   (2, -1.0, False)])
+def test_temporal_blend_matches_oracle(hist_mode, alpha, fused):
+    w = configs.small()
+    frames = 4
+    _, cfg = _small(width=128, height=96, bounces=2, hist_mode=hist_mode, log2_hist_slots=19)
+    tab = pps.Table(cfg)
+    hist = O.History.empty()
+    for f in range(frames):
+        spec = configs.frame_spec(w, 0, f)
+        spec.view = scene.View(128, 96, eye=(0.05 * f, 3.0, -12.0), target=(0.05 * f, 0.5, 0.0))
+        spec.bounces = 2
+        v = _gen(spec, f)
+        d = _dev(v)
+        if fused:
+            out = tab.filter(d, spec.view.eye, f, blend=True, alpha=alpha)
+        else:
+            tab.build(spec.view.eye, f)
+            slots = torch.empty(d["px"].numel(), dtype=torch.int32, device="cuda")
+            tab.insert(d, slots)
+            tab.blend(alpha)
+            out = tab.query(d, slots)
+        fr = _oracle(cfg, spec.view.eye, f, _np(v))
+        hist, val, cnt = O.blend(hist, fr, alpha, fp16=hist_mode == 2,
+                                 n_cap=65535 if hist_mode == 2 else None)
+        assert np.array_equal(out["count"].cpu().numpy().astype(np.int64), cnt)
+        got = _rgb(out).astype(np.float64)
+        rel = np.abs(got - val) / np.abs(val)
+        if hist_mode == 1:
+            tol = np.maximum(1e-5, (fr.count + 1) * U)[:, None] + 8 * U * (f + 1)
+        else:
+            tol = 2.0 ** -10 + 1e-5
+        assert np.all(rel <= tol), f"frame {f}: max rel {rel.max():.3e}"
+    st = tab.stats()
+    assert st["hist_overflow"] == 0
+    assert st["hist_occupied"] == hist.tuples.shape[0]
+    tab.close()
+
+
+# ------------------------------------------------------------------ host path, errors
+def test_filter_host_matches_device_path():
+    spec, cfg = _small(width=100, height=80, bounces=2, accum_fixed=True)
+    v = _gen(spec)
+    n = v["px"].numel()
+    tab = pps.Table(cfg)
+    out_d = tab.filter(_dev(v), spec.view.eye, 5)
+    torch.cuda.synchronize()
+    host = {k: v[k].contiguous().pin_memory() for k in scene.STREAMS}
+    oh = pps.empty_output(n, "cpu")
+    pps.pps_filter_host(tab.handle, pps.camera(spec.view.eye), 5,
+                        pps.make_vertices(host, n, device=False), n, False, 0.0,
+                        pps.make_output(oh, n, device=False))
+    for c in ("r", "g", "b", "count", "status"):
+        assert torch.equal(oh[c], out_d[c].cpu())
+    tab.close()
+
+
+def test_call_order_and_argument_errors():
+    spec, cfg = _small()
+    v = _dev(_gen(spec))
+    tab = pps.Table(cfg)
+    with pytest.raises(pps.PPSError) as e:
+        tab.insert(v)
+    assert e.value.code == pps.PPS_ESTATE
+    with pytest.raises(pps.PPSError) as e:
+        tab.query(v)
+    assert e.value.code == pps.PPS_ESTATE
+    tab.build(spec.view.eye, 0)
+    with pytest.raises(pps.PPSError) as e:
+        tab.blend(0.2)  # no history in this table
+    assert e.value.code == pps.PPS_EINVAL
+    tab.close()
+
+
+# ------------------------------------------------------------------ full size
+def test_hd_frame_full_size_in_bench_configuration():
+    """The HD workload (5.06 M vertices, T = 2^23, FP32 history 2^25, alpha 0.2)
+    through the fused launch the benchmark times: two consecutive frames, every
+    vertex checked against the oracle (counts exact, values within the bar)."""
+    w = configs.hd()
+    cfg = w.filters[0]
+    tab = pps.Table(cfg)
+    hist = O.History.empty()
+    for f in range(2):
+        spec = configs.frame_spec(w, 0, f)
+        v = scene.trace_stream(spec, f, "cuda")
+        d = {k: v[k] for k in scene.STREAMS}
+        out = tab.filter(d, spec.view.eye, f, blend=True, alpha=cfg.alpha)
+        fr = _oracle(cfg, spec.view.eye, f, _np(d))
+        hist, val, cnt = O.blend(hist, fr, cfg.alpha)
+        assert np.array_equal(out["count"].cpu().numpy().astype(np.int64), cnt)
+        got = _rgb(out).astype(np.float64)
+        rel = np.abs(got - val) / np.abs(val)
+        tol = np.maximum(1e-5, (fr.count + 1) * U)[:, None] + 8 * U * (f + 1)
+        assert np.all(rel <= tol), f"frame {f}: max rel {rel.max():.3e}"
+        st = tab.stats()
+        assert st["overflow_vertices"] == 0 and st["hist_overflow"] == 0
+        assert st["frame_cells"] == fr.tuples.shape[0]
+    tab.close()
+
+
+def test_global_stash_path_matches_oracle():
+    """More vertices than the on-chip stash holds: the slot indices live in the
+    table's scratch buffer instead; results must not change."""
+    g = torch.Generator(device="cuda").manual_seed(9)
+    N = 12_000_000
+    p = (torch.rand((N, 3), generator=g, device="cuda") * 40 - 20)
+    nn = torch.nn.functional.normalize(torch.randn((N, 3), generator=g, device="cuda"), dim=1)
+    rgb = torch.exp(-1 + 1.5 * torch.randn((N, 3), generator=g, device="cuda"))
+    d = {k: t.contiguous() for k, t in zip(scene.STREAMS, [p[:, 0], p[:, 1], p[:, 2], nn[:, 0],
+                                                         nn[:, 1], nn[:, 2], rgb[:, 0], rgb[:, 1],
+                                                         rgb[:, 2]])}
+    _, cfg = _small(log2_slots=25, voxel_scale=64.0, accum_fixed=True)
+    tab = pps.Table(cfg)
+    out = tab.filter(d, (0, 3, -12), 0)
+    fr = _oracle(cfg, (0, 3, -12), 0, _np(d))
+    assert np.array_equal(out["count"].cpu().numpy().astype(np.int64), fr.count)
+    assert np.array_equal(_rgb(out), fr.mean_fixed)
+    tab.close()
