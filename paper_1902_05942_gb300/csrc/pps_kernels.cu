@@ -428,43 +428,58 @@ cudaError_t launch_count_occupied(const uint32_t* fp, uint32_t T, unsigned long 
   return cudaGetLastError();
 }
 
+// Largest dynamic shared memory a k_fused CTA may request: the opt-in limit
+// per block minus the kernel's static shared memory.
+template <bool TEMPORAL>
+static cudaError_t fused_dyn_smem_limit(size_t* limit) {
+  static size_t cached = 0;
+  if (!cached) {
+    int dev = 0, maxopt = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&maxopt, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa;
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_fused<TEMPORAL>);
+    if (e != cudaSuccess) return e;
+    const size_t lim = static_cast<size_t>(maxopt) - fa.sharedSizeBytes;
+    e = cudaFuncSetAttribute(k_fused<TEMPORAL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(lim));
+    if (e != cudaSuccess) return e;
+    cached = lim;
+  }
+  *limit = cached;
+  return cudaSuccess;
+}
+
 template <bool TEMPORAL>
 static cudaError_t fused_blocks_per_sm(size_t smem, int* nb) {
-  static bool attr_set = false;
-  if (!attr_set) {
-    int dev = 0, maxopt = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&maxopt, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    cudaError_t e =
-        cudaFuncSetAttribute(k_fused<TEMPORAL>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxopt);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
+  size_t lim = 0;
+  cudaError_t e = fused_dyn_smem_limit<TEMPORAL>(&lim);
+  if (e != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, k_fused<TEMPORAL>, kFusedBlock, smem);
 }
 
 cudaError_t plan_fused(size_t n, bool temporal, FusedPlan* plan) {
   const int sms = sm_count();
-  int dev = 0, maxopt = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&maxopt, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  size_t maxdyn = 0;
+  cudaError_t e = temporal ? fused_dyn_smem_limit<true>(&maxdyn) : fused_dyn_smem_limit<false>(&maxdyn);
+  if (e != cudaSuccess) return e;
   int b0 = 0;
-  cudaError_t e = temporal ? fused_blocks_per_sm<true>(0, &b0) : fused_blocks_per_sm<false>(0, &b0);
+  e = temporal ? fused_blocks_per_sm<true>(0, &b0) : fused_blocks_per_sm<false>(0, &b0);
   if (e != cudaSuccess) return e;
   if (b0 < 1) return cudaErrorInvalidConfiguration;
   for (int b = b0; b >= 1; --b) {
     const int grid = sms * b;
     size_t chunk = (n + grid - 1) / grid;
-    chunk = (chunk + 3) & ~static_cast<size_t>(3);
+    chunk = std::max<size_t>((chunk + 3) & ~static_cast<size_t>(3), 4);
     const size_t smem = chunk * sizeof(uint32_t);
-    if (smem > static_cast<size_t>(maxopt)) continue;
+    if (smem > maxdyn) continue;
     int nb = 0;
     e = temporal ? fused_blocks_per_sm<true>(smem, &nb) : fused_blocks_per_sm<false>(smem, &nb);
     if (e != cudaSuccess) return e;
     if (nb >= b) {
       plan->grid = grid;
       plan->block = kFusedBlock;
-      plan->chunk = std::max<size_t>(chunk, 4);
+      plan->chunk = chunk;
       plan->smem = smem;
       plan->global_stash = false;
       return cudaSuccess;
@@ -473,10 +488,10 @@ cudaError_t plan_fused(size_t n, bool temporal, FusedPlan* plan) {
   // The stash does not fit on chip: keep it in a global scratch buffer.
   const int grid = sms * b0;
   size_t chunk = (n + grid - 1) / grid;
-  chunk = (chunk + 3) & ~static_cast<size_t>(3);
+  chunk = std::max<size_t>((chunk + 3) & ~static_cast<size_t>(3), 4);
   plan->grid = grid;
   plan->block = kFusedBlock;
-  plan->chunk = std::max<size_t>(chunk, 4);
+  plan->chunk = chunk;
   plan->smem = 0;
   plan->global_stash = true;
   return cudaSuccess;
