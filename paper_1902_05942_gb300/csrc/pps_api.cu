@@ -6,6 +6,7 @@
 // kernels of pps_kernels.cu.
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 
@@ -148,13 +149,8 @@ void set_camera(pps_table* t, const pps_camera* cam, uint32_t frame) {
 }
 
 void free_all(pps_table* t) {
-  cudaFree(t->dev.fp);
-  cudaFree(t->dev.acc);
-  cudaFree(t->dev.acc64);
-  cudaFree(t->dev.hist);
-  cudaFree(t->dev.hist16);
-  cudaFree(t->dev.hfp);
-  cudaFree(t->dev.hslot);
+  cudaFree(t->dev.cells);
+  cudaFree(t->dev.hcells);
   cudaFree(t->dev.dirty);
   cudaFree(t->dev.ctrl);
   cudaFree(t->gstash);
@@ -193,21 +189,14 @@ int pps_create(pps_table** out, const pps_params* p) {
     if (e == cudaSuccess) e = cudaMemset(*ptr, 0, bytes);
     return e;
   };
-  cudaError_t e = alloc(reinterpret_cast<void**>(&t->dev.fp), T * sizeof(uint32_t));
-  if (e == cudaSuccess) {
-    if (p->accum_mode == PPS_ACCUM_FP32)
-      e = alloc(reinterpret_cast<void**>(&t->dev.acc), T * sizeof(float4));
-    else
-      e = alloc(reinterpret_cast<void**>(&t->dev.acc64), T * sizeof(pps::AccFixed));
-  }
-  if (e == cudaSuccess && p->hist_mode != PPS_HIST_NONE) {
-    e = alloc(reinterpret_cast<void**>(&t->dev.hfp), Th * sizeof(uint32_t));
-    if (e == cudaSuccess) e = alloc(reinterpret_cast<void**>(&t->dev.hslot), T * sizeof(uint32_t));
-  }
-  if (e == cudaSuccess && p->hist_mode == PPS_HIST_FP32)
-    e = alloc(reinterpret_cast<void**>(&t->dev.hist), Th * sizeof(float4));
-  if (e == cudaSuccess && p->hist_mode == PPS_HIST_FP16)
-    e = alloc(reinterpret_cast<void**>(&t->dev.hist16), Th * sizeof(uint2));
+  const bool fixed = p->accum_mode == PPS_ACCUM_FIXED;
+  t->dev.stride = fixed ? 64u : 32u;
+  t->dev.fp_off = fixed ? 32u : 16u;
+  t->dev.hstride = p->hist_mode == PPS_HIST_FP16 ? 16u : 32u;
+  t->dev.hfp_off = p->hist_mode == PPS_HIST_FP16 ? 8u : 16u;
+  cudaError_t e = alloc(reinterpret_cast<void**>(&t->dev.cells), T * t->dev.stride);
+  if (e == cudaSuccess && p->hist_mode != PPS_HIST_NONE)
+    e = alloc(reinterpret_cast<void**>(&t->dev.hcells), Th * t->dev.hstride);
   if (e == cudaSuccess) e = alloc(reinterpret_cast<void**>(&t->dev.dirty), T * sizeof(uint32_t));
   if (e == cudaSuccess) e = alloc(reinterpret_cast<void**>(&t->dev.ctrl), sizeof(pps::Ctrl));
   if (e == cudaSuccess) e = alloc(reinterpret_cast<void**>(&t->scratch_u64), 2 * sizeof(unsigned long long));
@@ -398,8 +387,11 @@ int pps_stats(pps_table* t, pps_stats_t* out, void* stream) {
   if (!out) return fail(PPS_EINVAL, "out is NULL");
   const cudaStream_t st = static_cast<cudaStream_t>(stream);
   PPS_CUDA(cudaMemsetAsync(t->scratch_u64, 0, 2 * sizeof(unsigned long long), st));
-  PPS_CUDA(pps::launch_count_occupied(t->dev.fp, t->T, t->scratch_u64, st));
-  if (t->dev.hfp) PPS_CUDA(pps::launch_count_occupied(t->dev.hfp, t->Th, t->scratch_u64 + 1, st));
+  PPS_CUDA(pps::launch_count_occupied(t->dev.cells, t->dev.stride, t->dev.fp_off, t->T,
+                                      t->scratch_u64, st));
+  if (t->dev.hcells)
+    PPS_CUDA(pps::launch_count_occupied(t->dev.hcells, t->dev.hstride, t->dev.hfp_off, t->Th,
+                                        t->scratch_u64 + 1, st));
   pps::Ctrl c;
   unsigned long long occ[2] = {0, 0};
   PPS_CUDA(cudaMemcpyAsync(&c, t->dev.ctrl, sizeof(c), cudaMemcpyDeviceToHost, st));
@@ -429,15 +421,23 @@ int pps_table_dump(pps_table* t, uint32_t* fp_host, void* acc_host, void* stream
   if (int rc = check_table(t)) return rc;
   if (!fp_host) return fail(PPS_EINVAL, "fp_host is NULL");
   const cudaStream_t st = static_cast<cudaStream_t>(stream);
-  PPS_CUDA(cudaMemcpyAsync(fp_host, t->dev.fp, t->T * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
-  if (acc_host) {
-    if (t->dev.fixed)
-      PPS_CUDA(cudaMemcpyAsync(acc_host, t->dev.acc64, t->T * sizeof(pps::AccFixed),
-                               cudaMemcpyDeviceToHost, st));
-    else
-      PPS_CUDA(cudaMemcpyAsync(acc_host, t->dev.acc, t->T * sizeof(float4), cudaMemcpyDeviceToHost, st));
+  const size_t bytes = static_cast<size_t>(t->T) * t->dev.stride;
+  unsigned char* raw = static_cast<unsigned char*>(std::malloc(bytes));
+  if (!raw) return fail(PPS_ENOMEM, "pps_table_dump: host buffer");
+  cudaError_t e = cudaMemcpyAsync(raw, t->dev.cells, bytes, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    std::free(raw);
+    return cuda_fail("pps_table_dump", e);
   }
-  PPS_CUDA(cudaStreamSynchronize(st));
+  // de-interleave the cells: fingerprint array and 4-word accumulator array
+  const size_t acc_bytes = t->dev.fixed ? 32 : 16;
+  for (size_t i = 0; i < t->T; ++i) {
+    const unsigned char* c = raw + i * t->dev.stride;
+    std::memcpy(fp_host + i, c + t->dev.fp_off, sizeof(uint32_t));
+    if (acc_host) std::memcpy(static_cast<unsigned char*>(acc_host) + i * acc_bytes, c, acc_bytes);
+  }
+  std::free(raw);
   return PPS_OK;
 }
 

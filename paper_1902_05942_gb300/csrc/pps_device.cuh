@@ -55,31 +55,34 @@ enum : unsigned int {
   kErrBadSlot = 2u,
 };
 
-// Fixed-point accumulator of one cell: sums of round(v * 2^24) and the count.
-struct __align__(32) AccFixed {
-  long long r, g, b;
-  unsigned long long n;
-};
-
-// The frame table (fp, acc) is emptied every frame.  Temporal state lives in a
-// separate history table (hfp, hist / hist16) whose fingerprints persist across
-// frames; the owner of a frame cell links it to its history cell (hslot).
+// Table layout: one cell is one 32-byte L2 sector (64 bytes in fixed mode), so
+// probing, accumulation, the history link, the lookup and the clear of a cell
+// all touch the same sector.
+//
+//   frame cell, FP32 mode (32 B):  [0,16) {sum r, sum g, sum b, count} FP32
+//                                  [16,20) fingerprint   [20,24) history cell
+//   frame cell, fixed mode (64 B): [0,32) {sum r, sum g, sum b, count} int64
+//                                  [32,36) fingerprint   [36,40) history cell
+//   history cell, FP32 (32 B):     [0,16) {c r, c g, c b, N}  [16,20) fingerprint
+//   history cell, FP16 (16 B):     [0,8) {half r, half g, half b, uint16 N}
+//                                  [8,12) fingerprint
+// After the blend, the first 16 bytes of a frame cell hold the blended value
+// {c r, c g, c b, N} for the lookups of the frame (both modes).
 struct TableDev {
-  uint32_t* fp;       // [T] fingerprints, 0 = empty
-  float4* acc;        // [T] FP32 {sum r, sum g, sum b, count} (FP32 mode)
-  AccFixed* acc64;    // [T] fixed-point accumulators (fixed mode)
-  uint32_t* dirty;    // [T] cells claimed this frame (split path)
-  uint32_t* hslot;    // [T] history cell of each claimed frame cell
-  uint32_t* hfp;      // [Th] history fingerprints
-  float4* hist;       // [Th] FP32 history {c r, c g, c b, N bits} (hist FP32)
-  uint2* hist16;      // [Th] FP16 history {half2(r,g), half b | u16 N << 16}
+  unsigned char* cells;   // [T] frame cells
+  unsigned char* hcells;  // [Th] history cells (temporal tables)
+  uint32_t* dirty;        // [T] cells claimed this frame (split path)
   Ctrl* ctrl;
-  uint32_t mask;      // T - 1
-  uint32_t hmask;     // Th - 1
+  uint32_t stride;        // bytes per frame cell: 32 or 64
+  uint32_t fp_off;        // fingerprint offset in a frame cell: 16 or 32
+  uint32_t hstride;       // bytes per history cell: 32 or 16
+  uint32_t hfp_off;       // fingerprint offset in a history cell: 16 or 8
+  uint32_t mask;          // T - 1
+  uint32_t hmask;         // Th - 1
   uint32_t max_probes;
   uint32_t lowcount;
-  int fixed;          // accumulation mode
-  int hist_mode;      // 0 none, 1 FP32, 2 FP16
+  int fixed;              // accumulation mode
+  int hist_mode;          // 0 none, 1 FP32, 2 FP16
 };
 
 struct VertexPtrs {
@@ -226,89 +229,95 @@ __device__ __forceinline__ Key vertex_key(const KeyConst& kc, float px, float py
 }
 
 // ---------------------------------------------------------------- memory helpers
-__device__ __forceinline__ uint32_t ld_relaxed(const uint32_t* p) {
-  uint32_t v;
-  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-
-__device__ __forceinline__ void red_add_v4(float4* p, float a, float b, float c, float d) {
+__device__ __forceinline__ void red_add_v4(float* p, float a, float b, float c, float d) {
   asm volatile("red.relaxed.gpu.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a),
                "f"(b), "f"(c), "f"(d)
                : "memory");
-}
-
-__device__ __forceinline__ float4 atom_add_v4(float4* p, float a, float b, float c, float d) {
-  float4 o;
-  asm volatile("atom.relaxed.gpu.global.add.v4.f32 {%0, %1, %2, %3}, [%4], {%5, %6, %7, %8};"
-               : "=f"(o.x), "=f"(o.y), "=f"(o.z), "=f"(o.w)
-               : "l"(p), "f"(a), "f"(b), "f"(c), "f"(d)
-               : "memory");
-  return o;
 }
 
 __device__ __forceinline__ long long to_fixed(float v) {
   return __float2ll_rn(__fmul_rn(v, 16777216.0f));  // round(v * 2^24), exact product
 }
 
-// Linear probing on the fingerprint word (Sec. 3.2): a slot holding f is a hit,
-// an empty slot is claimed with one compare-and-swap, anything else is skipped.
-// Fingerprints are only ever published, never moved, so a key that exists in
-// the window is found before any empty slot.  Returns kOverflowSlot after P
-// steps.  `claimed` is set when this call published f.
-__device__ __forceinline__ uint32_t probe_insert(uint32_t* fp, uint32_t mask, uint32_t P,
-                                                 uint32_t home, uint32_t f, bool& claimed) {
+__device__ __forceinline__ unsigned char* frame_cell(const TableDev& t, uint32_t s) {
+  return t.cells + static_cast<size_t>(s) * t.stride;
+}
+__device__ __forceinline__ uint32_t* frame_fp(const TableDev& t, uint32_t s) {
+  return reinterpret_cast<uint32_t*>(frame_cell(t, s) + t.fp_off);
+}
+__device__ __forceinline__ uint32_t* frame_hslot(const TableDev& t, uint32_t s) {
+  return frame_fp(t, s) + 1;
+}
+__device__ __forceinline__ float4* frame_value(const TableDev& t, uint32_t s) {
+  return reinterpret_cast<float4*>(frame_cell(t, s));
+}
+__device__ __forceinline__ unsigned char* hist_cell(const TableDev& t, uint32_t h) {
+  return t.hcells + static_cast<size_t>(h) * t.hstride;
+}
+__device__ __forceinline__ uint32_t* hist_fp(const TableDev& t, uint32_t h) {
+  return reinterpret_cast<uint32_t*>(hist_cell(t, h) + t.hfp_off);
+}
+
+// Linear probing on the fingerprint word (Sec. 3.2): one compare-and-swap per
+// step publishes f into an empty cell or reports the cell's key; a cell holding
+// f is a hit, any other key moves the probe on.  Fingerprints are published,
+// never moved, within a frame, so a key present in the window is met before any
+// empty cell.  The first step (p = 0) is issued by the caller for several
+// vertices at once; this continues from step p0.  kOverflowSlot after P steps.
+struct ProbeTable {
+  unsigned char* base;
+  uint32_t stride, fp_off, mask, P;
+};
+
+__device__ __forceinline__ uint32_t* probe_fp(const ProbeTable& pt, uint32_t s) {
+  return reinterpret_cast<uint32_t*>(pt.base + static_cast<size_t>(s) * pt.stride + pt.fp_off);
+}
+
+__device__ __forceinline__ uint32_t probe_insert_from(const ProbeTable& pt, uint32_t home,
+                                                      uint32_t f, uint32_t p0, bool& claimed) {
   claimed = false;
-  for (uint32_t p = 0; p < P; ++p) {
-    const uint32_t s = (home + p) & mask;
-    const uint32_t cur = ld_relaxed(fp + s);
-    if (cur == f) return s;
-    if (cur == 0u) {
-      const uint32_t old = atomicCAS(fp + s, 0u, f);
-      if (old == 0u) {
-        claimed = true;
-        return s;
-      }
-      if (old == f) return s;
+  for (uint32_t p = p0; p < pt.P; ++p) {
+    const uint32_t s = (home + p) & pt.mask;
+    const uint32_t old = atomicCAS(probe_fp(pt, s), 0u, f);
+    if (old == 0u) {
+      claimed = true;
+      return s;
     }
+    if (old == f) return s;
   }
   return kOverflowSlot;
 }
 
 // Read-only probe (query without a stored slot index).
-__device__ __forceinline__ uint32_t probe_find(const uint32_t* fp, uint32_t mask, uint32_t P,
-                                               uint32_t home, uint32_t f) {
-  for (uint32_t p = 0; p < P; ++p) {
-    const uint32_t s = (home + p) & mask;
-    const uint32_t cur = __ldcg(fp + s);
+__device__ __forceinline__ uint32_t probe_find(const TableDev& t, uint32_t home, uint32_t f) {
+  for (uint32_t p = 0; p < t.max_probes; ++p) {
+    const uint32_t s = (home + p) & t.mask;
+    const uint32_t cur = __ldcg(frame_fp(t, s));
     if (cur == f) return s;
     if (cur == 0u) return kOverflowSlot;
   }
   return kOverflowSlot;
 }
 
-// Accumulate one contribution (or a group of `cnt` combined ones) into cell s.
+__device__ __forceinline__ ProbeTable frame_probe(const TableDev& t) {
+  return ProbeTable{t.cells, t.stride, t.fp_off, t.mask, t.max_probes};
+}
+__device__ __forceinline__ ProbeTable hist_probe(const TableDev& t) {
+  return ProbeTable{t.hcells, t.hstride, t.hfp_off, t.hmask, t.max_probes};
+}
+
+// Accumulate a group of `cnt` contributions (sums r, g, b) into cell s.
 __device__ __forceinline__ void accumulate(const TableDev& t, uint32_t s, float r, float g, float b,
                                            long long fr, long long fg, long long fb, uint32_t cnt) {
   if (!t.fixed) {
-    red_add_v4(t.acc + s, r, g, b, static_cast<float>(cnt));
+    red_add_v4(reinterpret_cast<float*>(frame_cell(t, s)), r, g, b, static_cast<float>(cnt));
     return;
   }
-  AccFixed* a = t.acc64 + s;
-  atomicAdd(reinterpret_cast<unsigned long long*>(&a->r), static_cast<unsigned long long>(fr));
-  atomicAdd(reinterpret_cast<unsigned long long*>(&a->g), static_cast<unsigned long long>(fg));
-  atomicAdd(reinterpret_cast<unsigned long long*>(&a->b), static_cast<unsigned long long>(fb));
-  atomicAdd(&a->n, static_cast<unsigned long long>(cnt));
-}
-
-// The owner (claimer) of frame cell s finds or claims the key's history cell
-// and records it in hslot[s] (kOverflowSlot when the history window is full).
-__device__ __forceinline__ void link_history(const TableDev& t, uint32_t s, uint32_t h1, uint32_t f,
-                                             unsigned long long& n_hovf) {
-  bool claimed;
-  const uint32_t hs = probe_insert(t.hfp, t.hmask, t.max_probes, h1 & t.hmask, f, claimed);
-  n_hovf += hs == kOverflowSlot ? 1ull : 0ull;
-  __stcg(t.hslot + s, hs);
+  unsigned long long* a = reinterpret_cast<unsigned long long*>(frame_cell(t, s));
+  atomicAdd(a + 0, static_cast<unsigned long long>(fr));
+  atomicAdd(a + 1, static_cast<unsigned long long>(fg));
+  atomicAdd(a + 2, static_cast<unsigned long long>(fb));
+  atomicAdd(a + 3, static_cast<unsigned long long>(cnt));
 }
 
 // Cell average of this frame: sum / count, one FP32 round-to-nearest division
@@ -318,18 +327,36 @@ struct CellMean {
   uint32_t n;
 };
 
-__device__ __forceinline__ CellMean cell_mean(const TableDev& t, uint32_t s) {
+// The raw accumulator of a cell as loaded from memory (both modes).
+struct AccRaw {
+  float4 lo;  // FP32 sums, or int64 sums r, g as bits (fixed)
+  float4 hi;  // fixed mode: int64 sum b and count as bits
+};
+
+__device__ __forceinline__ AccRaw load_acc(const TableDev& t, uint32_t s) {
+  AccRaw a;
+  const float4* p = frame_value(t, s);
+  a.lo = __ldcg(p);
+  a.hi = t.fixed ? __ldcg(p + 1) : make_float4(0.f, 0.f, 0.f, 0.f);
+  return a;
+}
+
+__device__ __forceinline__ long long bits64(float x, float y) {
+  return static_cast<long long>((static_cast<unsigned long long>(__float_as_uint(y)) << 32) |
+                                __float_as_uint(x));
+}
+
+__device__ __forceinline__ CellMean mean_of(const TableDev& t, const AccRaw& a) {
   CellMean m;
   if (!t.fixed) {
-    const float4 a = __ldcg(t.acc + s);
-    m.r = __fdiv_rn(a.x, a.w);
-    m.g = __fdiv_rn(a.y, a.w);
-    m.b = __fdiv_rn(a.z, a.w);
-    m.n = static_cast<uint32_t>(a.w);
+    m.r = __fdiv_rn(a.lo.x, a.lo.w);
+    m.g = __fdiv_rn(a.lo.y, a.lo.w);
+    m.b = __fdiv_rn(a.lo.z, a.lo.w);
+    m.n = static_cast<uint32_t>(a.lo.w);
   } else {
-    const AccFixed* a = t.acc64 + s;
-    const long long sr = __ldcg(&a->r), sg = __ldcg(&a->g), sb = __ldcg(&a->b);
-    const unsigned long long n = __ldcg(&a->n);
+    const long long sr = bits64(a.lo.x, a.lo.y), sg = bits64(a.lo.z, a.lo.w);
+    const long long sb = bits64(a.hi.x, a.hi.y);
+    const unsigned long long n = static_cast<unsigned long long>(bits64(a.hi.z, a.hi.w));
     const float fn = __ull2float_rn(n);
     m.r = __fdiv_rn(__fmul_rn(__ll2float_rn(sr), 0x1p-24f), fn);
     m.g = __fdiv_rn(__fmul_rn(__ll2float_rn(sg), 0x1p-24f), fn);
@@ -339,60 +366,62 @@ __device__ __forceinline__ CellMean cell_mean(const TableDev& t, uint32_t s) {
   return m;
 }
 
-// The blended value of a frame cell replaces its accumulator: 16 bytes
-// {c r, c g, c b, N bits} at the start of the cell's accumulator (both modes).
-__device__ __forceinline__ float4* blended_slot(const TableDev& t, uint32_t s) {
-  return t.fixed ? reinterpret_cast<float4*>(t.acc64 + s) : t.acc + s;
+// History value as loaded from memory.
+struct HistRaw {
+  float r, g, b;
+  uint32_t n;
+};
+
+__device__ __forceinline__ HistRaw load_hist(const TableDev& t, uint32_t h) {
+  HistRaw o;
+  if (t.hist_mode == 1) {
+    const float4 v = __ldcg(reinterpret_cast<const float4*>(hist_cell(t, h)));
+    o.r = v.x;
+    o.g = v.y;
+    o.b = v.z;
+    o.n = __float_as_uint(v.w);
+  } else {
+    const uint2 v = __ldcg(reinterpret_cast<const uint2*>(hist_cell(t, h)));
+    const float2 rg = __half22float2(*reinterpret_cast<const __half2*>(&v.x));
+    o.r = rg.x;
+    o.g = rg.y;
+    o.b = __half2float(__ushort_as_half(static_cast<unsigned short>(v.y & 0xFFFFu)));
+    o.n = v.y >> 16;
+  }
+  return o;
 }
 
 // Temporal filtering / integration of one cell (Sec. 3.4.1), run once per
 // claimed frame cell by its owner: c = alpha c_old + (1 - alpha) c_new, where
 // alpha < 0 means alpha = N_old / (N_old + N_new); no history -> c = c_new.
-// The history cell is updated and the result is left in the frame cell for
-// the lookups of this frame.  A cell whose history window was full keeps
-// c_new and N = N_new.
-__device__ __forceinline__ void blend_cell(const TableDev& t, uint32_t s, float alpha) {
-  const CellMean m = cell_mean(t, s);
+// The history cell `h` is updated (h == kOverflowSlot: the history window was
+// full, the cell keeps c_new and N = N_new) and the result is left in the
+// frame cell s for the lookups of this frame.
+__device__ __forceinline__ void blend_store(const TableDev& t, uint32_t s, uint32_t h,
+                                            const CellMean& m, const HistRaw& old, float alpha) {
   float cr = m.r, cg = m.g, cb = m.b;
   uint32_t N = m.n;
-  const uint32_t hs = __ldcg(t.hslot + s);
-  if (hs != kOverflowSlot) {
-    uint32_t n_old;
-    float or_, og, ob;
-    if (t.hist_mode == 1) {
-      const float4 h = __ldcg(t.hist + hs);
-      or_ = h.x;
-      og = h.y;
-      ob = h.z;
-      n_old = __float_as_uint(h.w);
-    } else {
-      const uint2 h = __ldcg(t.hist16 + hs);
-      const float2 rg = __half22float2(*reinterpret_cast<const __half2*>(&h.x));
-      or_ = rg.x;
-      og = rg.y;
-      ob = __half2float(__ushort_as_half(static_cast<unsigned short>(h.y & 0xFFFFu)));
-      n_old = h.y >> 16;
-    }
-    if (n_old != 0u) {
+  if (h != kOverflowSlot) {
+    if (old.n != 0u) {
       const float a =
           alpha >= 0.0f ? alpha
-                        : __fdiv_rn(__uint2float_rn(n_old),
-                                    __fadd_rn(__uint2float_rn(n_old), __uint2float_rn(m.n)));
+                        : __fdiv_rn(__uint2float_rn(old.n),
+                                    __fadd_rn(__uint2float_rn(old.n), __uint2float_rn(m.n)));
       const float a1 = __fsub_rn(1.0f, a);
-      cr = __fadd_rn(__fmul_rn(a, or_), __fmul_rn(a1, cr));
-      cg = __fadd_rn(__fmul_rn(a, og), __fmul_rn(a1, cg));
-      cb = __fadd_rn(__fmul_rn(a, ob), __fmul_rn(a1, cb));
+      cr = __fadd_rn(__fmul_rn(a, old.r), __fmul_rn(a1, cr));
+      cg = __fadd_rn(__fmul_rn(a, old.g), __fmul_rn(a1, cg));
+      cb = __fadd_rn(__fmul_rn(a, old.b), __fmul_rn(a1, cb));
     }
     if (t.hist_mode == 1) {
-      N = n_old + m.n;
-      __stcg(t.hist + hs, make_float4(cr, cg, cb, __uint_as_float(N)));
+      N = old.n + m.n;
+      __stcg(reinterpret_cast<float4*>(hist_cell(t, h)), make_float4(cr, cg, cb, __uint_as_float(N)));
     } else {
-      N = min(n_old + m.n, 65535u);
+      N = min(old.n + m.n, 65535u);
       const __half2 rg = __floats2half2_rn(cr, cg);
       const __half hb = __float2half_rn(cb);
       const uint32_t lo = *reinterpret_cast<const uint32_t*>(&rg);
       const uint32_t hi = static_cast<uint32_t>(__half_as_ushort(hb)) | (N << 16);
-      __stcg(t.hist16 + hs, make_uint2(lo, hi));
+      __stcg(reinterpret_cast<uint2*>(hist_cell(t, h)), make_uint2(lo, hi));
       // lookups see what the history stores
       const float2 back = __half22float2(rg);
       cr = back.x;
@@ -400,32 +429,44 @@ __device__ __forceinline__ void blend_cell(const TableDev& t, uint32_t s, float 
       cb = __half2float(hb);
     }
   }
-  __stcg(blended_slot(t, s), make_float4(cr, cg, cb, __uint_as_float(N)));
+  __stcg(frame_value(t, s), make_float4(cr, cg, cb, __uint_as_float(N)));
 }
 
-// Value returned for a vertex of cell s: the cell average, or the blended
-// value left in the cell by blend_cell.
-__device__ __forceinline__ CellMean cell_value(const TableDev& t, uint32_t s, bool blended) {
-  if (!blended) return cell_mean(t, s);
-  const float4 h = __ldcg(blended_slot(t, s));
+// Blend one cell (loads and all); used where cells are visited one at a time.
+__device__ __forceinline__ void blend_cell(const TableDev& t, uint32_t s, float alpha) {
+  const AccRaw a = load_acc(t, s);
+  const uint32_t h = __ldcg(frame_hslot(t, s));
+  HistRaw old{0.f, 0.f, 0.f, 0u};
+  if (h != kOverflowSlot) old = load_hist(t, h);
+  blend_store(t, s, h, mean_of(t, a), old, alpha);
+}
+
+// Value returned for cell s: the cell average, or the blended value.
+__device__ __forceinline__ CellMean value_of(const TableDev& t, const AccRaw& a, bool blended) {
+  if (!blended) return mean_of(t, a);
   CellMean m;
-  m.r = h.x;
-  m.g = h.y;
-  m.b = h.z;
-  m.n = __float_as_uint(h.w);
+  m.r = a.lo.x;
+  m.g = a.lo.y;
+  m.b = a.lo.z;
+  m.n = __float_as_uint(a.lo.w);
   return m;
+}
+
+__device__ __forceinline__ AccRaw load_value(const TableDev& t, uint32_t s, bool blended) {
+  if (!blended) return load_acc(t, s);
+  AccRaw a;
+  a.lo = __ldcg(frame_value(t, s));
+  a.hi = make_float4(0.f, 0.f, 0.f, 0.f);
+  return a;
 }
 
 // Empty a frame cell (fingerprint and accumulator) for the next frame.
 __device__ __forceinline__ void clear_cell(const TableDev& t, uint32_t s) {
-  if (!t.fixed) {
-    __stcg(t.acc + s, make_float4(0.f, 0.f, 0.f, 0.f));
-  } else {
-    float4* p = reinterpret_cast<float4*>(t.acc64 + s);
-    __stcg(p, make_float4(0.f, 0.f, 0.f, 0.f));
-    __stcg(p + 1, make_float4(0.f, 0.f, 0.f, 0.f));
-  }
-  __stcg(t.fp + s, 0u);
+  float4* p = frame_value(t, s);
+  const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+  __stcg(p, z);
+  __stcg(p + 1, z);  // FP32: fingerprint, history link, padding; fixed: sum b, count
+  if (t.fixed) __stcg(frame_fp(t, s), 0u);
 }
 
 // ---------------------------------------------------------------- grid barrier

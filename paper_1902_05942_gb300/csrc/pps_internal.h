@@ -27,8 +27,8 @@ cudaError_t launch_keys(const KeyConst& kc, const VertexPtrs& v, size_t n, uint3
                         uint32_t* f_out, cudaStream_t st);
 cudaError_t launch_blend(const TableDev& t, float alpha, cudaStream_t st);
 cudaError_t launch_clear_dirty(const TableDev& t, cudaStream_t st);
-cudaError_t launch_count_occupied(const uint32_t* fp, uint32_t T, unsigned long long* out,
-                                  cudaStream_t st);
+cudaError_t launch_count_occupied(const unsigned char* cells, uint32_t stride, uint32_t fp_off,
+                                  uint32_t T, unsigned long long* out, cudaStream_t st);
 cudaError_t plan_fused(size_t n, bool temporal, FusedPlan* plan);
 cudaError_t launch_fused(const KeyConst& kc, const TableDev& t, const VertexPtrs& v, size_t n,
                          const OutPtrs& o, bool temporal, bool blend, float alpha,

@@ -57,10 +57,16 @@ __device__ __forceinline__ T block_sum(T x) {
   return tot;  // valid in thread 0
 }
 
-// Insert the four vertices j..j+3 (those below `end`); returns their cell
+// Insert the four vertices j..j+3 (those below `end`).  Returns their cell
 // indices (kOverflowSlot on probe overflow) and which of them own their cell
-// this frame (published its fingerprint).  With a history, owners also link
-// their cell to its history cell.
+// this frame (published its fingerprint).  Owners of a temporal table also
+// link their cell to its history cell.
+//
+// The four vertices go through each step together so that their memory
+// operations overlap: keys; merging of equal keys among the four (their
+// contributions are summed in registers and sent with one atomic); the first
+// probe of every distinct key (four compare-and-swaps in flight); the rare
+// longer probes; the accumulating reds; and the owners' history probes.
 struct Four {
   uint32_t slot[4];
   bool owner[4];
@@ -74,39 +80,126 @@ __device__ __forceinline__ Four insert_four(const KeyConst& kc, const TableDev& 
                PZ = load4(v.pz, j, end, vec);
   const float4 NX = load4(v.nx, j, end, vec), NY = load4(v.ny, j, end, vec),
                NZ = load4(v.nz, j, end, vec);
-  const float4 R = load4(v.r, j, end, vec), G = load4(v.g, j, end, vec),
-               B = load4(v.b, j, end, vec);
-  Four f;
+  uint32_t h1[4], f[4];
+  bool lead[4];
+  int of[4];
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
-    f.slot[q] = kOverflowSlot;
-    f.owner[q] = false;
-    if (j + q < end) {
-      const Key k = vertex_key(kc, comp(PX, q), comp(PY, q), comp(PZ, q), comp(NX, q),
-                               comp(NY, q), comp(NZ, q), vertex_id(v, j + q), v.stream_id);
-      bool claimed;
-      const uint32_t s = probe_insert(t.fp, t.mask, t.max_probes, k.h1 & t.mask, k.fp, claimed);
-      f.slot[q] = s;
-      if (s == kOverflowSlot) {
-        ++n_ovf;
-      } else {
-        const float r = comp(R, q), g = comp(G, q), b = comp(B, q);
-        long long fr = 0, fg = 0, fb = 0;
-        if (t.fixed) {
-          fr = to_fixed(r);
-          fg = to_fixed(g);
-          fb = to_fixed(b);
-        }
-        accumulate(t, s, r, g, b, fr, fg, fb, 1u);
-        f.owner[q] = claimed;
-        if (claimed) {
-          ++n_cells;
-          if (t.hist_mode) link_history(t, s, k.h1, k.fp, n_hovf);
-        }
+    const bool valid = j + q < end;
+    Key k{0u, 0u};
+    if (valid)
+      k = vertex_key(kc, comp(PX, q), comp(PY, q), comp(PZ, q), comp(NX, q), comp(NY, q),
+                     comp(NZ, q), vertex_id(v, j + q), v.stream_id);
+    h1[q] = k.h1;
+    f[q] = k.fp;  // 0 marks an absent vertex (fingerprints are never 0)
+    lead[q] = valid;
+    of[q] = q;
+  }
+  // merge equal keys: a later vertex joins the first earlier one with its key
+#pragma unroll
+  for (int q = 1; q < 4; ++q) {
+#pragma unroll
+    for (int p = 0; p < q; ++p) {
+      if (lead[q] && lead[p] && of[q] == q && h1[p] == h1[q] && f[p] == f[q]) {
+        lead[q] = false;
+        of[q] = p;
       }
     }
   }
-  return f;
+  const float4 R = load4(v.r, j, end, vec), G = load4(v.g, j, end, vec),
+               B = load4(v.b, j, end, vec);
+  float sr[4], sg[4], sb[4];
+  long long fr[4], fg[4], fb[4];
+  uint32_t cnt[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    sr[q] = 0.f;
+    sg[q] = 0.f;
+    sb[q] = 0.f;
+    fr[q] = fg[q] = fb[q] = 0;
+    cnt[q] = 0u;
+  }
+  // (static indices only: both loops unroll completely)
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const bool use = f[q] != 0u;
+    const float r = use ? comp(R, q) : 0.f, g = use ? comp(G, q) : 0.f, b = use ? comp(B, q) : 0.f;
+    long long xr = 0, xg = 0, xb = 0;
+    if (t.fixed) {
+      xr = to_fixed(r);
+      xg = to_fixed(g);
+      xb = to_fixed(b);
+    }
+#pragma unroll
+    for (int p = 0; p <= q; ++p) {
+      if (!use || of[q] != p) continue;
+      sr[p] = __fadd_rn(sr[p], r);
+      sg[p] = __fadd_rn(sg[p], g);
+      sb[p] = __fadd_rn(sb[p], b);
+      fr[p] += xr;
+      fg[p] += xg;
+      fb[p] += xb;
+      ++cnt[p];
+    }
+  }
+  // first probe of every distinct key, all in flight together
+  const ProbeTable fpt = frame_probe(t);
+  uint32_t old[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+    old[q] = lead[q] ? atomicCAS(probe_fp(fpt, h1[q] & t.mask), 0u, f[q]) : 0u;
+  uint32_t slot[4];
+  bool claimed[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    slot[q] = kOverflowSlot;
+    claimed[q] = false;
+    if (!lead[q]) continue;
+    if (old[q] == 0u || old[q] == f[q]) {
+      slot[q] = h1[q] & t.mask;
+      claimed[q] = old[q] == 0u;
+    } else {
+      bool c;
+      slot[q] = probe_insert_from(fpt, h1[q] & t.mask, f[q], 1u, c);
+      claimed[q] = c;
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+    if (lead[q] && slot[q] != kOverflowSlot)
+      accumulate(t, slot[q], sr[q], sg[q], sb[q], fr[q], fg[q], fb[q], cnt[q]);
+  // owners of a temporal table find or claim their history cell
+  if (t.hist_mode) {
+    const ProbeTable hpt = hist_probe(t);
+    uint32_t hold[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      hold[q] = claimed[q] ? atomicCAS(probe_fp(hpt, h1[q] & t.hmask), 0u, f[q]) : 0u;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      if (!claimed[q]) continue;
+      uint32_t h = h1[q] & t.hmask;
+      if (hold[q] != 0u && hold[q] != f[q]) {
+        bool hc;
+        h = probe_insert_from(hpt, h1[q] & t.hmask, f[q], 1u, hc);
+      }
+      n_hovf += h == kOverflowSlot ? 1ull : 0ull;
+      __stcg(frame_hslot(t, slot[q]), h);
+    }
+  }
+  Four out;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    uint32_t sl = slot[0];
+#pragma unroll
+    for (int p = 1; p <= q; ++p)
+      if (of[q] == p) sl = slot[p];
+    out.slot[q] = f[q] == 0u ? kOverflowSlot : sl;
+    out.owner[q] = claimed[q];
+    if (f[q] != 0u && out.slot[q] == kOverflowSlot) ++n_ovf;
+    n_cells += claimed[q] ? 1ull : 0ull;
+  }
+  return out;
 }
 
 struct Result {
@@ -115,25 +208,56 @@ struct Result {
   uint8_t status;
 };
 
-__device__ __forceinline__ Result resolve(const TableDev& t, const VertexPtrs& v, size_t j,
-                                          uint32_t s, bool blended) {
-  Result res;
-  if (s == kOverflowSlot) {
-    // probe limit exceeded: the unfiltered contribution of the vertex itself
-    res.r = __ldcs(v.r + j);
-    res.g = __ldcs(v.g + j);
-    res.b = __ldcs(v.b + j);
-    res.n = 0u;
-    res.status = 2;
-  } else {
-    const CellMean m = cell_value(t, s, blended);
-    res.r = m.r;
-    res.g = m.g;
-    res.b = m.b;
-    res.n = m.n;
-    res.status = m.n < t.lowcount ? 1 : 0;
+// Look up the four cells s[0..3] (loads issued together) and resolve each
+// vertex: cell average / blended value, or its own contribution on overflow.
+__device__ __forceinline__ void resolve_four(const TableDev& t, const VertexPtrs& v, size_t j,
+                                             size_t end, const uint32_t (&s)[4], bool blended,
+                                             Result (&res)[4]) {
+  AccRaw a[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+    if (j + q < end && s[q] != kOverflowSlot) a[q] = load_value(t, s[q], blended);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    res[q] = Result{0.f, 0.f, 0.f, 0u, 0};
+    if (j + q >= end) continue;
+    if (s[q] == kOverflowSlot) {
+      // probe limit exceeded: the unfiltered contribution of the vertex itself
+      res[q].r = __ldcs(v.r + j + q);
+      res[q].g = __ldcs(v.g + j + q);
+      res[q].b = __ldcs(v.b + j + q);
+      res[q].status = 2;
+    } else {
+      const CellMean m = value_of(t, a[q], blended);
+      res[q].r = m.r;
+      res[q].g = m.g;
+      res[q].b = m.b;
+      res[q].n = m.n;
+      res[q].status = m.n < t.lowcount ? 1 : 0;
+    }
   }
-  return res;
+}
+
+// Blend the owned cells among four stash entries, loads issued together.
+__device__ __forceinline__ void blend_four(const TableDev& t, const uint32_t (&s)[4],
+                                           const bool (&own)[4], float alpha) {
+  AccRaw a[4];
+  uint32_t h[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    if (!own[q]) continue;
+    a[q] = load_acc(t, s[q]);
+    h[q] = __ldcg(frame_hslot(t, s[q]));
+  }
+  HistRaw old[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    old[q] = HistRaw{0.f, 0.f, 0.f, 0u};
+    if (own[q] && h[q] != kOverflowSlot) old[q] = load_hist(t, h[q]);
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+    if (own[q]) blend_store(t, s[q], h[q], mean_of(t, a[q]), old[q], alpha);
 }
 
 __device__ __forceinline__ void store_four(const OutPtrs& o, size_t j, size_t end, bool vec,
@@ -222,19 +346,19 @@ __global__ void __launch_bounds__(kBlock) k_query(KeyConst kc, TableDev t, Verte
         if (j + q < n) {
           const Key k = vertex_key(kc, comp(PX, q), comp(PY, q), comp(PZ, q), comp(NX, q),
                                    comp(NY, q), comp(NZ, q), vertex_id(v, j + q), v.stream_id);
-          s[q] = probe_find(t.fp, t.mask, t.max_probes, k.h1 & t.mask, k.fp);
+          s[q] = probe_find(t, k.h1 & t.mask, k.fp);
         }
       }
     }
-    Result res[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      if (s[q] != kOverflowSlot && s[q] > t.mask) {  // not a slot of this table
+      if (s[q] != kOverflowSlot && s[q] > t.mask) {  // not a cell of this table
         atomicOr(&t.ctrl->error, kErrBadSlot);
         s[q] = kOverflowSlot;
       }
-      res[q] = j + q < n ? resolve(t, v, j + q, s[q], blended != 0) : Result{0.f, 0.f, 0.f, 0u, 0};
     }
+    Result res[4];
+    resolve_four(t, v, j, n, s, blended != 0, res);
     store_four(o, j, n, ovec != 0, res);
   }
 }
@@ -263,11 +387,12 @@ __global__ void __launch_bounds__(kBlock) k_keys(KeyConst kc, VertexPtrs v, size
   }
 }
 
-__global__ void __launch_bounds__(kBlock) k_count_occupied(const uint32_t* fp, uint32_t T,
-                                                           unsigned long long* out) {
+__global__ void __launch_bounds__(kBlock) k_count_occupied(const unsigned char* cells,
+                                                           uint32_t stride, uint32_t fp_off,
+                                                           uint32_t T, unsigned long long* out) {
   unsigned long long c = 0;
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < T; i += gridDim.x * blockDim.x)
-    c += fp[i] != 0u;
+    c += *reinterpret_cast<const uint32_t*>(cells + static_cast<size_t>(i) * stride + fp_off) != 0u;
   const unsigned long long s = block_sum(c);
   if (threadIdx.x == 0 && s) atomicAdd(out, s);
 }
@@ -286,7 +411,7 @@ struct FusedArgs {
 };
 
 template <bool TEMPORAL>
-__global__ void __launch_bounds__(kFusedBlock, 2) k_fused(FusedArgs a) {
+__global__ void __launch_bounds__(kFusedBlock, 1) k_fused(FusedArgs a) {
   extern __shared__ __align__(16) uint32_t s_stash[];
   const TableDev& t = a.t;
   const size_t beg = static_cast<size_t>(blockIdx.x) * a.chunk;
@@ -325,10 +450,14 @@ __global__ void __launch_bounds__(kFusedBlock, 2) k_fused(FusedArgs a) {
     for (size_t j = beg + 4 * threadIdx.x; j < end; j += step) {
       const uint4 w = *reinterpret_cast<const uint4*>(stash + (j - beg));
       const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+      uint32_t sl[4];
+      bool own[4];
 #pragma unroll
-      for (int q = 0; q < 4; ++q)
-        if (j + q < end && ws[q] != kStashOverflow && (ws[q] & kOwnerBit))
-          blend_cell(t, ws[q] & ~kOwnerBit, a.alpha);
+      for (int q = 0; q < 4; ++q) {
+        own[q] = j + q < end && ws[q] != kStashOverflow && (ws[q] & kOwnerBit);
+        sl[q] = ws[q] & ~kOwnerBit;
+      }
+      blend_four(t, sl, own, a.alpha);
     }
     if (!grid_barrier(t.ctrl, gridDim.x)) return;
   }
@@ -338,12 +467,11 @@ __global__ void __launch_bounds__(kFusedBlock, 2) k_fused(FusedArgs a) {
   for (size_t j = beg + 4 * threadIdx.x; j < end; j += step) {
     const uint4 w = *reinterpret_cast<const uint4*>(stash + (j - beg));
     const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
-    Result res[4];
+    uint32_t sl[4];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const uint32_t s = ws[q] == kStashOverflow ? kOverflowSlot : (ws[q] & ~kOwnerBit);
-      res[q] = j + q < end ? resolve(t, a.v, j + q, s, blended) : Result{0.f, 0.f, 0.f, 0u, 0};
-    }
+    for (int q = 0; q < 4; ++q) sl[q] = ws[q] == kStashOverflow ? kOverflowSlot : (ws[q] & ~kOwnerBit);
+    Result res[4];
+    resolve_four(t, a.v, j, end, sl, blended, res);
     store_four(a.o, j, end, ovec, res);
   }
   if (!grid_barrier(t.ctrl, gridDim.x)) return;
@@ -422,9 +550,9 @@ cudaError_t launch_clear_dirty(const TableDev& t, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_count_occupied(const uint32_t* fp, uint32_t T, unsigned long long* out,
-                                  cudaStream_t st) {
-  k_count_occupied<<<sm_count() * 4, kBlock, 0, st>>>(fp, T, out);
+cudaError_t launch_count_occupied(const unsigned char* cells, uint32_t stride, uint32_t fp_off,
+                                  uint32_t T, unsigned long long* out, cudaStream_t st) {
+  k_count_occupied<<<sm_count() * 4, kBlock, 0, st>>>(cells, stride, fp_off, T, out);
   return cudaGetLastError();
 }
 

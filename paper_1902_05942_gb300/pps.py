@@ -81,6 +81,8 @@ SIGNATURES = {
                  ctypes.c_int),
     "pps_stats": ([_vp, ctypes.POINTER(pps_stats_t), _vp], ctypes.c_int),
     "pps_table_dump": ([_vp, _vp, _vp, _vp], ctypes.c_int),
+    "pps_bench_rate": ([ctypes.c_int, ctypes.c_size_t, ctypes.c_size_t, _vp, _vp,
+                        ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
 }
 
 _lib: Optional[ctypes.CDLL] = None
@@ -240,6 +242,20 @@ def pps_table_dump(handle, T: int, fixed: bool, stream=None):
     acc = np.zeros((T, 4), dtype=np.int64 if fixed else np.float32)
     _check(lib().pps_table_dump(handle, fp.ctypes.data, acc.ctypes.data, _stream(stream)))
     return fp, acc
+
+
+RATE_KINDS = {"red_v4_f32": 0, "cas_b32": 1, "red_f32": 2, "gather_v4": 3}
+
+
+def pps_bench_rate(kind: str, region: torch.Tensor, ops: int, stream=None) -> float:
+    """Random memory operations per second of `kind` over the device tensor
+    `region` (its contents are overwritten)."""
+    out = ctypes.c_double()
+    rc = lib().pps_bench_rate(RATE_KINDS[kind], region.numel() * region.element_size(), ops,
+                              region.data_ptr(), _stream(stream), ctypes.byref(out))
+    if rc:
+        raise PPSError(rc, "pps_bench_rate failed")
+    return out.value
 
 
 # ---------------------------------------------------------------- convenience

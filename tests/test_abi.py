@@ -10,7 +10,7 @@ import pytest
 
 from conftest import ROOT
 
-HEADER = os.path.join(ROOT, "include", "pps.h")
+HEADERS = [os.path.join(ROOT, "include", h) for h in ("pps.h", "pps_bench.h")]
 
 
 def _lib():
@@ -20,7 +20,7 @@ def _lib():
 
 
 def declared_functions():
-    src = open(HEADER).read()
+    src = "".join(open(h).read() for h in HEADERS)
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
     return sorted(set(re.findall(r"\b(pps_[a-z_0-9]+)\s*\(", src)))
 
