@@ -355,6 +355,45 @@ def run_reference(args):
     }), flush=True)
 
 
+def run_ncu_case(args):
+    """A small fixed case for profilers: one HD frame through the fused launch,
+    three times (history on, batch width from --batch), no timing."""
+    import torch
+    from paper_1902_05942_gb300 import build, configs, pps, scene
+    build.build()
+    torch.cuda.set_device(0)
+    w = configs.hd()
+    cfg = w.filters[0]
+    spec = configs.frame_spec(w, 0, 0)
+    v = scene.trace_stream(spec, 0, "cuda")
+    d = {k: v[k] for k in scene.STREAMS}
+    out = pps.empty_output(d["px"].numel(), "cuda", count=False)
+    tab = pps.Table(cfg, hist_mode=args.hist)
+    if args.batch:
+        tab.tune(args.batch)
+    for i in range(3):
+        tab.filter(d, spec.view.eye, i, blend=args.hist != 0, alpha=cfg.alpha, out=out)
+    torch.cuda.synchronize()
+    print(json.dumps({"ncu_case": "hd", "hist": args.hist, "stats": tab.stats()}))
+
+
+def run_rates(args):
+    """Random memory-operation rates of this GPU (pps_bench_rate): each
+    operation on its own random 32-byte sector of a 32 MB (L2-resident) and a
+    1 GB region."""
+    import torch
+    from paper_1902_05942_gb300 import build, pps
+    build.build()
+    torch.cuda.set_device(0)
+    out = {}
+    for mb in (32, 1024):
+        region = torch.zeros(mb << 20, dtype=torch.uint8, device="cuda")
+        for kind in pps.RATE_KINDS:
+            out[f"{kind}@{mb}MB"] = pps.pps_bench_rate(kind, region, 1 << 25) / 1e9
+        del region
+    print(json.dumps({"rates_G_ops_per_s": out}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -364,7 +403,15 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=1_500_000)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ncu-case", action="store_true", help="small fixed case for profilers")
+    ap.add_argument("--rates", action="store_true", help="random memory-operation rates")
+    ap.add_argument("--hist", type=int, default=1, help="--ncu-case: history mode")
+    ap.add_argument("--batch", type=int, default=0, help="--ncu-case: batch width")
     args = ap.parse_args()
+    if args.ncu_case:
+        return run_ncu_case(args)
+    if args.rates:
+        return run_rates(args)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":

@@ -156,6 +156,17 @@ typedef struct pps_stats_t {
   uint32_t frame;             /* frame number of the last pps_build/pps_filter */
 } pps_stats_t;
 
+/*
+ * Launch shape of a table's kernels (no effect on results).
+ *  batch     vertices each thread carries through one insert step together
+ *            (their probes and atomics overlap): 2 or 4; 0 = library default (2).
+ *  reserved  must be zero.
+ */
+typedef struct pps_tuning {
+  uint32_t batch;
+  uint32_t reserved[7];
+} pps_tuning;
+
 typedef struct pps_table pps_table;
 
 /* Library version string (static storage). */
@@ -241,6 +252,11 @@ int pps_filter(pps_table *t, const pps_camera *cam, uint32_t frame, const pps_ve
 int pps_filter_host(pps_table *t, const pps_camera *cam, uint32_t frame,
                     const pps_vertices *v_host, size_t n, int blend, float alpha,
                     const pps_output *out_host, void *stream);
+
+/* pps_set_tuning / pps_get_tuning: set or read the launch shape (pps_tuning).
+ * Results do not depend on it.  Errors: PPS_EINVAL. */
+int pps_set_tuning(pps_table *t, const pps_tuning *tune);
+int pps_get_tuning(pps_table *t, pps_tuning *tune);
 
 /*
  * pps_keys: Algorithm 1 alone, for inspection: for each vertex write the full

@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
+#include <algorithm>
 #include <cstring>
 #include <string>
 
@@ -44,6 +45,9 @@ struct pps_table {
   pps::TableDev dev{};
   pps::KeyConst kc{};
   int state = kClean;
+  uint32_t frame_tiles = 0;  // split path: tiles (cell-id blocks) used this frame
+  pps_tuning tune{};         // launch shape (batch width 0 = library default)
+  size_t D = 0;              // capacity of the dense cell arrays
   uint32_t* gstash = nullptr;
   size_t gstash_cap = 0;
   void* stage = nullptr;  // pps_filter_host device staging
@@ -129,15 +133,63 @@ pps::OutPtrs to_dev(const pps_output* o) {
 
 bool temporal(const pps_table* t) { return t->p.hist_mode != PPS_HIST_NONE; }
 
-// Empty the cells touched since the last clear (dirty list) and reset the
-// frame counters.
+int batch_of(const pps_table* t) { return t->tune.batch == 4 ? 4 : 2; }
+
+// Empty the cells of the split path's frame (the fused path leaves none behind)
+// and reset the frame counters.
 int reset_frame(pps_table* t, cudaStream_t st) {
   if (t->state != kClean) {
-    PPS_CUDA(pps::launch_clear_dirty(t->dev, st));
-    PPS_CUDA(cudaMemsetAsync(&t->dev.ctrl->dirty_count, 0, sizeof(unsigned int), st));
+    PPS_CUDA(pps::launch_clear(t->dev, t->frame_tiles, st));
+    t->frame_tiles = 0;
     t->state = kClean;
   }
   PPS_CUDA(cudaMemsetAsync(t->dev.ctrl, 0, pps::kCtrlFrameBytes, st));
+  return PPS_OK;
+}
+
+// Make the dense cell arrays hold at least `need` cells, keeping the first
+// `keep` cells (accumulators, cell info and tile counts).  New accumulators
+// start at zero.
+int ensure_dense(pps_table* t, size_t need, size_t keep, cudaStream_t st) {
+  if (need <= t->D) return PPS_OK;
+  if (need > 0xFFFFFFF0ull) return fail(PPS_EINVAL, "more than 2^32 - 16 cells in one frame");
+  size_t cap = t->D ? t->D : 1;
+  while (cap < need) cap *= 2;
+  if (cap > 0xFFFFFFF0ull) cap = 0xFFFFFFF0ull;
+  const size_t acc_b = t->dev.fixed ? 32 : 16;
+  const size_t nb = cap / 4 + 16;  // tile counts: one per block of >= 4 cells
+  void *acc = nullptr, *info = nullptr, *bc = nullptr;
+  cudaError_t e = cudaMalloc(&acc, cap * acc_b);
+  if (e == cudaSuccess) e = cudaMalloc(&info, cap * sizeof(uint4));
+  if (e == cudaSuccess) e = cudaMalloc(&bc, nb * sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMemsetAsync(acc, 0, cap * acc_b, st);
+  void* old_acc = t->dev.fixed ? static_cast<void*>(t->dev.acc64) : static_cast<void*>(t->dev.acc);
+  if (e == cudaSuccess && keep) {
+    e = cudaMemcpyAsync(acc, old_acc, keep * acc_b, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(info, t->dev.info, keep * sizeof(uint4), cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(bc, t->dev.bcount, (t->D / 4 + 16) * sizeof(uint32_t),
+                          cudaMemcpyDeviceToDevice, st);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    cudaFree(acc);
+    cudaFree(info);
+    cudaFree(bc);
+    cudaGetLastError();
+    return fail(PPS_ENOMEM, std::string("dense cell arrays: ") + cudaGetErrorString(e));
+  }
+  cudaFree(old_acc);
+  cudaFree(t->dev.info);
+  cudaFree(t->dev.bcount);
+  if (t->dev.fixed)
+    t->dev.acc64 = static_cast<unsigned long long*>(acc);
+  else
+    t->dev.acc = static_cast<float4*>(acc);
+  t->dev.info = static_cast<uint4*>(info);
+  t->dev.bcount = static_cast<uint32_t*>(bc);
+  t->D = cap;
   return PPS_OK;
 }
 
@@ -149,9 +201,12 @@ void set_camera(pps_table* t, const pps_camera* cam, uint32_t frame) {
 }
 
 void free_all(pps_table* t) {
-  cudaFree(t->dev.cells);
+  cudaFree(t->dev.slots);
+  cudaFree(t->dev.acc);
+  cudaFree(t->dev.acc64);
+  cudaFree(t->dev.info);
+  cudaFree(t->dev.bcount);
   cudaFree(t->dev.hcells);
-  cudaFree(t->dev.dirty);
   cudaFree(t->dev.ctrl);
   cudaFree(t->gstash);
   cudaFree(t->stage);
@@ -190,17 +245,17 @@ int pps_create(pps_table** out, const pps_params* p) {
     return e;
   };
   const bool fixed = p->accum_mode == PPS_ACCUM_FIXED;
-  t->dev.stride = fixed ? 64u : 32u;
-  t->dev.fp_off = fixed ? 32u : 16u;
+  t->dev.fixed = fixed;
   t->dev.hstride = p->hist_mode == PPS_HIST_FP16 ? 16u : 32u;
   t->dev.hfp_off = p->hist_mode == PPS_HIST_FP16 ? 8u : 16u;
-  cudaError_t e = alloc(reinterpret_cast<void**>(&t->dev.cells), T * t->dev.stride);
+  cudaError_t e = alloc(reinterpret_cast<void**>(&t->dev.slots), T * sizeof(unsigned long long));
   if (e == cudaSuccess && p->hist_mode != PPS_HIST_NONE)
     e = alloc(reinterpret_cast<void**>(&t->dev.hcells), Th * t->dev.hstride);
-  if (e == cudaSuccess) e = alloc(reinterpret_cast<void**>(&t->dev.dirty), T * sizeof(uint32_t));
   if (e == cudaSuccess) e = alloc(reinterpret_cast<void**>(&t->dev.ctrl), sizeof(pps::Ctrl));
   if (e == cudaSuccess) e = alloc(reinterpret_cast<void**>(&t->scratch_u64), 2 * sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e == cudaSuccess && ensure_dense(t, std::min<size_t>(T, 1u << 22), 0, nullptr) != PPS_OK)
+    e = cudaErrorMemoryAllocation;
   if (e != cudaSuccess) {
     free_all(t);
     delete t;
@@ -212,7 +267,6 @@ int pps_create(pps_table** out, const pps_params* p) {
   t->dev.hmask = t->Th - 1;
   t->dev.max_probes = p->max_probes;
   t->dev.lowcount = p->lowcount_threshold;
-  t->dev.fixed = p->accum_mode == PPS_ACCUM_FIXED;
   t->dev.hist_mode = static_cast<int>(p->hist_mode);
   t->kc.k = p->voxel_scale * p->pixel_angle;  // fl32(s * theta_px)
   t->kc.seed = p->seed;
@@ -254,8 +308,13 @@ int pps_insert(pps_table* t, const pps_vertices* v, size_t n, uint32_t* slot_out
   if (int rc = check_table(t)) return rc;
   if (int rc = check_vertices(v, n)) return rc;
   if (t->state != kOpen) return fail(PPS_ESTATE, "pps_insert needs pps_build first (and no pps_blend since)");
-  PPS_CUDA(pps::launch_insert(t->kc, t->dev, to_dev(v), n, slot_out,
-                              static_cast<cudaStream_t>(stream)));
+  const cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t tile = static_cast<size_t>(pps::tile_size());
+  const size_t tiles = (n + tile - 1) / tile;
+  if (int rc = ensure_dense(t, (t->frame_tiles + tiles) * tile, t->frame_tiles * tile, st)) return rc;
+  PPS_CUDA(pps::launch_insert(t->kc, t->dev, to_dev(v), n, slot_out, t->frame_tiles,
+                              batch_of(t), st));
+  t->frame_tiles += static_cast<uint32_t>(tiles);
   return PPS_OK;
 }
 
@@ -264,7 +323,7 @@ int pps_blend(pps_table* t, float alpha, void* stream) {
   if (!temporal(t)) return fail(PPS_EINVAL, "pps_blend needs a table with hist_mode != NONE");
   if (!std::isfinite(alpha) || alpha > 1.0f) return fail(PPS_EINVAL, "alpha must be finite and <= 1");
   if (t->state != kOpen) return fail(PPS_ESTATE, "pps_blend needs an open frame (pps_build, pps_insert)");
-  PPS_CUDA(pps::launch_blend(t->dev, alpha, static_cast<cudaStream_t>(stream)));
+  PPS_CUDA(pps::launch_blend(t->dev, t->frame_tiles, alpha, static_cast<cudaStream_t>(stream)));
   t->state = kBlended;
   return PPS_OK;
 }
@@ -275,8 +334,9 @@ int pps_query(pps_table* t, const pps_vertices* v, size_t n, const uint32_t* slo
   if (int rc = check_vertices(v, n)) return rc;
   if (int rc = check_output(out, n)) return rc;
   if (t->state == kClean) return fail(PPS_ESTATE, "pps_query needs an open frame");
+  const uint32_t id_limit = t->frame_tiles * static_cast<uint32_t>(pps::tile_size());
   PPS_CUDA(pps::launch_query(t->kc, t->dev, to_dev(v), n, slot_in, to_dev(out),
-                             t->state == kBlended, static_cast<cudaStream_t>(stream)));
+                             t->state == kBlended, id_limit, static_cast<cudaStream_t>(stream)));
   return PPS_OK;
 }
 
@@ -294,20 +354,21 @@ int pps_filter(pps_table* t, const pps_camera* cam, uint32_t frame, const pps_ve
   set_camera(t, cam, frame);
   if (n == 0) return PPS_OK;
   pps::FusedPlan plan;
-  PPS_CUDA(pps::plan_fused(n, temporal(t), &plan));
-  // the kernel writes stash words [0, chunk * grid): CTA b owns [b * chunk, (b + 1) * chunk)
-  const size_t stash_need = plan.chunk * static_cast<size_t>(plan.grid);
+  PPS_CUDA(pps::plan_fused(n, temporal(t), batch_of(t), &plan));
+  // cell ids and (off-chip) stash words cover whole tiles: [0, ntiles * tile)
+  const size_t ftile = static_cast<size_t>(pps::fused_tile_size());
+  const size_t stash_need = (n + ftile - 1) / ftile * ftile;
+  if (int rc = ensure_dense(t, stash_need, 0, st)) return rc;
   if (plan.global_stash && t->gstash_cap < stash_need) {
     cudaFree(t->gstash);
     t->gstash = nullptr;
     t->gstash_cap = 0;
-    const size_t cap = stash_need;
-    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&t->gstash), cap * sizeof(uint32_t));
+    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&t->gstash), stash_need * sizeof(uint32_t));
     if (e != cudaSuccess) {
       cudaGetLastError();
       return fail(PPS_ENOMEM, "pps_filter: scratch stash allocation failed");
     }
-    t->gstash_cap = cap;
+    t->gstash_cap = stash_need;
   }
   PPS_CUDA(pps::launch_fused(t->kc, t->dev, to_dev(v), n, to_dev(out), temporal(t), blend != 0,
                              alpha, plan, t->gstash, st));
@@ -373,6 +434,25 @@ int pps_filter_host(pps_table* t, const pps_camera* cam, uint32_t frame, const p
   return PPS_OK;
 }
 
+int pps_set_tuning(pps_table* t, const pps_tuning* tune) {
+  if (int rc = check_table(t)) return rc;
+  if (!tune) return fail(PPS_EINVAL, "tuning is NULL");
+  if (tune->batch != 0 && tune->batch != 2 && tune->batch != 4)
+    return fail(PPS_EINVAL, "batch must be 0, 2 or 4");
+  for (uint32_t r : tune->reserved)
+    if (r) return fail(PPS_EINVAL, "reserved fields must be zero");
+  t->tune = *tune;
+  return PPS_OK;
+}
+
+int pps_get_tuning(pps_table* t, pps_tuning* tune) {
+  if (int rc = check_table(t)) return rc;
+  if (!tune) return fail(PPS_EINVAL, "tuning is NULL");
+  *tune = t->tune;
+  tune->batch = static_cast<uint32_t>(batch_of(t));
+  return PPS_OK;
+}
+
 int pps_keys(pps_table* t, const pps_vertices* v, size_t n, uint32_t* h_out, uint32_t* f_out,
              void* stream) {
   if (int rc = check_table(t)) return rc;
@@ -387,11 +467,10 @@ int pps_stats(pps_table* t, pps_stats_t* out, void* stream) {
   if (!out) return fail(PPS_EINVAL, "out is NULL");
   const cudaStream_t st = static_cast<cudaStream_t>(stream);
   PPS_CUDA(cudaMemsetAsync(t->scratch_u64, 0, 2 * sizeof(unsigned long long), st));
-  PPS_CUDA(pps::launch_count_occupied(t->dev.cells, t->dev.stride, t->dev.fp_off, t->T,
-                                      t->scratch_u64, st));
+  PPS_CUDA(pps::launch_count_nonzero(t->dev.slots, 8, 0, 8, t->T, t->scratch_u64, st));
   if (t->dev.hcells)
-    PPS_CUDA(pps::launch_count_occupied(t->dev.hcells, t->dev.hstride, t->dev.hfp_off, t->Th,
-                                        t->scratch_u64 + 1, st));
+    PPS_CUDA(pps::launch_count_nonzero(t->dev.hcells, t->dev.hstride, t->dev.hfp_off, 4, t->Th,
+                                       t->scratch_u64 + 1, st));
   pps::Ctrl c;
   unsigned long long occ[2] = {0, 0};
   PPS_CUDA(cudaMemcpyAsync(&c, t->dev.ctrl, sizeof(c), cudaMemcpyDeviceToHost, st));
@@ -408,7 +487,7 @@ int pps_stats(pps_table* t, pps_stats_t* out, void* stream) {
   out->frame = t->kc.frame;
   if (c.error) {
     // clear the error word and the barrier state so the table stays usable
-    PPS_CUDA(cudaMemsetAsync(&t->dev.ctrl->error, 0, 3 * sizeof(unsigned int), st));
+    PPS_CUDA(cudaMemsetAsync(&t->dev.ctrl->error, 0, 3 * sizeof(unsigned int), st));  // + barrier
     PPS_CUDA(cudaStreamSynchronize(st));
     char buf[96];
     std::snprintf(buf, sizeof(buf), "device error word 0x%x", c.error);
@@ -421,23 +500,40 @@ int pps_table_dump(pps_table* t, uint32_t* fp_host, void* acc_host, void* stream
   if (int rc = check_table(t)) return rc;
   if (!fp_host) return fail(PPS_EINVAL, "fp_host is NULL");
   const cudaStream_t st = static_cast<cudaStream_t>(stream);
-  const size_t bytes = static_cast<size_t>(t->T) * t->dev.stride;
-  unsigned char* raw = static_cast<unsigned char*>(std::malloc(bytes));
-  if (!raw) return fail(PPS_ENOMEM, "pps_table_dump: host buffer");
-  cudaError_t e = cudaMemcpyAsync(raw, t->dev.cells, bytes, cudaMemcpyDeviceToHost, st);
+  const size_t acc_b = t->dev.fixed ? 32 : 16;
+  unsigned long long* slots =
+      static_cast<unsigned long long*>(std::malloc(t->T * sizeof(unsigned long long)));
+  unsigned char* acc = static_cast<unsigned char*>(std::malloc(t->D * acc_b));
+  if (!slots || !acc) {
+    std::free(slots);
+    std::free(acc);
+    return fail(PPS_ENOMEM, "pps_table_dump: host buffer");
+  }
+  const void* dacc = t->dev.fixed ? static_cast<const void*>(t->dev.acc64)
+                                  : static_cast<const void*>(t->dev.acc);
+  cudaError_t e = cudaMemcpyAsync(slots, t->dev.slots, t->T * sizeof(unsigned long long),
+                                  cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(acc, dacc, t->D * acc_b, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) {
-    std::free(raw);
+    std::free(slots);
+    std::free(acc);
     return cuda_fail("pps_table_dump", e);
   }
-  // de-interleave the cells: fingerprint array and 4-word accumulator array
-  const size_t acc_bytes = t->dev.fixed ? 32 : 16;
+  // per slot: the fingerprint, and the accumulator of the slot's cell
   for (size_t i = 0; i < t->T; ++i) {
-    const unsigned char* c = raw + i * t->dev.stride;
-    std::memcpy(fp_host + i, c + t->dev.fp_off, sizeof(uint32_t));
-    if (acc_host) std::memcpy(static_cast<unsigned char*>(acc_host) + i * acc_bytes, c, acc_bytes);
+    const unsigned long long w = slots[i];
+    fp_host[i] = static_cast<uint32_t>(w);
+    if (!acc_host) continue;
+    unsigned char* dst = static_cast<unsigned char*>(acc_host) + i * acc_b;
+    const size_t id = static_cast<size_t>(w >> 32);  // cell id + 1, 0 = empty
+    if (id == 0 || id - 1 >= t->D)
+      std::memset(dst, 0, acc_b);
+    else
+      std::memcpy(dst, acc + (id - 1) * acc_b, acc_b);
   }
-  std::free(raw);
+  std::free(slots);
+  std::free(acc);
   return PPS_OK;
 }
 

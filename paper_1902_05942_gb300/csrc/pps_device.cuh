@@ -42,48 +42,55 @@ struct Ctrl {
   unsigned long long overflow_vertices;
   unsigned long long vertices;
   unsigned long long hist_overflow;
-  unsigned int dirty_count;
+  unsigned long long tile_next;  // persistent kernel: next vertex tile to hand out
   unsigned int error;
   unsigned int bar_count;
   unsigned int bar_gen;
-  unsigned int pad[4];
+  unsigned int pad[5];
 };
-constexpr size_t kCtrlFrameBytes = 4 * sizeof(unsigned long long);  // reset per frame
+constexpr size_t kCtrlFrameBytes = 5 * sizeof(unsigned long long);  // reset per frame
 
 enum : unsigned int {
   kErrBarrierTimeout = 1u,
   kErrBadSlot = 2u,
 };
 
-// Table layout: one cell is one 32-byte L2 sector (64 bytes in fixed mode), so
-// probing, accumulation, the history link, the lookup and the clear of a cell
-// all touch the same sector.
+// Table layout.
 //
-//   frame cell, FP32 mode (32 B):  [0,16) {sum r, sum g, sum b, count} FP32
-//                                  [16,20) fingerprint   [20,24) history cell
-//   frame cell, fixed mode (64 B): [0,32) {sum r, sum g, sum b, count} int64
-//                                  [32,36) fingerprint   [36,40) history cell
-//   history cell, FP32 (32 B):     [0,16) {c r, c g, c b, N}  [16,20) fingerprint
-//   history cell, FP16 (16 B):     [0,8) {half r, half g, half b, uint16 N}
-//                                  [8,12) fingerprint
-// After the blend, the first 16 bytes of a frame cell hold the blended value
-// {c r, c g, c b, N} for the lookups of the frame (both modes).
+// The hashed table of Sec. 3.2 holds, per slot, only the key's 32-bit
+// fingerprint and the id of its cell: slot = (id + 1) << 32 | fingerprint, 0 =
+// empty.  At 8 bytes a slot, a table of 2^23 slots (64 MB) stays in L2, where
+// the probing compare-and-swaps run several times faster than on DRAM-backed
+// lines.  The cells themselves live in dense arrays indexed by the cell id:
+//   acc   {sum r, sum g, sum b, count} FP32 (16 B), or int64 sums (32 B, fixed)
+//   info  {slot, home hash, fingerprint, history cell} (16 B)
+// Ids are handed out per block of vertices: a CTA (or a tile of the split
+// path) owns the id range [block * B, block * B + count[block]), where B is its
+// vertex count, so a frame's cells occupy a few contiguous runs and the
+// per-cell passes (blend, clear) are coalesced sweeps over them.
+//
+// History cell, FP32 (32 B): [0,16) {c r, c g, c b, N}, [16,20) fingerprint.
+// History cell, FP16 (16 B): [0,8) {half r, half g, half b, uint16 N}, [8,12) fp.
+// After the blend the cell's acc holds the blended value {c r, c g, c b, N}.
 struct TableDev {
-  unsigned char* cells;   // [T] frame cells
-  unsigned char* hcells;  // [Th] history cells (temporal tables)
-  uint32_t* dirty;        // [T] cells claimed this frame (split path)
+  unsigned long long* slots;  // [T] index of the hashed table
+  float4* acc;                // [D] FP32 accumulators (FP32 mode)
+  unsigned long long* acc64;  // [D][4] fixed-point accumulators (fixed mode)
+  uint4* info;                // [D] {slot, h1, fingerprint, history cell}
+  uint32_t* bcount;           // [blocks] cells claimed per id block
+  unsigned char* hcells;      // [Th] history cells (temporal tables)
   Ctrl* ctrl;
-  uint32_t stride;        // bytes per frame cell: 32 or 64
-  uint32_t fp_off;        // fingerprint offset in a frame cell: 16 or 32
-  uint32_t hstride;       // bytes per history cell: 32 or 16
-  uint32_t hfp_off;       // fingerprint offset in a history cell: 16 or 8
-  uint32_t mask;          // T - 1
-  uint32_t hmask;         // Th - 1
+  uint32_t hstride;           // bytes per history cell: 32 or 16
+  uint32_t hfp_off;           // fingerprint offset in a history cell: 16 or 8
+  uint32_t mask;              // T - 1
+  uint32_t hmask;             // Th - 1
   uint32_t max_probes;
   uint32_t lowcount;
-  int fixed;              // accumulation mode
-  int hist_mode;          // 0 none, 1 FP32, 2 FP16
+  int fixed;                  // accumulation mode
+  int hist_mode;              // 0 none, 1 FP32, 2 FP16
 };
+
+constexpr uint32_t kNoSlot = 0xFFFFFFFFu;  // info.x of an id reserved but not used
 
 struct VertexPtrs {
   const float *px, *py, *pz, *nx, *ny, *nz, *r, *g, *b;
@@ -187,7 +194,7 @@ __device__ __forceinline__ Key vertex_key(const KeyConst& kc, float px, float py
     const float w = __fsub_rn(__fmul_rn(__uint2float_rn(rnd.y >> 8), 0x1p-24f), 0.5f);
     // tangent frame after Duff et al. (JCGT 2017)
     const float s = copysignf(1.0f, nz);
-    const float a = __fdiv_rn(-1.0f, __fadd_rn(s, nz));
+    const float a = -__frcp_rn(__fadd_rn(s, nz));  // = -1 / (s + nz), correctly rounded
     const float q = __fmul_rn(__fmul_rn(nx, ny), a);
     const float tx = __fadd_rn(1.0f, __fmul_rn(s, __fmul_rn(__fmul_rn(nx, nx), a)));
     const float ty = __fmul_rn(s, q);
@@ -229,91 +236,111 @@ __device__ __forceinline__ Key vertex_key(const KeyConst& kc, float px, float py
 }
 
 // ---------------------------------------------------------------- memory helpers
-__device__ __forceinline__ void red_add_v4(float* p, float a, float b, float c, float d) {
+__device__ __forceinline__ void red_add_v4(float4* p, float a, float b, float c, float d) {
   asm volatile("red.relaxed.gpu.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a),
                "f"(b), "f"(c), "f"(d)
                : "memory");
+}
+
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
 }
 
 __device__ __forceinline__ long long to_fixed(float v) {
   return __float2ll_rn(__fmul_rn(v, 16777216.0f));  // round(v * 2^24), exact product
 }
 
-__device__ __forceinline__ unsigned char* frame_cell(const TableDev& t, uint32_t s) {
-  return t.cells + static_cast<size_t>(s) * t.stride;
+__device__ __forceinline__ unsigned long long slot_word(uint32_t f, uint32_t id) {
+  return (static_cast<unsigned long long>(id + 1u) << 32) | f;
 }
-__device__ __forceinline__ uint32_t* frame_fp(const TableDev& t, uint32_t s) {
-  return reinterpret_cast<uint32_t*>(frame_cell(t, s) + t.fp_off);
+__device__ __forceinline__ uint32_t slot_fp(unsigned long long w) {
+  return static_cast<uint32_t>(w);
 }
-__device__ __forceinline__ uint32_t* frame_hslot(const TableDev& t, uint32_t s) {
-  return frame_fp(t, s) + 1;
-}
-__device__ __forceinline__ float4* frame_value(const TableDev& t, uint32_t s) {
-  return reinterpret_cast<float4*>(frame_cell(t, s));
-}
-__device__ __forceinline__ unsigned char* hist_cell(const TableDev& t, uint32_t h) {
-  return t.hcells + static_cast<size_t>(h) * t.hstride;
-}
-__device__ __forceinline__ uint32_t* hist_fp(const TableDev& t, uint32_t h) {
-  return reinterpret_cast<uint32_t*>(hist_cell(t, h) + t.hfp_off);
+__device__ __forceinline__ uint32_t slot_id(unsigned long long w) {
+  return static_cast<uint32_t>(w >> 32) - 1u;
 }
 
-// Linear probing on the fingerprint word (Sec. 3.2): one compare-and-swap per
-// step publishes f into an empty cell or reports the cell's key; a cell holding
-// f is a hit, any other key moves the probe on.  Fingerprints are published,
-// never moved, within a frame, so a key present in the window is met before any
-// empty cell.  The first step (p = 0) is issued by the caller for several
-// vertices at once; this continues from step p0.  kOverflowSlot after P steps.
-struct ProbeTable {
-  unsigned char* base;
-  uint32_t stride, fp_off, mask, P;
-};
+// One probe step in the hashed table (Sec. 3.2, linear probing on the
+// fingerprint): `w` is the word read at the slot.  A slot holding f is a hit; an
+// empty slot is claimed with one 64-bit compare-and-swap that publishes the
+// fingerprint and the cell id together (so a reader never sees a fingerprint
+// without its cell); a slot holding another key moves the probe on.  Words are
+// only ever published, never changed, within a frame, so a key present in the
+// window is met before any empty slot.
+enum ProbeOutcome { kHit, kClaimed, kNext };
 
-__device__ __forceinline__ uint32_t* probe_fp(const ProbeTable& pt, uint32_t s) {
-  return reinterpret_cast<uint32_t*>(pt.base + static_cast<size_t>(s) * pt.stride + pt.fp_off);
-}
-
-__device__ __forceinline__ uint32_t probe_insert_from(const ProbeTable& pt, uint32_t home,
-                                                      uint32_t f, uint32_t p0, bool& claimed) {
-  claimed = false;
-  for (uint32_t p = p0; p < pt.P; ++p) {
-    const uint32_t s = (home + p) & pt.mask;
-    const uint32_t old = atomicCAS(probe_fp(pt, s), 0u, f);
-    if (old == 0u) {
-      claimed = true;
-      return s;
+__device__ __forceinline__ ProbeOutcome probe_step(unsigned long long* slot, unsigned long long w,
+                                                   uint32_t f, uint32_t my_id, uint32_t& id) {
+  if (w != 0ull) {
+    if (slot_fp(w) == f) {
+      id = slot_id(w);
+      return kHit;
     }
-    if (old == f) return s;
+    return kNext;
+  }
+  const unsigned long long old = atomicCAS(slot, 0ull, slot_word(f, my_id));
+  if (old == 0ull) {
+    id = my_id;
+    return kClaimed;
+  }
+  if (slot_fp(old) == f) {
+    id = slot_id(old);
+    return kHit;
+  }
+  return kNext;
+}
+
+// The rest of a probe sequence, one step at a time, from step p0.  Returns the
+// slot (kOverflowSlot after P steps) and the cell id through `id`.
+__device__ __forceinline__ uint32_t probe_rest(const TableDev& t, uint32_t home, uint32_t f,
+                                               uint32_t p0, uint32_t my_id, uint32_t& id,
+                                               bool& claimed) {
+  claimed = false;
+  for (uint32_t p = p0; p < t.max_probes; ++p) {
+    const uint32_t s = (home + p) & t.mask;
+    const ProbeOutcome o = probe_step(t.slots + s, ld_relaxed_u64(t.slots + s), f, my_id, id);
+    if (o == kNext) continue;
+    claimed = o == kClaimed;
+    return s;
   }
   return kOverflowSlot;
 }
 
-// Read-only probe (query without a stored slot index).
+// Read-only lookup of a key's cell id (query without a stored id).
 __device__ __forceinline__ uint32_t probe_find(const TableDev& t, uint32_t home, uint32_t f) {
   for (uint32_t p = 0; p < t.max_probes; ++p) {
-    const uint32_t s = (home + p) & t.mask;
-    const uint32_t cur = __ldcg(frame_fp(t, s));
-    if (cur == f) return s;
-    if (cur == 0u) return kOverflowSlot;
+    const unsigned long long w = __ldcg(t.slots + ((home + p) & t.mask));
+    if (w == 0ull) return kOverflowSlot;
+    if (slot_fp(w) == f) return slot_id(w);
   }
   return kOverflowSlot;
 }
 
-__device__ __forceinline__ ProbeTable frame_probe(const TableDev& t) {
-  return ProbeTable{t.cells, t.stride, t.fp_off, t.mask, t.max_probes};
-}
-__device__ __forceinline__ ProbeTable hist_probe(const TableDev& t) {
-  return ProbeTable{t.hcells, t.hstride, t.hfp_off, t.hmask, t.max_probes};
+// History table probing: 32-bit compare-and-swap on the history fingerprint.
+__device__ __forceinline__ uint32_t* hist_fp(const TableDev& t, uint32_t h) {
+  return reinterpret_cast<uint32_t*>(t.hcells + static_cast<size_t>(h) * t.hstride + t.hfp_off);
 }
 
-// Accumulate a group of `cnt` contributions (sums r, g, b) into cell s.
-__device__ __forceinline__ void accumulate(const TableDev& t, uint32_t s, float r, float g, float b,
+__device__ __forceinline__ uint32_t hist_probe_rest(const TableDev& t, uint32_t home, uint32_t f,
+                                                    uint32_t p0) {
+  for (uint32_t p = p0; p < t.max_probes; ++p) {
+    const uint32_t h = (home + p) & t.hmask;
+    const uint32_t old = atomicCAS(hist_fp(t, h), 0u, f);
+    if (old == 0u || old == f) return h;
+  }
+  return kOverflowSlot;
+}
+
+// Accumulate a group of `cnt` contributions (sums r, g, b) into cell `id`.
+__device__ __forceinline__ void accumulate(const TableDev& t, uint32_t id, float r, float g, float b,
                                            long long fr, long long fg, long long fb, uint32_t cnt) {
   if (!t.fixed) {
-    red_add_v4(reinterpret_cast<float*>(frame_cell(t, s)), r, g, b, static_cast<float>(cnt));
+    red_add_v4(t.acc + id, r, g, b, static_cast<float>(cnt));
     return;
   }
-  unsigned long long* a = reinterpret_cast<unsigned long long*>(frame_cell(t, s));
+  unsigned long long* a = t.acc64 + 4 * static_cast<size_t>(id);
   atomicAdd(a + 0, static_cast<unsigned long long>(fr));
   atomicAdd(a + 1, static_cast<unsigned long long>(fg));
   atomicAdd(a + 2, static_cast<unsigned long long>(fb));
@@ -333,9 +360,13 @@ struct AccRaw {
   float4 hi;  // fixed mode: int64 sum b and count as bits
 };
 
-__device__ __forceinline__ AccRaw load_acc(const TableDev& t, uint32_t s) {
+__device__ __forceinline__ float4* value_ptr(const TableDev& t, uint32_t id) {
+  return t.fixed ? reinterpret_cast<float4*>(t.acc64 + 4 * static_cast<size_t>(id)) : t.acc + id;
+}
+
+__device__ __forceinline__ AccRaw load_acc(const TableDev& t, uint32_t id) {
   AccRaw a;
-  const float4* p = frame_value(t, s);
+  const float4* p = value_ptr(t, id);
   a.lo = __ldcg(p);
   a.hi = t.fixed ? __ldcg(p + 1) : make_float4(0.f, 0.f, 0.f, 0.f);
   return a;
@@ -374,14 +405,15 @@ struct HistRaw {
 
 __device__ __forceinline__ HistRaw load_hist(const TableDev& t, uint32_t h) {
   HistRaw o;
+  const unsigned char* c = t.hcells + static_cast<size_t>(h) * t.hstride;
   if (t.hist_mode == 1) {
-    const float4 v = __ldcg(reinterpret_cast<const float4*>(hist_cell(t, h)));
+    const float4 v = __ldcg(reinterpret_cast<const float4*>(c));
     o.r = v.x;
     o.g = v.y;
     o.b = v.z;
     o.n = __float_as_uint(v.w);
   } else {
-    const uint2 v = __ldcg(reinterpret_cast<const uint2*>(hist_cell(t, h)));
+    const uint2 v = __ldcg(reinterpret_cast<const uint2*>(c));
     const float2 rg = __half22float2(*reinterpret_cast<const __half2*>(&v.x));
     o.r = rg.x;
     o.g = rg.y;
@@ -391,13 +423,12 @@ __device__ __forceinline__ HistRaw load_hist(const TableDev& t, uint32_t h) {
   return o;
 }
 
-// Temporal filtering / integration of one cell (Sec. 3.4.1), run once per
-// claimed frame cell by its owner: c = alpha c_old + (1 - alpha) c_new, where
-// alpha < 0 means alpha = N_old / (N_old + N_new); no history -> c = c_new.
-// The history cell `h` is updated (h == kOverflowSlot: the history window was
-// full, the cell keeps c_new and N = N_new) and the result is left in the
-// frame cell s for the lookups of this frame.
-__device__ __forceinline__ void blend_store(const TableDev& t, uint32_t s, uint32_t h,
+// Temporal filtering / integration of one cell (Sec. 3.4.1):
+// c = alpha c_old + (1 - alpha) c_new, alpha < 0 meaning alpha = N_old / (N_old +
+// N_new); no history -> c = c_new.  The history cell h is updated (h ==
+// kOverflowSlot: the history window was full; the cell keeps c_new and
+// N = N_new) and the result replaces the cell's accumulator for the lookups.
+__device__ __forceinline__ void blend_store(const TableDev& t, uint32_t id, uint32_t h,
                                             const CellMean& m, const HistRaw& old, float alpha) {
   float cr = m.r, cg = m.g, cb = m.b;
   uint32_t N = m.n;
@@ -412,16 +443,17 @@ __device__ __forceinline__ void blend_store(const TableDev& t, uint32_t s, uint3
       cg = __fadd_rn(__fmul_rn(a, old.g), __fmul_rn(a1, cg));
       cb = __fadd_rn(__fmul_rn(a, old.b), __fmul_rn(a1, cb));
     }
+    unsigned char* c = t.hcells + static_cast<size_t>(h) * t.hstride;
     if (t.hist_mode == 1) {
       N = old.n + m.n;
-      __stcg(reinterpret_cast<float4*>(hist_cell(t, h)), make_float4(cr, cg, cb, __uint_as_float(N)));
+      __stcg(reinterpret_cast<float4*>(c), make_float4(cr, cg, cb, __uint_as_float(N)));
     } else {
       N = min(old.n + m.n, 65535u);
       const __half2 rg = __floats2half2_rn(cr, cg);
       const __half hb = __float2half_rn(cb);
       const uint32_t lo = *reinterpret_cast<const uint32_t*>(&rg);
       const uint32_t hi = static_cast<uint32_t>(__half_as_ushort(hb)) | (N << 16);
-      __stcg(reinterpret_cast<uint2*>(hist_cell(t, h)), make_uint2(lo, hi));
+      __stcg(reinterpret_cast<uint2*>(c), make_uint2(lo, hi));
       // lookups see what the history stores
       const float2 back = __half22float2(rg);
       cr = back.x;
@@ -429,19 +461,10 @@ __device__ __forceinline__ void blend_store(const TableDev& t, uint32_t s, uint3
       cb = __half2float(hb);
     }
   }
-  __stcg(frame_value(t, s), make_float4(cr, cg, cb, __uint_as_float(N)));
+  __stcg(value_ptr(t, id), make_float4(cr, cg, cb, __uint_as_float(N)));
 }
 
-// Blend one cell (loads and all); used where cells are visited one at a time.
-__device__ __forceinline__ void blend_cell(const TableDev& t, uint32_t s, float alpha) {
-  const AccRaw a = load_acc(t, s);
-  const uint32_t h = __ldcg(frame_hslot(t, s));
-  HistRaw old{0.f, 0.f, 0.f, 0u};
-  if (h != kOverflowSlot) old = load_hist(t, h);
-  blend_store(t, s, h, mean_of(t, a), old, alpha);
-}
-
-// Value returned for cell s: the cell average, or the blended value.
+// Value returned for cell `id`: the cell average, or the blended value.
 __device__ __forceinline__ CellMean value_of(const TableDev& t, const AccRaw& a, bool blended) {
   if (!blended) return mean_of(t, a);
   CellMean m;
@@ -452,21 +475,21 @@ __device__ __forceinline__ CellMean value_of(const TableDev& t, const AccRaw& a,
   return m;
 }
 
-__device__ __forceinline__ AccRaw load_value(const TableDev& t, uint32_t s, bool blended) {
-  if (!blended) return load_acc(t, s);
+__device__ __forceinline__ AccRaw load_value(const TableDev& t, uint32_t id, bool blended) {
+  if (!blended) return load_acc(t, id);
   AccRaw a;
-  a.lo = __ldcg(frame_value(t, s));
+  a.lo = __ldcg(value_ptr(t, id));
   a.hi = make_float4(0.f, 0.f, 0.f, 0.f);
   return a;
 }
 
-// Empty a frame cell (fingerprint and accumulator) for the next frame.
-__device__ __forceinline__ void clear_cell(const TableDev& t, uint32_t s) {
-  float4* p = frame_value(t, s);
+// Empty cell `id` (its accumulator and its slot) for the next frame.
+__device__ __forceinline__ void clear_cell(const TableDev& t, uint32_t id, uint32_t slot) {
   const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+  float4* p = value_ptr(t, id);
   __stcg(p, z);
-  __stcg(p + 1, z);  // FP32: fingerprint, history link, padding; fixed: sum b, count
-  if (t.fixed) __stcg(frame_fp(t, s), 0u);
+  if (t.fixed) __stcg(p + 1, z);
+  if (slot != kNoSlot) __stcg(t.slots + slot, 0ull);
 }
 
 // ---------------------------------------------------------------- grid barrier

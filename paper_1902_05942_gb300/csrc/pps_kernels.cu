@@ -1,19 +1,21 @@
 // Kernels of the hashed path space filter (sm_103a) and their launchers.
 //
 //  k_insert        key construction (Alg. 1) + probing insert + atomic
-//                  accumulation (Sec. 3.2, 3.3.1); appends touched cells to the
-//                  frame's dirty list.
-//  k_blend         temporal blend over the dirty list (Sec. 3.4.1).
+//                  accumulation (Sec. 3.2, 3.3.1) for one tile of vertices per
+//                  CTA iteration; a tile's new cells get ids from the tile's
+//                  own id range.
+//  k_blend_sweep   temporal blend of every cell claimed this frame (Sec. 3.4.1).
 //  k_query         one lookup per vertex: cell average or blended value.
-//  k_clear_dirty   empties the cells of the dirty list for the next frame.
+//  k_clear_sweep   empties the frame's cells for the next frame.
 //  k_fused         the whole frame in one persistent cooperative launch: the
 //                  four steps above separated by grid barriers; each vertex's
-//                  cell index stays in shared memory between the phases.
+//                  cell id stays in shared memory between the phases and each
+//                  CTA blends and clears the cells it created.
 //
 // Vertex streams are read four consecutive vertices per thread with 128-bit
 // streaming loads (ld.global.cs) when the arrays are 16-byte aligned; table
-// words are read at L2 (ld.global.cg) because they are written by atomics and
-// by other CTAs.
+// words are read at L2 (ld.relaxed.gpu / ld.global.cg) because other CTAs
+// write them.
 #include <algorithm>
 
 #include "pps_internal.h"
@@ -22,8 +24,33 @@ namespace pps {
 
 namespace {
 
-constexpr int kBlock = 256;        // split kernels
-constexpr int kFusedBlock = 512;   // persistent kernel
+constexpr int kBlock = 256;            // split kernels
+constexpr int kTile = kBlock * 4;      // vertices (and cell ids) per split-path tile
+constexpr int kFusedBlock = 512;       // persistent kernel
+constexpr int kFusedTile = kFusedBlock * 4;  // vertices per persistent-kernel tile
+constexpr int kMaxTilesPerCta = 1024;  // tile list of one persistent CTA
+
+// W consecutive floats of one stream (one 8- or 16-byte load when aligned).
+template <int W>
+__device__ __forceinline__ void loadw(float (&x)[W], const float* p, size_t j, size_t end,
+                                      bool vec) {
+  if (vec && j + W <= end) {
+    if constexpr (W == 4) {
+      const float4 v = __ldcs(reinterpret_cast<const float4*>(p + j));
+      x[0] = v.x;
+      x[1] = v.y;
+      x[2] = v.z;
+      x[3] = v.w;
+    } else {
+      const float2 v = __ldcs(reinterpret_cast<const float2*>(p + j));
+      x[0] = v.x;
+      x[1] = v.y;
+    }
+    return;
+  }
+#pragma unroll
+  for (int q = 0; q < W; ++q) x[q] = j + q < end ? __ldcs(p + j + q) : 0.f;
+}
 
 __device__ __forceinline__ float4 load4(const float* p, size_t j, size_t end, bool vec) {
   if (vec && j + 4 <= end) return __ldcs(reinterpret_cast<const float4*>(p + j));
@@ -57,39 +84,80 @@ __device__ __forceinline__ T block_sum(T x) {
   return tot;  // valid in thread 0
 }
 
-// Insert the four vertices j..j+3 (those below `end`).  Returns their cell
-// indices (kOverflowSlot on probe overflow) and which of them own their cell
-// this frame (published its fingerprint).  Owners of a temporal table also
-// link their cell to its history cell.
-//
-// The four vertices go through each step together so that their memory
-// operations overlap: keys; merging of equal keys among the four (their
-// contributions are summed in registers and sent with one atomic); the first
-// probe of every distinct key (four compare-and-swaps in flight); the rare
-// longer probes; the accumulating reds; and the owners' history probes.
-struct Four {
-  uint32_t slot[4];
-  bool owner[4];
+struct Counters {
+  unsigned long long ovf = 0, cells = 0;
 };
 
-__device__ __forceinline__ Four insert_four(const KeyConst& kc, const TableDev& t,
-                                            const VertexPtrs& v, size_t j, size_t end, bool vec,
-                                            unsigned long long& n_ovf, unsigned long long& n_cells,
-                                            unsigned long long& n_hovf) {
-  const float4 PX = load4(v.px, j, end, vec), PY = load4(v.py, j, end, vec),
-               PZ = load4(v.pz, j, end, vec);
-  const float4 NX = load4(v.nx, j, end, vec), NY = load4(v.ny, j, end, vec),
-               NZ = load4(v.nz, j, end, vec);
-  uint32_t h1[4], f[4];
-  bool lead[4];
-  int of[4];
+// The rare continuation of a probe whose home slot held another key, kept out
+// of line so that the four-wide insert stays fully unrolled in registers.
+// `my` is the id reserved for this key (kOverflowSlot: none yet).
+struct MoreProbe {
+  uint32_t slot, id, my;
+  bool claimed;
+};
+
+__device__ __noinline__ MoreProbe probe_more(unsigned long long* slots, uint32_t mask,
+                                             uint32_t max_probes, uint32_t home, uint32_t f,
+                                             uint32_t my, uint32_t id_base, uint32_t* claims) {
+  MoreProbe r{kOverflowSlot, kOverflowSlot, my, false};
+  for (uint32_t p = 1; p < max_probes; ++p) {
+    const uint32_t s = (home + p) & mask;
+    unsigned long long w = ld_relaxed_u64(slots + s);
+    if (w == 0ull) {
+      if (r.my == kOverflowSlot) r.my = id_base + atomicAdd(claims, 1u);
+      w = atomicCAS(slots + s, 0ull, slot_word(f, r.my));
+      if (w == 0ull) {
+        r.slot = s;
+        r.id = r.my;
+        r.claimed = true;
+        return r;
+      }
+    }
+    if (slot_fp(w) == f) {
+      r.slot = s;
+      r.id = slot_id(w);
+      return r;
+    }
+  }
+  return r;
+}
+
+// Insert the W vertices j..j+W-1 (those below `end`) and return their cell
+// ids (kOverflowSlot on probe overflow).  New cells take ids id_base + k, k
+// drawn from the tile's claim counter *claims (shared memory).
+//
+// The W vertices go through each step together so that their memory
+// operations overlap: keys; merging of equal keys among them (their
+// contributions are summed in registers and sent with one atomic); the first
+// probe of every distinct key (W loads in flight, then the compare-and-swaps
+// for empty slots); the rare longer probes; the accumulating reductions.
+template <int W>
+struct Batch {
+  uint32_t id[W];
+};
+
+template <int W>
+__device__ __forceinline__ Batch<W> insert_batch(const KeyConst& kc, const TableDev& t,
+                                                 const VertexPtrs& v, size_t j, size_t end,
+                                                 bool vec, uint32_t id_base, uint32_t* claims,
+                                                 Counters& cnt_out) {
+  float PX[W], PY[W], PZ[W], NX[W], NY[W], NZ[W];
+  loadw<W>(PX, v.px, j, end, vec);
+  loadw<W>(PY, v.py, j, end, vec);
+  loadw<W>(PZ, v.pz, j, end, vec);
+  loadw<W>(NX, v.nx, j, end, vec);
+  loadw<W>(NY, v.ny, j, end, vec);
+  loadw<W>(NZ, v.nz, j, end, vec);
+  uint32_t h1[W], f[W];
+  bool lead[W];
+  int of[W];
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
+  for (int q = 0; q < W; ++q) {
     const bool valid = j + q < end;
     Key k{0u, 0u};
     if (valid)
-      k = vertex_key(kc, comp(PX, q), comp(PY, q), comp(PZ, q), comp(NX, q), comp(NY, q),
-                     comp(NZ, q), vertex_id(v, j + q), v.stream_id);
+      k = vertex_key(kc, PX[q], PY[q], PZ[q], NX[q], NY[q], NZ[q], vertex_id(v, j + q),
+                     v.stream_id);
     h1[q] = k.h1;
     f[q] = k.fp;  // 0 marks an absent vertex (fingerprints are never 0)
     lead[q] = valid;
@@ -97,107 +165,107 @@ __device__ __forceinline__ Four insert_four(const KeyConst& kc, const TableDev& 
   }
   // merge equal keys: a later vertex joins the first earlier one with its key
 #pragma unroll
-  for (int q = 1; q < 4; ++q) {
+  for (int q = 1; q < W; ++q) {
 #pragma unroll
     for (int p = 0; p < q; ++p) {
-      if (lead[q] && lead[p] && of[q] == q && h1[p] == h1[q] && f[p] == f[q]) {
+      if (lead[q] && lead[p] && h1[p] == h1[q] && f[p] == f[q]) {
         lead[q] = false;
         of[q] = p;
       }
     }
   }
-  const float4 R = load4(v.r, j, end, vec), G = load4(v.g, j, end, vec),
-               B = load4(v.b, j, end, vec);
-  float sr[4], sg[4], sb[4];
-  long long fr[4], fg[4], fb[4];
-  uint32_t cnt[4];
+  float rr[W], rg[W], rb[W];
+  loadw<W>(rr, v.r, j, end, vec);
+  loadw<W>(rg, v.g, j, end, vec);
+  loadw<W>(rb, v.b, j, end, vec);
+  long long xr[W], xg[W], xb[W];
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    sr[q] = 0.f;
-    sg[q] = 0.f;
-    sb[q] = 0.f;
-    fr[q] = fg[q] = fb[q] = 0;
-    cnt[q] = 0u;
+  for (int q = 0; q < W; ++q) {
+    xr[q] = t.fixed ? to_fixed(rr[q]) : 0;
+    xg[q] = t.fixed ? to_fixed(rg[q]) : 0;
+    xb[q] = t.fixed ? to_fixed(rb[q]) : 0;
   }
-  // (static indices only: both loops unroll completely)
+  // group sums of each leader p over its members q >= p (static bounds, selects)
+  float sr[W], sg[W], sb[W];
+  long long fr[W], fg[W], fb[W];
+  uint32_t cnt[W];
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const bool use = f[q] != 0u;
-    const float r = use ? comp(R, q) : 0.f, g = use ? comp(G, q) : 0.f, b = use ? comp(B, q) : 0.f;
-    long long xr = 0, xg = 0, xb = 0;
-    if (t.fixed) {
-      xr = to_fixed(r);
-      xg = to_fixed(g);
-      xb = to_fixed(b);
-    }
+  for (int p = 0; p < W; ++p) {
+    sr[p] = sg[p] = sb[p] = 0.f;
+    fr[p] = fg[p] = fb[p] = 0;
+    cnt[p] = 0u;
 #pragma unroll
-    for (int p = 0; p <= q; ++p) {
-      if (!use || of[q] != p) continue;
-      sr[p] = __fadd_rn(sr[p], r);
-      sg[p] = __fadd_rn(sg[p], g);
-      sb[p] = __fadd_rn(sb[p], b);
-      fr[p] += xr;
-      fg[p] += xg;
-      fb[p] += xb;
-      ++cnt[p];
+    for (int q = p; q < W; ++q) {
+      const bool m = f[q] != 0u && of[q] == p;
+      sr[p] = m ? __fadd_rn(sr[p], rr[q]) : sr[p];
+      sg[p] = m ? __fadd_rn(sg[p], rg[q]) : sg[p];
+      sb[p] = m ? __fadd_rn(sb[p], rb[q]) : sb[p];
+      fr[p] += m ? xr[q] : 0;
+      fg[p] += m ? xg[q] : 0;
+      fb[p] += m ? xb[q] : 0;
+      cnt[p] += m ? 1u : 0u;
     }
   }
-  // first probe of every distinct key, all in flight together
-  const ProbeTable fpt = frame_probe(t);
-  uint32_t old[4];
+  // first probe step of every distinct key: loads in flight together
+  unsigned long long w[W];
 #pragma unroll
-  for (int q = 0; q < 4; ++q)
-    old[q] = lead[q] ? atomicCAS(probe_fp(fpt, h1[q] & t.mask), 0u, f[q]) : 0u;
-  uint32_t slot[4];
-  bool claimed[4];
+  for (int q = 0; q < W; ++q)
+    w[q] = lead[q] ? ld_relaxed_u64(t.slots + (h1[q] & t.mask)) : 1ull;
+  // an empty home needs a cell id to publish with the fingerprint
+  uint32_t my[W];
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
+  for (int q = 0; q < W; ++q)
+    my[q] = lead[q] && w[q] == 0ull ? id_base + atomicAdd(claims, 1u) : kOverflowSlot;
+  unsigned long long old[W];
+#pragma unroll
+  for (int q = 0; q < W; ++q)
+    old[q] = my[q] != kOverflowSlot
+                 ? atomicCAS(t.slots + (h1[q] & t.mask), 0ull, slot_word(f[q], my[q]))
+                 : w[q];
+  uint32_t id[W], slot[W];
+  bool claimed[W];
+#pragma unroll
+  for (int q = 0; q < W; ++q) {
+    id[q] = kOverflowSlot;
     slot[q] = kOverflowSlot;
     claimed[q] = false;
     if (!lead[q]) continue;
-    if (old[q] == 0u || old[q] == f[q]) {
-      slot[q] = h1[q] & t.mask;
-      claimed[q] = old[q] == 0u;
+    const uint32_t home = h1[q] & t.mask;
+    if (my[q] != kOverflowSlot && old[q] == 0ull) {
+      id[q] = my[q];
+      slot[q] = home;
+      claimed[q] = true;
+    } else if (slot_fp(old[q]) == f[q]) {
+      id[q] = slot_id(old[q]);
+      slot[q] = home;
     } else {
-      bool c;
-      slot[q] = probe_insert_from(fpt, h1[q] & t.mask, f[q], 1u, c);
-      claimed[q] = c;
+      // the home slot holds another key: keep probing (rare at low load)
+      const MoreProbe m = probe_more(t.slots, t.mask, t.max_probes, home, f[q], my[q], id_base,
+                                     claims);
+      slot[q] = m.slot;
+      id[q] = m.id;
+      my[q] = m.my;
+      claimed[q] = m.claimed;
     }
+    // record the cell, or mark a reserved id that ended up unused
+    if (my[q] != kOverflowSlot)
+      __stcg(t.info + my[q], claimed[q] ? make_uint4(slot[q], h1[q], f[q], kOverflowSlot)
+                                        : make_uint4(kNoSlot, 0u, 0u, kOverflowSlot));
   }
 #pragma unroll
-  for (int q = 0; q < 4; ++q)
-    if (lead[q] && slot[q] != kOverflowSlot)
-      accumulate(t, slot[q], sr[q], sg[q], sb[q], fr[q], fg[q], fb[q], cnt[q]);
-  // owners of a temporal table find or claim their history cell
-  if (t.hist_mode) {
-    const ProbeTable hpt = hist_probe(t);
-    uint32_t hold[4];
+  for (int q = 0; q < W; ++q)
+    if (lead[q] && id[q] != kOverflowSlot)
+      accumulate(t, id[q], sr[q], sg[q], sb[q], fr[q], fg[q], fb[q], cnt[q]);
+  Batch<W> out;
 #pragma unroll
-    for (int q = 0; q < 4; ++q)
-      hold[q] = claimed[q] ? atomicCAS(probe_fp(hpt, h1[q] & t.hmask), 0u, f[q]) : 0u;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      if (!claimed[q]) continue;
-      uint32_t h = h1[q] & t.hmask;
-      if (hold[q] != 0u && hold[q] != f[q]) {
-        bool hc;
-        h = probe_insert_from(hpt, h1[q] & t.hmask, f[q], 1u, hc);
-      }
-      n_hovf += h == kOverflowSlot ? 1ull : 0ull;
-      __stcg(frame_hslot(t, slot[q]), h);
-    }
-  }
-  Four out;
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    uint32_t sl = slot[0];
+  for (int q = 0; q < W; ++q) {
+    uint32_t d = id[0];
 #pragma unroll
     for (int p = 1; p <= q; ++p)
-      if (of[q] == p) sl = slot[p];
-    out.slot[q] = f[q] == 0u ? kOverflowSlot : sl;
-    out.owner[q] = claimed[q];
-    if (f[q] != 0u && out.slot[q] == kOverflowSlot) ++n_ovf;
-    n_cells += claimed[q] ? 1ull : 0ull;
+      if (of[q] == p) d = id[p];
+    out.id[q] = f[q] == 0u ? kOverflowSlot : d;
+    if (f[q] != 0u && out.id[q] == kOverflowSlot) ++cnt_out.ovf;
+    cnt_out.cells += claimed[q] ? 1ull : 0ull;
   }
   return out;
 }
@@ -208,20 +276,21 @@ struct Result {
   uint8_t status;
 };
 
-// Look up the four cells s[0..3] (loads issued together) and resolve each
-// vertex: cell average / blended value, or its own contribution on overflow.
-__device__ __forceinline__ void resolve_four(const TableDev& t, const VertexPtrs& v, size_t j,
-                                             size_t end, const uint32_t (&s)[4], bool blended,
-                                             Result (&res)[4]) {
-  AccRaw a[4];
+// Look up the cells id[0..W-1] (loads issued together) and resolve each vertex:
+// cell average / blended value, or its own contribution on overflow.
+template <int W>
+__device__ __forceinline__ void resolve_batch(const TableDev& t, const VertexPtrs& v, size_t j,
+                                              size_t end, const uint32_t (&id)[W], bool blended,
+                                              Result (&res)[W]) {
+  AccRaw a[W];
 #pragma unroll
-  for (int q = 0; q < 4; ++q)
-    if (j + q < end && s[q] != kOverflowSlot) a[q] = load_value(t, s[q], blended);
+  for (int q = 0; q < W; ++q)
+    if (j + q < end && id[q] != kOverflowSlot) a[q] = load_value(t, id[q], blended);
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
+  for (int q = 0; q < W; ++q) {
     res[q] = Result{0.f, 0.f, 0.f, 0u, 0};
     if (j + q >= end) continue;
-    if (s[q] == kOverflowSlot) {
+    if (id[q] == kOverflowSlot) {
       // probe limit exceeded: the unfiltered contribution of the vertex itself
       res[q].r = __ldcs(v.r + j + q);
       res[q].g = __ldcs(v.g + j + q);
@@ -238,45 +307,36 @@ __device__ __forceinline__ void resolve_four(const TableDev& t, const VertexPtrs
   }
 }
 
-// Blend the owned cells among four stash entries, loads issued together.
-__device__ __forceinline__ void blend_four(const TableDev& t, const uint32_t (&s)[4],
-                                           const bool (&own)[4], float alpha) {
-  AccRaw a[4];
-  uint32_t h[4];
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    if (!own[q]) continue;
-    a[q] = load_acc(t, s[q]);
-    h[q] = __ldcg(frame_hslot(t, s[q]));
-  }
-  HistRaw old[4];
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    old[q] = HistRaw{0.f, 0.f, 0.f, 0u};
-    if (own[q] && h[q] != kOverflowSlot) old[q] = load_hist(t, h[q]);
-  }
-#pragma unroll
-  for (int q = 0; q < 4; ++q)
-    if (own[q]) blend_store(t, s[q], h[q], mean_of(t, a[q]), old[q], alpha);
-}
-
-__device__ __forceinline__ void store_four(const OutPtrs& o, size_t j, size_t end, bool vec,
-                                           const Result (&res)[4]) {
-  if (vec && j + 4 <= end) {
-    __stcs(reinterpret_cast<float4*>(o.r + j), make_float4(res[0].r, res[1].r, res[2].r, res[3].r));
-    __stcs(reinterpret_cast<float4*>(o.g + j), make_float4(res[0].g, res[1].g, res[2].g, res[3].g));
-    __stcs(reinterpret_cast<float4*>(o.b + j), make_float4(res[0].b, res[1].b, res[2].b, res[3].b));
-    if (o.count)
-      __stcs(reinterpret_cast<uint4*>(o.count + j), make_uint4(res[0].n, res[1].n, res[2].n, res[3].n));
-    if (o.status) {
-      const uint32_t w = res[0].status | (res[1].status << 8) | (res[2].status << 16) |
-                         (static_cast<uint32_t>(res[3].status) << 24);
-      __stcs(reinterpret_cast<unsigned int*>(o.status + j), w);
+template <int W>
+__device__ __forceinline__ void store_batch(const OutPtrs& o, size_t j, size_t end, bool vec,
+                                            const Result (&res)[W]) {
+  if (vec && j + W <= end) {
+    if constexpr (W == 4) {
+      __stcs(reinterpret_cast<float4*>(o.r + j), make_float4(res[0].r, res[1].r, res[2].r, res[3].r));
+      __stcs(reinterpret_cast<float4*>(o.g + j), make_float4(res[0].g, res[1].g, res[2].g, res[3].g));
+      __stcs(reinterpret_cast<float4*>(o.b + j), make_float4(res[0].b, res[1].b, res[2].b, res[3].b));
+      if (o.count)
+        __stcs(reinterpret_cast<uint4*>(o.count + j),
+               make_uint4(res[0].n, res[1].n, res[2].n, res[3].n));
+      if (o.status) {
+        const uint32_t w = res[0].status | (res[1].status << 8) | (res[2].status << 16) |
+                           (static_cast<uint32_t>(res[3].status) << 24);
+        __stcs(reinterpret_cast<unsigned int*>(o.status + j), w);
+      }
+    } else {
+      __stcs(reinterpret_cast<float2*>(o.r + j), make_float2(res[0].r, res[1].r));
+      __stcs(reinterpret_cast<float2*>(o.g + j), make_float2(res[0].g, res[1].g));
+      __stcs(reinterpret_cast<float2*>(o.b + j), make_float2(res[0].b, res[1].b));
+      if (o.count) __stcs(reinterpret_cast<uint2*>(o.count + j), make_uint2(res[0].n, res[1].n));
+      if (o.status) {
+        const unsigned short w = static_cast<unsigned short>(res[0].status | (res[1].status << 8));
+        __stcs(reinterpret_cast<unsigned short*>(o.status + j), w);
+      }
     }
     return;
   }
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
+  for (int q = 0; q < W; ++q) {
     if (j + q < end) {
       o.r[j + q] = res[q].r;
       o.g[j + q] = res[q].g;
@@ -287,54 +347,119 @@ __device__ __forceinline__ void store_four(const OutPtrs& o, size_t j, size_t en
   }
 }
 
-// ------------------------------------------------------------------ split path
-__global__ void __launch_bounds__(kBlock) k_insert(KeyConst kc, TableDev t, VertexPtrs v,
-                                                   size_t n, uint32_t* slot_out, int vec) {
-  __shared__ uint32_t s_cells[kBlock * 4];
-  __shared__ uint32_t s_count, s_base;
-  unsigned long long n_ovf = 0, n_cells = 0, n_hovf = 0;
-  const size_t ngroups = (n + 3) / 4;
-  const size_t tiles = (ngroups + kBlock - 1) / kBlock;
-  for (size_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
-    if (threadIdx.x == 0) s_count = 0;
-    __syncthreads();
-    const size_t j = (tile * kBlock + threadIdx.x) * 4;
-    if (j < n) {
-      const Four f = insert_four(kc, t, v, j, n, vec != 0, n_ovf, n_cells, n_hovf);
+// Blend the cells [base, base + count): each thread takes BW cells, one from
+// each of BW consecutive runs of `stride` ids (coalesced loads), and issues
+// their history probes together.  `first` is this thread's offset.
+template <int BW>
+__device__ __forceinline__ void blend_range(const TableDev& t, uint32_t base, uint32_t count,
+                                            uint32_t first, uint32_t stride, float alpha,
+                                            unsigned long long& n_hovf) {
+  for (uint32_t k0 = first; k0 < count; k0 += BW * stride) {
+    uint32_t d[BW], home[BW], f[BW], h[BW];
+    bool use[BW];
+    AccRaw a[BW];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        if (f.owner[q]) s_cells[atomicAdd(&s_count, 1u)] = f.slot[q];
-        if (slot_out && j + q < n) slot_out[j + q] = f.slot[q];
+    for (int q = 0; q < BW; ++q) {
+      const uint32_t k = k0 + q * stride;
+      d[q] = base + k;
+      use[q] = false;
+      home[q] = 0u;
+      f[q] = 0u;
+      if (k < count) {
+        const uint4 in = __ldcg(t.info + d[q]);
+        use[q] = in.x != kNoSlot;
+        home[q] = in.y & t.hmask;
+        f[q] = in.z;
+        if (use[q]) a[q] = load_acc(t, d[q]);
+      }
+    }
+    uint32_t old[BW];
+#pragma unroll
+    for (int q = 0; q < BW; ++q) old[q] = use[q] ? atomicCAS(hist_fp(t, home[q]), 0u, f[q]) : 0u;
+#pragma unroll
+    for (int q = 0; q < BW; ++q) {
+      h[q] = home[q];
+      if (use[q] && old[q] != 0u && old[q] != f[q]) h[q] = hist_probe_rest(t, home[q], f[q], 1u);
+      if (use[q] && h[q] == kOverflowSlot) ++n_hovf;
+    }
+    HistRaw hv[BW];
+#pragma unroll
+    for (int q = 0; q < BW; ++q) {
+      hv[q] = HistRaw{0.f, 0.f, 0.f, 0u};
+      if (use[q] && h[q] != kOverflowSlot) hv[q] = load_hist(t, h[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < BW; ++q)
+      if (use[q]) blend_store(t, d[q], h[q], mean_of(t, a[q]), hv[q], alpha);
+  }
+}
+
+// Empty the cells [base, base + count): their accumulators, and their slots
+// unless the whole slot table is swept separately (`slots_swept`).
+__device__ __forceinline__ void clear_range(const TableDev& t, uint32_t base, uint32_t count,
+                                            uint32_t first, uint32_t stride, bool slots_swept) {
+  for (uint32_t k = first; k < count; k += stride) {
+    const uint32_t slot = slots_swept ? kNoSlot : __ldcg(t.info + base + k).x;
+    clear_cell(t, base + k, slot);
+  }
+}
+
+// Zero the whole slot table with 16-byte stores, `gthreads` threads from
+// thread `gid`: cheaper than one scattered store per cell once a good share
+// of the table is in use.
+__device__ __forceinline__ void sweep_slots(const TableDev& t, size_t gid, size_t gthreads) {
+  uint4* p = reinterpret_cast<uint4*>(t.slots);
+  const size_t n16 = (static_cast<size_t>(t.mask) + 1) / 2;
+  for (size_t i = gid; i < n16; i += gthreads) __stcg(p + i, make_uint4(0u, 0u, 0u, 0u));
+}
+
+// ------------------------------------------------------------------ split path
+template <int W>
+__global__ void __launch_bounds__(kBlock) k_insert(KeyConst kc, TableDev t, VertexPtrs v,
+                                                   size_t n, uint32_t* id_out, int vec,
+                                                   uint32_t tile_base) {
+  __shared__ uint32_t s_claims;
+  Counters c;
+  const size_t tiles = (n + kTile - 1) / kTile;
+  for (size_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+    if (threadIdx.x == 0) s_claims = 0;
+    __syncthreads();
+    const uint32_t tix = tile_base + static_cast<uint32_t>(tile);
+#pragma unroll 1
+    for (int sub = 0; sub < 4; sub += W) {
+      const size_t j = tile * kTile + threadIdx.x * 4 + sub;
+      if (j < n) {
+        const Batch<W> b = insert_batch<W>(kc, t, v, j, n, vec != 0, tix * kTile, &s_claims, c);
+        if (id_out) {
+#pragma unroll
+          for (int q = 0; q < W; ++q)
+            if (j + q < n) id_out[j + q] = b.id[q];
+        }
       }
     }
     __syncthreads();
-    if (threadIdx.x == 0) s_base = s_count ? atomicAdd(&t.ctrl->dirty_count, s_count) : 0u;
-    __syncthreads();
-    for (uint32_t i = threadIdx.x; i < s_count; i += kBlock) t.dirty[s_base + i] = s_cells[i];
-    __syncthreads();
+    if (threadIdx.x == 0) t.bcount[tix] = s_claims;
   }
-  const unsigned long long a = block_sum(n_ovf);
-  const unsigned long long c = block_sum(n_cells);
-  const unsigned long long h = block_sum(n_hovf);
+  const unsigned long long a = block_sum(c.ovf);
+  const unsigned long long b = block_sum(c.cells);
   if (threadIdx.x == 0) {
     if (a) atomicAdd(&t.ctrl->overflow_vertices, a);
-    if (c) atomicAdd(&t.ctrl->frame_cells, c);
-    if (h) atomicAdd(&t.ctrl->hist_overflow, h);
+    if (b) atomicAdd(&t.ctrl->frame_cells, b);
     if (blockIdx.x == 0) atomicAdd(&t.ctrl->vertices, static_cast<unsigned long long>(n));
   }
 }
 
 __global__ void __launch_bounds__(kBlock) k_query(KeyConst kc, TableDev t, VertexPtrs v, size_t n,
-                                                  const uint32_t* slot_in, OutPtrs o, int vec,
-                                                  int ovec, int blended) {
+                                                  const uint32_t* id_in, OutPtrs o, int vec,
+                                                  int ovec, int blended, uint32_t id_limit) {
   const size_t ngroups = (n + 3) / 4;
   for (size_t gi = blockIdx.x * (size_t)blockDim.x + threadIdx.x; gi < ngroups;
        gi += (size_t)gridDim.x * blockDim.x) {
     const size_t j = gi * 4;
-    uint32_t s[4];
-    if (slot_in) {
+    uint32_t id[4];
+    if (id_in) {
 #pragma unroll
-      for (int q = 0; q < 4; ++q) s[q] = j + q < n ? __ldcs(slot_in + j + q) : kOverflowSlot;
+      for (int q = 0; q < 4; ++q) id[q] = j + q < n ? __ldcs(id_in + j + q) : kOverflowSlot;
     } else {
       const float4 PX = load4(v.px, j, n, vec), PY = load4(v.py, j, n, vec),
                    PZ = load4(v.pz, j, n, vec);
@@ -342,37 +467,41 @@ __global__ void __launch_bounds__(kBlock) k_query(KeyConst kc, TableDev t, Verte
                    NZ = load4(v.nz, j, n, vec);
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        s[q] = kOverflowSlot;
+        id[q] = kOverflowSlot;
         if (j + q < n) {
           const Key k = vertex_key(kc, comp(PX, q), comp(PY, q), comp(PZ, q), comp(NX, q),
                                    comp(NY, q), comp(NZ, q), vertex_id(v, j + q), v.stream_id);
-          s[q] = probe_find(t, k.h1 & t.mask, k.fp);
+          id[q] = probe_find(t, k.h1 & t.mask, k.fp);
         }
       }
     }
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      if (s[q] != kOverflowSlot && s[q] > t.mask) {  // not a cell of this table
+      if (id[q] != kOverflowSlot && id[q] >= id_limit) {  // not a cell of this frame
         atomicOr(&t.ctrl->error, kErrBadSlot);
-        s[q] = kOverflowSlot;
+        id[q] = kOverflowSlot;
       }
     }
     Result res[4];
-    resolve_four(t, v, j, n, s, blended != 0, res);
-    store_four(o, j, n, ovec != 0, res);
+    resolve_batch<4>(t, v, j, n, id, blended != 0, res);
+    store_batch<4>(o, j, n, ovec != 0, res);
   }
 }
 
-__global__ void __launch_bounds__(kBlock) k_blend(TableDev t, float alpha) {
-  const uint32_t cnt = t.ctrl->dirty_count;
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += gridDim.x * blockDim.x)
-    blend_cell(t, t.dirty[i], alpha);
+__global__ void __launch_bounds__(kBlock) k_blend_sweep(TableDev t, uint32_t ntiles, float alpha) {
+  unsigned long long n_hovf = 0;
+  for (uint32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x)
+    blend_range<4>(t, tile * kTile, t.bcount[tile], threadIdx.x, blockDim.x, alpha, n_hovf);
+  const unsigned long long h = block_sum(n_hovf);
+  if (threadIdx.x == 0 && h) atomicAdd(&t.ctrl->hist_overflow, h);
 }
 
-__global__ void __launch_bounds__(kBlock) k_clear_dirty(TableDev t) {
-  const uint32_t cnt = t.ctrl->dirty_count;
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += gridDim.x * blockDim.x)
-    clear_cell(t, t.dirty[i]);
+__global__ void __launch_bounds__(kBlock) k_clear_sweep(TableDev t, uint32_t ntiles, int sweep) {
+  for (uint32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x)
+    clear_range(t, tile * kTile, t.bcount[tile], threadIdx.x, blockDim.x, sweep != 0);
+  if (sweep)
+    sweep_slots(t, blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x,
+                static_cast<size_t>(gridDim.x) * blockDim.x);
 }
 
 __global__ void __launch_bounds__(kBlock) k_keys(KeyConst kc, VertexPtrs v, size_t n,
@@ -387,12 +516,16 @@ __global__ void __launch_bounds__(kBlock) k_keys(KeyConst kc, VertexPtrs v, size
   }
 }
 
-__global__ void __launch_bounds__(kBlock) k_count_occupied(const unsigned char* cells,
-                                                           uint32_t stride, uint32_t fp_off,
-                                                           uint32_t T, unsigned long long* out) {
+__global__ void __launch_bounds__(kBlock) k_count_nonzero(const unsigned char* base, uint32_t stride,
+                                                          uint32_t off, uint32_t width, uint64_t n,
+                                                          unsigned long long* out) {
   unsigned long long c = 0;
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < T; i += gridDim.x * blockDim.x)
-    c += *reinterpret_cast<const uint32_t*>(cells + static_cast<size_t>(i) * stride + fp_off) != 0u;
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    const unsigned char* p = base + i * stride + off;
+    c += width == 8 ? (*reinterpret_cast<const unsigned long long*>(p) != 0ull)
+                    : (*reinterpret_cast<const uint32_t*>(p) != 0u);
+  }
   const unsigned long long s = block_sum(c);
   if (threadIdx.x == 0 && s) atomicAdd(out, s);
 }
@@ -404,95 +537,130 @@ struct FusedArgs {
   VertexPtrs v;
   OutPtrs o;
   size_t n;
-  size_t chunk;
-  uint32_t* gstash;
+  uint32_t cap_tiles;  // tiles this CTA may take (its stash capacity)
+  uint32_t* gstash;    // global stash (indexed by vertex) when it does not fit on chip
   float alpha;
   int vec, ovec, blend;
+  int sweep;  // zero the whole slot table at the end instead of slot by slot
 };
 
-template <bool TEMPORAL>
-__global__ void __launch_bounds__(kFusedBlock, 1) k_fused(FusedArgs a) {
+// The persistent kernel.  Phase A hands out tiles of kFusedTile consecutive
+// vertices from a per-frame counter, so CTAs that meet cheap (coherent)
+// vertices take more tiles; each CTA remembers its tiles, keeps every vertex's
+// cell id in its shared-memory stash, and later blends, looks up and clears
+// exactly those tiles.  A tile's new cells take ids from the tile's own range
+// [tile * kFusedTile, tile * kFusedTile + claims).
+template <bool TEMPORAL, int W>
+__global__ void __launch_bounds__(kFusedBlock, W == 4 ? 1 : 2) k_fused(FusedArgs a) {
   extern __shared__ __align__(16) uint32_t s_stash[];
+  __shared__ uint32_t s_tile[kMaxTilesPerCta];
+  __shared__ uint32_t s_claims[kMaxTilesPerCta];
+  __shared__ uint32_t s_next, s_taken;
   const TableDev& t = a.t;
-  const size_t beg = static_cast<size_t>(blockIdx.x) * a.chunk;
-  const size_t end = min(a.n, beg + a.chunk);
-  uint32_t* stash = a.gstash ? a.gstash + beg : s_stash;
+  const uint32_t ntiles = static_cast<uint32_t>((a.n + kFusedTile - 1) / kFusedTile);
   const bool vec = a.vec != 0;
-  const size_t step = 4 * static_cast<size_t>(blockDim.x);
+  if (threadIdx.x == 0) s_taken = 0;
 
-  // Phase A: keys, probing insert, accumulation.
-  unsigned long long n_ovf = 0, n_cells = 0, n_hovf = 0;
-  for (size_t j = beg + 4 * threadIdx.x; j < end; j += step) {
-    const Four f = insert_four(a.kc, t, a.v, j, end, vec, n_ovf, n_cells, n_hovf);
-    uint4 w;
-    w.x = f.slot[0] == kOverflowSlot ? kStashOverflow : (f.slot[0] | (f.owner[0] ? kOwnerBit : 0u));
-    w.y = f.slot[1] == kOverflowSlot ? kStashOverflow : (f.slot[1] | (f.owner[1] ? kOwnerBit : 0u));
-    w.z = f.slot[2] == kOverflowSlot ? kStashOverflow : (f.slot[2] | (f.owner[2] ? kOwnerBit : 0u));
-    w.w = f.slot[3] == kOverflowSlot ? kStashOverflow : (f.slot[3] | (f.owner[3] ? kOwnerBit : 0u));
-    *reinterpret_cast<uint4*>(stash + (j - beg)) = w;
+  // Phase A: keys, probing insert, accumulation, tile by tile.
+  Counters c;
+  unsigned long long nv = 0;
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      uint32_t tile = ntiles;
+      if (s_taken < a.cap_tiles)
+        tile = static_cast<uint32_t>(atomicAdd(&t.ctrl->tile_next, 1ull));
+      s_next = tile;
+      if (tile < ntiles) {
+        s_tile[s_taken] = tile;
+        s_claims[s_taken] = 0;
+      }
+    }
+    __syncthreads();
+    const uint32_t tile = s_next;
+    if (tile >= ntiles) break;
+    const uint32_t k = s_taken;
+    const size_t t0 = static_cast<size_t>(tile) * kFusedTile;
+    const size_t end = min(a.n, t0 + kFusedTile);
+    nv += end - t0;
+    uint32_t* stash = a.gstash ? a.gstash + t0 : s_stash + static_cast<size_t>(k) * kFusedTile;
+#pragma unroll 1
+    for (int sub = 0; sub < 4; sub += W) {
+      const size_t j = t0 + threadIdx.x * 4 + sub;
+      if (j < end) {
+        const Batch<W> b = insert_batch<W>(a.kc, t, a.v, j, end, vec, static_cast<uint32_t>(t0),
+                                           &s_claims[k], c);
+#pragma unroll
+        for (int q = 0; q < W; ++q) stash[j - t0 + q] = b.id[q];
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) ++s_taken;
   }
   {
-    const unsigned long long o = block_sum(n_ovf);
-    const unsigned long long c = block_sum(n_cells);
-    const unsigned long long h = block_sum(n_hovf);
+    const unsigned long long o = block_sum(c.ovf);
+    const unsigned long long k = block_sum(c.cells);
     if (threadIdx.x == 0) {
       if (o) atomicAdd(&t.ctrl->overflow_vertices, o);
-      if (c) atomicAdd(&t.ctrl->frame_cells, c);
-      if (h) atomicAdd(&t.ctrl->hist_overflow, h);
-      if (end > beg) atomicAdd(&t.ctrl->vertices, static_cast<unsigned long long>(end - beg));
+      if (k) atomicAdd(&t.ctrl->frame_cells, k);
+      if (nv) atomicAdd(&t.ctrl->vertices, threadIdx.x == 0 ? nv : 0ull);
     }
   }
   if (!grid_barrier(t.ctrl, gridDim.x)) return;
+  const uint32_t taken = s_taken;
 
-  // Phase B: temporal blend, once per touched cell by its owner.
+  // Phase B: temporal blend of the cells this CTA's tiles created.
   const bool blended = TEMPORAL && a.blend;
   if (blended) {
-    for (size_t j = beg + 4 * threadIdx.x; j < end; j += step) {
-      const uint4 w = *reinterpret_cast<const uint4*>(stash + (j - beg));
-      const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
-      uint32_t sl[4];
-      bool own[4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        own[q] = j + q < end && ws[q] != kStashOverflow && (ws[q] & kOwnerBit);
-        sl[q] = ws[q] & ~kOwnerBit;
-      }
-      blend_four(t, sl, own, a.alpha);
-    }
+    unsigned long long n_hovf = 0;
+    for (uint32_t k = 0; k < taken; ++k)
+      blend_range<W>(t, s_tile[k] * static_cast<uint32_t>(kFusedTile), s_claims[k], threadIdx.x,
+                     blockDim.x, a.alpha, n_hovf);
+    const unsigned long long h = block_sum(n_hovf);
+    if (threadIdx.x == 0 && h) atomicAdd(&t.ctrl->hist_overflow, h);
     if (!grid_barrier(t.ctrl, gridDim.x)) return;
   }
 
-  // Phase C: one lookup per vertex.
+  // Phase C: one lookup per vertex of this CTA's tiles.
   const bool ovec = a.ovec != 0;
-  for (size_t j = beg + 4 * threadIdx.x; j < end; j += step) {
-    const uint4 w = *reinterpret_cast<const uint4*>(stash + (j - beg));
-    const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
-    uint32_t sl[4];
+  for (uint32_t k = 0; k < taken; ++k) {
+    const size_t t0 = static_cast<size_t>(s_tile[k]) * kFusedTile;
+    const size_t end = min(a.n, t0 + kFusedTile);
+    const uint32_t* stash = a.gstash ? a.gstash + t0 : s_stash + static_cast<size_t>(k) * kFusedTile;
+#pragma unroll 1
+    for (int sub = 0; sub < 4; sub += W) {
+      const size_t j = t0 + threadIdx.x * 4 + sub;
+      if (j < end) {
+        uint32_t id[W];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) sl[q] = ws[q] == kStashOverflow ? kOverflowSlot : (ws[q] & ~kOwnerBit);
-    Result res[4];
-    resolve_four(t, a.v, j, end, sl, blended, res);
-    store_four(a.o, j, end, ovec, res);
+        for (int q = 0; q < W; ++q) id[q] = stash[j - t0 + q];
+        Result res[W];
+        resolve_batch<W>(t, a.v, j, end, id, blended, res);
+        store_batch<W>(a.o, j, end, ovec, res);
+      }
+    }
   }
   if (!grid_barrier(t.ctrl, gridDim.x)) return;
 
-  // Phase D: owners empty their cells for the next frame.
-  for (size_t j = beg + 4 * threadIdx.x; j < end; j += step) {
-    const uint4 w = *reinterpret_cast<const uint4*>(stash + (j - beg));
-    const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
-#pragma unroll
-    for (int q = 0; q < 4; ++q)
-      if (j + q < end && ws[q] != kStashOverflow && (ws[q] & kOwnerBit))
-        clear_cell(t, ws[q] & ~kOwnerBit);
-  }
+  // Phase D: empty the cells this CTA's tiles created (and, when many slots
+  // are in use, sweep the slot table instead of clearing slot by slot).
+  for (uint32_t k = 0; k < taken; ++k)
+    clear_range(t, s_tile[k] * static_cast<uint32_t>(kFusedTile), s_claims[k], threadIdx.x,
+                blockDim.x, a.sweep != 0);
+  if (a.sweep)
+    sweep_slots(t, blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x,
+                static_cast<size_t>(gridDim.x) * blockDim.x);
 }
 
 int sm_count() {
-  int dev = 0;
-  cudaGetDevice(&dev);
-  int c = 0;
-  cudaDeviceGetAttribute(&c, cudaDevAttrMultiProcessorCount, dev);
-  return c > 0 ? c : 1;
+  static int cached = 0;
+  if (!cached) {
+    int dev = 0, c = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&c, cudaDevAttrMultiProcessorCount, dev);
+    cached = c > 0 ? c : 1;
+  }
+  return cached;
 }
 
 int split_grid(size_t work_items) {
@@ -502,6 +670,9 @@ int split_grid(size_t work_items) {
 }
 
 }  // namespace
+
+int tile_size() { return kTile; }
+int fused_tile_size() { return kFusedTile; }
 
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
@@ -517,19 +688,25 @@ static bool vec_outputs(const OutPtrs& o) {
 }
 
 cudaError_t launch_insert(const KeyConst& kc, const TableDev& t, const VertexPtrs& v, size_t n,
-                          uint32_t* slot_out, cudaStream_t st) {
+                          uint32_t* id_out, uint32_t tile_base, int batch, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
-  k_insert<<<split_grid((n + 3) / 4), kBlock, 0, st>>>(kc, t, v, n, slot_out, vec_inputs(v) ? 1 : 0);
+  const int grid = split_grid((n + 3) / 4);
+  const int vec = vec_inputs(v) ? 1 : 0;
+  if (batch == 2)
+    k_insert<2><<<grid, kBlock, 0, st>>>(kc, t, v, n, id_out, vec, tile_base);
+  else
+    k_insert<4><<<grid, kBlock, 0, st>>>(kc, t, v, n, id_out, vec, tile_base);
   return cudaGetLastError();
 }
 
 cudaError_t launch_query(const KeyConst& kc, const TableDev& t, const VertexPtrs& v, size_t n,
-                         const uint32_t* slot_in, const OutPtrs& o, bool blended,
+                         const uint32_t* id_in, const OutPtrs& o, bool blended, uint32_t id_limit,
                          cudaStream_t st) {
   if (n == 0) return cudaSuccess;
-  k_query<<<split_grid((n + 3) / 4), kBlock, 0, st>>>(kc, t, v, n, slot_in, o,
+  k_query<<<split_grid((n + 3) / 4), kBlock, 0, st>>>(kc, t, v, n, id_in, o,
                                                       vec_inputs(v) ? 1 : 0,
-                                                      vec_outputs(o) ? 1 : 0, blended ? 1 : 0);
+                                                      vec_outputs(o) ? 1 : 0, blended ? 1 : 0,
+                                                      id_limit);
   return cudaGetLastError();
 }
 
@@ -540,88 +717,113 @@ cudaError_t launch_keys(const KeyConst& kc, const VertexPtrs& v, size_t n, uint3
   return cudaGetLastError();
 }
 
-cudaError_t launch_blend(const TableDev& t, float alpha, cudaStream_t st) {
-  k_blend<<<sm_count() * 8, kBlock, 0, st>>>(t, alpha);
+cudaError_t launch_blend(const TableDev& t, uint32_t ntiles, float alpha, cudaStream_t st) {
+  if (ntiles == 0) return cudaSuccess;
+  const uint32_t grid = std::min<uint32_t>(ntiles, static_cast<uint32_t>(sm_count()) * 8);
+  k_blend_sweep<<<grid, kBlock, 0, st>>>(t, ntiles, alpha);
   return cudaGetLastError();
 }
 
-cudaError_t launch_clear_dirty(const TableDev& t, cudaStream_t st) {
-  k_clear_dirty<<<sm_count() * 8, kBlock, 0, st>>>(t);
+// Sweeping the slot table pays once the frame's vertices reach an eighth of it.
+static bool sweep_pays(const TableDev& t, size_t vertices) {
+  return vertices >= (static_cast<size_t>(t.mask) + 1) / 8;
+}
+
+cudaError_t launch_clear(const TableDev& t, uint32_t ntiles, cudaStream_t st) {
+  if (ntiles == 0) return cudaSuccess;
+  const int sweep = sweep_pays(t, static_cast<size_t>(ntiles) * kTile) ? 1 : 0;
+  const uint32_t grid = std::min<uint32_t>(std::max<uint32_t>(ntiles, sweep ? 1u << 30 : 0u),
+                                           static_cast<uint32_t>(sm_count()) * 8);
+  k_clear_sweep<<<grid, kBlock, 0, st>>>(t, ntiles, sweep);
   return cudaGetLastError();
 }
 
-cudaError_t launch_count_occupied(const unsigned char* cells, uint32_t stride, uint32_t fp_off,
-                                  uint32_t T, unsigned long long* out, cudaStream_t st) {
-  k_count_occupied<<<sm_count() * 4, kBlock, 0, st>>>(cells, stride, fp_off, T, out);
+cudaError_t launch_count_nonzero(const void* base, uint32_t stride, uint32_t off, uint32_t width,
+                                 uint64_t n, unsigned long long* out, cudaStream_t st) {
+  k_count_nonzero<<<sm_count() * 4, kBlock, 0, st>>>(static_cast<const unsigned char*>(base),
+                                                     stride, off, width, n, out);
   return cudaGetLastError();
+}
+
+template <bool TEMPORAL, int W>
+static const void* fused_fn() {
+  return reinterpret_cast<const void*>(k_fused<TEMPORAL, W>);
+}
+
+static const void* fused_kernel(bool temporal, int batch) {
+  if (temporal) return batch == 2 ? fused_fn<true, 2>() : fused_fn<true, 4>();
+  return batch == 2 ? fused_fn<false, 2>() : fused_fn<false, 4>();
 }
 
 // Largest dynamic shared memory a k_fused CTA may request: the opt-in limit
-// per block minus the kernel's static shared memory.
-template <bool TEMPORAL>
-static cudaError_t fused_dyn_smem_limit(size_t* limit) {
-  static size_t cached = 0;
-  if (!cached) {
-    int dev = 0, maxopt = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&maxopt, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    cudaFuncAttributes fa;
-    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_fused<TEMPORAL>);
-    if (e != cudaSuccess) return e;
-    const size_t lim = static_cast<size_t>(maxopt) - fa.sharedSizeBytes;
-    e = cudaFuncSetAttribute(k_fused<TEMPORAL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             static_cast<int>(lim));
-    if (e != cudaSuccess) return e;
-    cached = lim;
-  }
-  *limit = cached;
+// per block minus the kernel's static shared memory (set once per kernel).
+static cudaError_t fused_dyn_smem_limit(const void* fn, size_t* limit) {
+  static const void* done[4] = {nullptr, nullptr, nullptr, nullptr};
+  static size_t lims[4] = {0, 0, 0, 0};
+  for (int i = 0; i < 4; ++i)
+    if (done[i] == fn) {
+      *limit = lims[i];
+      return cudaSuccess;
+    }
+  int dev = 0, maxopt = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&maxopt, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaFuncAttributes fa;
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, fn);
+  if (e != cudaSuccess) return e;
+  const size_t lim = static_cast<size_t>(maxopt) - fa.sharedSizeBytes;
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(lim));
+  if (e != cudaSuccess) return e;
+  for (int i = 0; i < 4; ++i)
+    if (!done[i]) {
+      done[i] = fn;
+      lims[i] = lim;
+      break;
+    }
+  *limit = lim;
   return cudaSuccess;
 }
 
-template <bool TEMPORAL>
-static cudaError_t fused_blocks_per_sm(size_t smem, int* nb) {
-  size_t lim = 0;
-  cudaError_t e = fused_dyn_smem_limit<TEMPORAL>(&lim);
-  if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, k_fused<TEMPORAL>, kFusedBlock, smem);
-}
-
-cudaError_t plan_fused(size_t n, bool temporal, FusedPlan* plan) {
+cudaError_t plan_fused(size_t n, bool temporal, int batch, FusedPlan* plan) {
+  const void* fn = fused_kernel(temporal, batch);
   const int sms = sm_count();
   size_t maxdyn = 0;
-  cudaError_t e = temporal ? fused_dyn_smem_limit<true>(&maxdyn) : fused_dyn_smem_limit<false>(&maxdyn);
+  cudaError_t e = fused_dyn_smem_limit(fn, &maxdyn);
   if (e != cudaSuccess) return e;
   int b0 = 0;
-  e = temporal ? fused_blocks_per_sm<true>(0, &b0) : fused_blocks_per_sm<false>(0, &b0);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b0, fn, kFusedBlock, 0);
   if (e != cudaSuccess) return e;
   if (b0 < 1) return cudaErrorInvalidConfiguration;
+  int dev = 0, smem_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  const size_t ntiles = (n + kFusedTile - 1) / kFusedTile;
+  const size_t tile_bytes = kFusedTile * sizeof(uint32_t);
+  plan->block = kFusedBlock;
+  plan->batch = batch;
   for (int b = b0; b >= 1; --b) {
-    const int grid = sms * b;
-    size_t chunk = (n + grid - 1) / grid;
-    chunk = std::max<size_t>((chunk + 3) & ~static_cast<size_t>(3), 4);
-    const size_t smem = chunk * sizeof(uint32_t);
-    if (smem > maxdyn) continue;
+    // shared memory per CTA when b CTAs share an SM (static part and a reserve deducted)
+    const size_t per = std::min(maxdyn, static_cast<size_t>(smem_sm) / b - 12 * 1024);
+    const size_t cap = std::min<size_t>(per / tile_bytes, kMaxTilesPerCta);
+    if (cap == 0 || cap * static_cast<size_t>(sms) * b < ntiles) continue;
+    // keep some headroom so that fast CTAs can take extra tiles
     int nb = 0;
-    e = temporal ? fused_blocks_per_sm<true>(smem, &nb) : fused_blocks_per_sm<false>(smem, &nb);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, kFusedBlock, cap * tile_bytes);
     if (e != cudaSuccess) return e;
     if (nb >= b) {
-      plan->grid = grid;
-      plan->block = kFusedBlock;
-      plan->chunk = chunk;
-      plan->smem = smem;
+      plan->grid = sms * b;
+      plan->cap_tiles = static_cast<uint32_t>(cap);
+      plan->smem = cap * tile_bytes;
       plan->global_stash = false;
       return cudaSuccess;
     }
   }
   // The stash does not fit on chip: keep it in a global scratch buffer.
-  const int grid = sms * b0;
-  size_t chunk = (n + grid - 1) / grid;
-  chunk = std::max<size_t>((chunk + 3) & ~static_cast<size_t>(3), 4);
-  plan->grid = grid;
-  plan->block = kFusedBlock;
-  plan->chunk = chunk;
+  plan->grid = sms * b0;
+  plan->cap_tiles = kMaxTilesPerCta;
   plan->smem = 0;
   plan->global_stash = true;
+  if (static_cast<size_t>(plan->grid) * kMaxTilesPerCta < ntiles) return cudaErrorInvalidValue;
   return cudaSuccess;
 }
 
@@ -634,16 +836,16 @@ cudaError_t launch_fused(const KeyConst& kc, const TableDev& t, const VertexPtrs
   a.v = v;
   a.o = o;
   a.n = n;
-  a.chunk = plan.chunk;
+  a.cap_tiles = plan.cap_tiles;
   a.gstash = plan.global_stash ? gstash : nullptr;
   a.alpha = alpha;
   a.vec = vec_inputs(v) ? 1 : 0;
   a.ovec = vec_outputs(o) ? 1 : 0;
   a.blend = blend ? 1 : 0;
+  a.sweep = sweep_pays(t, n) ? 1 : 0;
   void* args[] = {&a};
-  const void* fn = temporal ? reinterpret_cast<const void*>(k_fused<true>)
-                            : reinterpret_cast<const void*>(k_fused<false>);
-  return cudaLaunchCooperativeKernel(fn, dim3(plan.grid), dim3(plan.block), args, plan.smem, st);
+  return cudaLaunchCooperativeKernel(fused_kernel(temporal, plan.batch), dim3(plan.grid),
+                                     dim3(plan.block), args, plan.smem, st);
 }
 
 }  // namespace pps

@@ -53,6 +53,10 @@ class pps_output(ctypes.Structure):
     _fields_ = [("r", _vp), ("g", _vp), ("b", _vp), ("count", _vp), ("status", _vp)]
 
 
+class pps_tuning(ctypes.Structure):
+    _fields_ = [("batch", _u32), ("reserved", _u32 * 7)]
+
+
 class pps_stats_t(ctypes.Structure):
     _fields_ = [("frame_cells", ctypes.c_uint64), ("overflow_vertices", ctypes.c_uint64),
                 ("occupied_slots", ctypes.c_uint64), ("vertices", ctypes.c_uint64),
@@ -80,6 +84,8 @@ SIGNATURES = {
     "pps_keys": ([_vp, ctypes.POINTER(pps_vertices), ctypes.c_size_t, _vp, _vp, _vp],
                  ctypes.c_int),
     "pps_stats": ([_vp, ctypes.POINTER(pps_stats_t), _vp], ctypes.c_int),
+    "pps_set_tuning": ([_vp, ctypes.POINTER(pps_tuning)], ctypes.c_int),
+    "pps_get_tuning": ([_vp, ctypes.POINTER(pps_tuning)], ctypes.c_int),
     "pps_table_dump": ([_vp, _vp, _vp, _vp], ctypes.c_int),
     "pps_bench_rate": ([ctypes.c_int, ctypes.c_size_t, ctypes.c_size_t, _vp, _vp,
                         ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
@@ -231,6 +237,16 @@ def pps_keys(handle, v: pps_vertices, n: int, h_out: torch.Tensor, f_out: torch.
                           _ptr(f_out, n, torch.int32, "f_out"), _stream(stream)))
 
 
+def pps_set_tuning(handle, batch: int = 0):
+    _check(lib().pps_set_tuning(handle, ctypes.byref(pps_tuning(batch))))
+
+
+def pps_get_tuning(handle) -> dict:
+    t = pps_tuning()
+    _check(lib().pps_get_tuning(handle, ctypes.byref(t)))
+    return {"batch": t.batch}
+
+
 def pps_stats(handle, stream=None) -> dict:
     s = pps_stats_t()
     _check(lib().pps_stats(handle, ctypes.byref(s), _stream(stream)))
@@ -323,6 +339,9 @@ class Table:
 
     def stats(self, stream=None) -> dict:
         return pps_stats(self.handle, stream)
+
+    def tune(self, batch: int = 0):
+        pps_set_tuning(self.handle, batch)
 
     def dump(self, stream=None):
         return pps_table_dump(self.handle, self.T, self.fixed, stream)

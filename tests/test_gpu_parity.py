@@ -84,6 +84,25 @@ def _check_frame(out, fr, fixed=False):
         _check_values(got, fr.mean64, fr.count)
 
 
+def _audit_table(fp, acc, fr, cells, max_probes, T):
+    """Each oracle cell in `cells` sits in the dumped table within P slots of
+    its home, under its own fingerprint, with the oracle's count."""
+    home = fr.cell_home[cells].astype(np.int64)
+    f = fr.cell_fp[cells]
+    pos = (home[:, None] + np.arange(max_probes)[None, :]) & (T - 1)
+    hit = fp[pos] == f[:, None]
+    assert hit.any(axis=1).all(), "a cell's fingerprint is missing from its probe window"
+    s = pos[np.arange(len(cells)), hit.argmax(axis=1)]
+    assert np.array_equal(acc[s, 3].astype(np.int64), fr.cell_count[cells])
+    return s
+
+
+def _check_ids(ids, fr, ok):
+    """Vertices share a cell id exactly when the oracle puts them in one cell."""
+    pairs = np.unique(np.column_stack([fr.cell[ok], ids[ok]]), axis=0)
+    assert len(np.unique(pairs[:, 0])) == len(pairs) == len(np.unique(pairs[:, 1]))
+
+
 # ------------------------------------------------------------------ keys
 @pytest.mark.parametrize("jitter,nih", [(True, True), (True, False), (False, True)])
 def test_keys_bit_exact(jitter, nih):
@@ -126,12 +145,14 @@ def test_keys_degenerate_inputs():
 
 
 # ------------------------------------------------------------------ one frame
-@pytest.mark.parametrize("fixed", [False, True])
-def test_fused_filter_matches_oracle(fixed):
+@pytest.mark.parametrize("fixed,batch", [(False, 4), (True, 4), (False, 2), (True, 2)])
+def test_fused_filter_matches_oracle(fixed, batch):
     spec, cfg = _small(width=160, height=120, bounces=3, accum_fixed=fixed)
     v = _gen(spec, 2)
     n = v["px"].numel() - 3
     tab = pps.Table(cfg)
+    tab.tune(batch)
+    assert pps.pps_get_tuning(tab.handle)["batch"] == batch
     out = tab.filter(_dev(v, n), spec.view.eye, 2)
     fr = _oracle(cfg, spec.view.eye, 2, _np(v, n))
     _check_frame(out, fr, fixed)
@@ -161,16 +182,13 @@ def test_split_path_matches_oracle_and_audit(fixed):
     _check_frame(out2, fr, fixed)
     if fixed:
         assert all(torch.equal(out1[c], out2[c]) for c in "rgb")
-    # table audit: slots hold the oracle's fingerprints inside the probe window
+    # table audit: every cell under its fingerprint inside its probe window
     fp, acc = tab.dump()
-    s = slots.cpu().numpy().view(np.uint32).astype(np.int64)
+    ids = slots.cpu().numpy().view(np.uint32).astype(np.int64)
+    _check_ids(ids, fr, np.ones(n, dtype=bool))
     T = 1 << cfg.log2_slots
-    assert np.array_equal(fp[s], fr.keys.fp)
-    dist = (s - fr.keys.home.astype(np.int64)) % T
-    assert dist.max() < cfg.max_probes
+    _audit_table(fp, acc, fr, np.arange(fr.tuples.shape[0]), cfg.max_probes, T)
     assert set(fp[fp != 0].tolist()) == set(fr.cell_fp.tolist())
-    cnt = acc[s, 3].astype(np.int64)
-    assert np.array_equal(cnt, fr.count)
     st = tab.stats()
     assert st["occupied_slots"] == fr.tuples.shape[0] == st["frame_cells"]
     tab.build(spec.view.eye, 2)  # empties the frame through the dirty list
@@ -261,14 +279,15 @@ def test_overflow_all_or_none_and_window_audit():
 
 
 # ------------------------------------------------------------------ temporal
-@pytest.mark.parametrize("hist_mode,alpha,fused", [(1, 0.2, True), (1, -1.0, True),
-                                                   (1, 0.2, False), (2, 0.2, True),
-                                                   (2, -1.0, False)])
-def test_temporal_blend_matches_oracle(hist_mode, alpha, fused):
+@pytest.mark.parametrize("hist_mode,alpha,fused,batch", [(1, 0.2, True, 4), (1, -1.0, True, 2),
+                                                         (1, 0.2, False, 4), (2, 0.2, True, 2),
+                                                         (2, -1.0, False, 2)])
+def test_temporal_blend_matches_oracle(hist_mode, alpha, fused, batch):
     w = configs.small()
     frames = 4
     _, cfg = _small(width=128, height=96, bounces=2, hist_mode=hist_mode, log2_hist_slots=19)
     tab = pps.Table(cfg)
+    tab.tune(batch)
     hist = O.History.empty()
     for f in range(frames):
         spec = configs.frame_spec(w, 0, f)
@@ -403,14 +422,14 @@ def test_hd_frame_split_path_window_audit():
     vn = _np(d)
     fr = _oracle(cfg, spec.view.eye, 0, vn)
     ovf = _audit_overflow(out, vn, fr)
-    s = slots.cpu().numpy().view(np.uint32).astype(np.int64)
-    assert np.all(s[ovf] == 0xFFFFFFFF)
+    ids = slots.cpu().numpy().view(np.uint32).astype(np.int64)
+    assert np.all(ids[ovf] == 0xFFFFFFFF)
     for j in np.nonzero(ovf)[0]:
         assert O.overflow_window_full(fp, int(fr.keys.home[j]), int(fr.keys.fp[j]), cfg.max_probes)
     ok = ~ovf
     T = 1 << cfg.log2_slots
-    assert np.array_equal(fp[s[ok]], fr.keys.fp[ok])
-    assert ((s[ok] - fr.keys.home[ok].astype(np.int64)) % T).max() < cfg.max_probes
+    _check_ids(ids, fr, ok)
+    _audit_table(fp, acc, fr, np.unique(fr.cell[ok]), cfg.max_probes, T)
     assert np.array_equal(out["count"].cpu().numpy().astype(np.int64)[ok], fr.count[ok])
     _check_values(_rgb(out)[ok], fr.mean64[ok], fr.count[ok])
     tab.close()
