@@ -269,6 +269,30 @@ int pps_keys(pps_table *t, const pps_vertices *v, size_t n, uint32_t *h_out, uin
              void *stream);
 
 /*
+ * pps_filter_noalloc: one frame of the plain filter (FP32 accumulation, no
+ * history) that allocates no device memory.  The paper has no counterpart:
+ * it serves callers that may not call cudaMalloc when they filter, such as a
+ * plug-in whose host application owns the GPU memory budget, or a real-time
+ * render thread that must not block on device allocation.  Results equal
+ * pps_filter on a table created from `p` (FP32 atomics: equal up to
+ * summation order).
+ *  - Working memory is one static device array inside the library (about
+ *    26 MB), held by every GPU that loads the library until the process exits.
+ *    Limits: log2_slots <= 20 and n <= 524,288; larger requests, another
+ *    accum_mode, or a history return PPS_EINVAL.
+ *  - The first call on a device (that device current) looks up the array's
+ *    device address with cudaGetSymbolAddress; make that first call before any
+ *    stream capture.
+ *  - All calls share the array and each starts by clearing what it uses; two
+ *    calls that overlap on the GPU (streams not ordered) race and give wrong
+ *    results.
+ * Arguments as for pps_params / pps_filter; every pointer is the caller's.
+ * Errors: PPS_EINVAL, PPS_ECUDA.
+ */
+int pps_filter_noalloc(const pps_params *p, const pps_camera *cam, uint32_t frame,
+                       const pps_vertices *v, size_t n, const pps_output *out, void *stream);
+
+/*
  * pps_stats: synchronize `stream` and read the table's counters.  Returns
  * PPS_EDEVICE if a kernel raised the device error word (the word is then
  * cleared).

@@ -37,6 +37,11 @@ enum FrameState { kClean = 0, kOpen = 1, kBlended = 2 };
 
 }  // namespace
 
+namespace pps {
+// Record an error for pps_last_error() from another translation unit.
+int record_error(int code, const char* msg) { return fail(code, msg); }
+}  // namespace pps
+
 struct pps_table {
   pps_params p{};
   int device = 0;

@@ -39,4 +39,6 @@ int tile_size();        // vertices (and cell ids) per tile of the split path
 int fused_tile_size();  // vertices (and cell ids) per tile of the persistent kernel
 bool aligned16(const void* p);
 
+int record_error(int code, const char* msg);  // message for pps_last_error()
+
 }  // namespace pps

@@ -85,6 +85,9 @@ SIGNATURES = {
                  ctypes.c_int),
     "pps_stats": ([_vp, ctypes.POINTER(pps_stats_t), _vp], ctypes.c_int),
     "pps_set_tuning": ([_vp, ctypes.POINTER(pps_tuning)], ctypes.c_int),
+    "pps_filter_noalloc": ([ctypes.POINTER(pps_params), ctypes.POINTER(pps_camera), _u32,
+                            ctypes.POINTER(pps_vertices), ctypes.c_size_t,
+                            ctypes.POINTER(pps_output), _vp], ctypes.c_int),
     "pps_get_tuning": ([_vp, ctypes.POINTER(pps_tuning)], ctypes.c_int),
     "pps_table_dump": ([_vp, _vp, _vp, _vp], ctypes.c_int),
     "pps_bench_rate": ([ctypes.c_int, ctypes.c_size_t, ctypes.c_size_t, _vp, _vp,
@@ -229,6 +232,12 @@ def pps_filter_host(handle, cam: pps_camera, frame: int, v: pps_vertices, n: int
     _check(lib().pps_filter_host(handle, ctypes.byref(cam), frame & 0xFFFFFFFF, ctypes.byref(v),
                                  n, 1 if blend else 0, float(alpha), ctypes.byref(out),
                                  _stream(stream)))
+
+
+def pps_filter_noalloc(params: pps_params, cam: pps_camera, frame: int, v: pps_vertices, n: int,
+                       out: pps_output, stream=None):
+    _check(lib().pps_filter_noalloc(ctypes.byref(params), ctypes.byref(cam), frame & 0xFFFFFFFF,
+                                    ctypes.byref(v), n, ctypes.byref(out), _stream(stream)))
 
 
 def pps_keys(handle, v: pps_vertices, n: int, h_out: torch.Tensor, f_out: torch.Tensor,
