@@ -48,6 +48,7 @@ extern "C" {
 #define PPS_STATUS_LOWCOUNT 1 /* average returned, count < lowcount_threshold  */
 #define PPS_STATUS_OVERFLOW 2 /* probe limit exceeded: the vertex's own,       */
                               /* unfiltered contribution returned (Sec. 3.2)   */
+#define PPS_STATUS_MLP 3      /* low count: the learned fallback's prediction  */
 
 /* ---- modes -------------------------------------------------------------- */
 #define PPS_ACCUM_FP32 0  /* FP32 sums, FP32 count lane: red.add.v4.f32         */
@@ -307,6 +308,81 @@ int pps_stats(pps_table *t, pps_stats_t *out, void *stream);
  * probe overflow and for inspection.  Errors: PPS_EINVAL, PPS_ECUDA.
  */
 int pps_table_dump(pps_table *t, uint32_t *fp_host, void *acc_host, void *stream);
+
+/* ---- learned fallback --------------------------------------------------- */
+/*
+ * A small network that answers for vertices whose cell holds too few samples
+ * (the low-density case of Sec. 3.3), trained online on the averages of
+ * well-populated cells that the filter itself produces.  Input: per axis
+ * sin/cos(pi 2^k p), k = 0..11, of the position normalized to the box (72),
+ * the unit normal (3), 5 zeros; three hidden layers of 64 with ReLU; linear
+ * RGB out.  BF16 weights and activations, FP32 accumulation (tensor cores).
+ * Loss 1/(2 batch) sum (y - t)^2; Adam on FP32 master weights.
+ *
+ * Parameter vector (13,699 floats, this order): W1 [64][80], b1 [64],
+ * W2 [64][64], b2 [64], W3 [64][64], b3 [64], W4 [3][64], b4 [3] (W as
+ * [out][in]).
+ *
+ *  box_min, box_max   position normalization box (p clamped to [0, 1]^3).
+ *  lr, beta1, beta2, eps  Adam.
+ *  batch              samples per training step, a multiple of 128.
+ *  steps              training steps per pps_mlp_train call.
+ *  train_min_count    a vertex is a training sample if its count >= this.
+ *  infer_max_count    pps_mlp_infer answers for counts below this.
+ *  seed               He initialisation and training-sample selection.
+ */
+typedef struct pps_mlp_params {
+  float box_min[3];
+  float box_max[3];
+  float lr, beta1, beta2, eps;
+  uint32_t batch;
+  uint32_t steps;
+  uint32_t train_min_count;
+  uint32_t infer_max_count;
+  uint32_t seed;
+  uint32_t reserved[3];
+} pps_mlp_params;
+
+typedef struct pps_mlp pps_mlp;
+
+/* pps_mlp_create: allocate a network on the current device; init_host
+ * (nullable, 13,699 floats) gives the initial weights, else He initialisation
+ * with zero biases from `seed`.  Errors: PPS_EINVAL, PPS_ENOMEM, PPS_ECUDA. */
+int pps_mlp_create(pps_mlp **out, const pps_mlp_params *p, const float *init_host);
+int pps_mlp_destroy(pps_mlp *m);
+
+/* Set / read the FP32 master weights (host arrays of 13,699 floats); setting
+ * also resets the Adam moments and step count.  Both synchronize the device. */
+int pps_mlp_set_weights(pps_mlp *m, const float *host, size_t count);
+int pps_mlp_get_weights(pps_mlp *m, float *host, size_t count);
+
+/*
+ * pps_mlp_train: `steps` Adam steps.  Each step draws `batch` samples: for
+ * sample i the first of 16 candidate vertices (Philox4x32-10, key (seed,
+ * frame), counter (i, step, try, 0); index = high 32 bits of x0 * n) whose
+ * filtered count is >= train_min_count (no candidate: the sample is left
+ * out); the target is that vertex's filtered value.  `filtered` holds the
+ * filter's per-vertex r, g, b and count (device).
+ */
+int pps_mlp_train(pps_mlp *m, const pps_vertices *v, size_t n, const pps_output *filtered,
+                  uint32_t frame, void *stream);
+
+/* pps_mlp_infer: for every vertex with count < infer_max_count whose status
+ * is not OVERFLOW, replace out->r, g, b by the network's prediction and set
+ * status PPS_STATUS_MLP.  out->count and out->status are required. */
+int pps_mlp_infer(pps_mlp *m, const pps_vertices *v, size_t n, const pps_output *out,
+                  void *stream);
+
+/* pps_mlp_forward: the network's prediction for every vertex (device r, g, b). */
+int pps_mlp_forward(pps_mlp *m, const pps_vertices *v, size_t n, float *r, float *g, float *b,
+                    void *stream);
+
+/* pps_mlp_gradient: the loss gradient (13,699 floats, device) over `batch`
+ * samples: vertex idx[i] (-1: left out) with target (tr, tg, tb)[idx[i]],
+ * normalised by `batch` (a multiple of 128).  No weights change. */
+int pps_mlp_gradient(pps_mlp *m, const pps_vertices *v, const float *tr, const float *tg,
+                     const float *tb, const int32_t *idx, uint32_t batch, float *grad_out,
+                     void *stream);
 
 #ifdef __cplusplus
 }

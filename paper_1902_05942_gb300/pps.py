@@ -21,7 +21,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libpps.so")
 
 PPS_OK, PPS_EINVAL, PPS_ENOMEM, PPS_ECUDA, PPS_EDEVICE, PPS_ESTATE = range(6)
-STATUS_OK, STATUS_LOWCOUNT, STATUS_OVERFLOW = 0, 1, 2
+STATUS_OK, STATUS_LOWCOUNT, STATUS_OVERFLOW, STATUS_MLP = 0, 1, 2, 3
+MLP_PARAMS = 13699
 ACCUM_FP32, ACCUM_FIXED = 0, 1
 HIST_NONE, HIST_FP32, HIST_FP16 = 0, 1, 2
 OVERFLOW_SLOT = 0xFFFFFFFF
@@ -64,6 +65,13 @@ class pps_stats_t(ctypes.Structure):
                 ("device_error", _u32), ("frame", _u32)]
 
 
+class pps_mlp_params(ctypes.Structure):
+    _fields_ = [("box_min", _f32 * 3), ("box_max", _f32 * 3), ("lr", _f32), ("beta1", _f32),
+                ("beta2", _f32), ("eps", _f32), ("batch", _u32), ("steps", _u32),
+                ("train_min_count", _u32), ("infer_max_count", _u32), ("seed", _u32),
+                ("reserved", _u32 * 3)]
+
+
 # Every exported function and its argument types.
 SIGNATURES = {
     "pps_version": ([], ctypes.c_char_p),
@@ -90,6 +98,18 @@ SIGNATURES = {
                             ctypes.POINTER(pps_output), _vp], ctypes.c_int),
     "pps_get_tuning": ([_vp, ctypes.POINTER(pps_tuning)], ctypes.c_int),
     "pps_table_dump": ([_vp, _vp, _vp, _vp], ctypes.c_int),
+    "pps_mlp_create": ([ctypes.POINTER(_vp), ctypes.POINTER(pps_mlp_params), _vp], ctypes.c_int),
+    "pps_mlp_destroy": ([_vp], ctypes.c_int),
+    "pps_mlp_set_weights": ([_vp, _vp, ctypes.c_size_t], ctypes.c_int),
+    "pps_mlp_get_weights": ([_vp, _vp, ctypes.c_size_t], ctypes.c_int),
+    "pps_mlp_train": ([_vp, ctypes.POINTER(pps_vertices), ctypes.c_size_t,
+                       ctypes.POINTER(pps_output), _u32, _vp], ctypes.c_int),
+    "pps_mlp_infer": ([_vp, ctypes.POINTER(pps_vertices), ctypes.c_size_t,
+                       ctypes.POINTER(pps_output), _vp], ctypes.c_int),
+    "pps_mlp_forward": ([_vp, ctypes.POINTER(pps_vertices), ctypes.c_size_t, _vp, _vp, _vp, _vp],
+                        ctypes.c_int),
+    "pps_mlp_gradient": ([_vp, ctypes.POINTER(pps_vertices), _vp, _vp, _vp, _vp, _u32, _vp, _vp],
+                         ctypes.c_int),
     "pps_bench_rate": ([ctypes.c_int, ctypes.c_size_t, ctypes.c_size_t, _vp, _vp,
                         ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
 }
@@ -281,6 +301,78 @@ def pps_bench_rate(kind: str, region: torch.Tensor, ops: int, stream=None) -> fl
     if rc:
         raise PPSError(rc, "pps_bench_rate failed")
     return out.value
+
+
+# ---------------------------------------------------------------- learned fallback
+def mlp_params(box_min=(-100.0, -100.0, -100.0), box_max=(100.0, 100.0, 100.0), lr=1e-3,
+               beta1=0.9, beta2=0.999, eps=1e-8, batch=16384, steps=4, train_min_count=8,
+               infer_max_count=4, seed=7) -> pps_mlp_params:
+    return pps_mlp_params((_f32 * 3)(*box_min), (_f32 * 3)(*box_max), lr, beta1, beta2, eps,
+                          batch, steps, train_min_count, infer_max_count, seed, (_u32 * 3)())
+
+
+class MLP:
+    """The learned fallback network on the current device."""
+
+    def __init__(self, params: Optional[pps_mlp_params] = None, init=None):
+        self.params = params or mlp_params()
+        h = _vp()
+        w = None
+        if init is not None:
+            w = np.ascontiguousarray(init, dtype=np.float32)
+            assert w.size == MLP_PARAMS
+        _check(lib().pps_mlp_create(ctypes.byref(h), ctypes.byref(self.params),
+                                    w.ctypes.data if w is not None else None))
+        self.handle = h.value
+
+    def close(self):
+        if self.handle:
+            lib().pps_mlp_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_weights(self, w):
+        w = np.ascontiguousarray(w, dtype=np.float32)
+        _check(lib().pps_mlp_set_weights(self.handle, w.ctypes.data, w.size))
+
+    def get_weights(self) -> np.ndarray:
+        w = np.zeros(MLP_PARAMS, dtype=np.float32)
+        _check(lib().pps_mlp_get_weights(self.handle, w.ctypes.data, w.size))
+        return w
+
+    def train(self, v, filtered, frame, stream=None, ids=None):
+        n = v["px"].numel()
+        _check(lib().pps_mlp_train(self.handle, ctypes.byref(make_vertices(v, n, ids)), n,
+                                   ctypes.byref(make_output(filtered, n)), frame & 0xFFFFFFFF,
+                                   _stream(stream)))
+
+    def infer(self, v, out, stream=None):
+        n = v["px"].numel()
+        _check(lib().pps_mlp_infer(self.handle, ctypes.byref(make_vertices(v, n)), n,
+                                   ctypes.byref(make_output(out, n)), _stream(stream)))
+
+    def forward(self, v, stream=None):
+        n = v["px"].numel()
+        o = {c: torch.empty(n, dtype=torch.float32, device=v["px"].device) for c in "rgb"}
+        _check(lib().pps_mlp_forward(self.handle, ctypes.byref(make_vertices(v, n)), n,
+                                     o["r"].data_ptr(), o["g"].data_ptr(), o["b"].data_ptr(),
+                                     _stream(stream)))
+        return o
+
+    def gradient(self, v, targets, idx: torch.Tensor, stream=None) -> torch.Tensor:
+        n = v["px"].numel()
+        g = torch.empty(MLP_PARAMS, dtype=torch.float32, device=v["px"].device)
+        _check(lib().pps_mlp_gradient(self.handle, ctypes.byref(make_vertices(v, n)),
+                                      targets["r"].data_ptr(), targets["g"].data_ptr(),
+                                      targets["b"].data_ptr(), _ptr(idx, idx.numel(), torch.int32,
+                                                                    "idx"),
+                                      idx.numel(), g.data_ptr(), _stream(stream)))
+        return g
 
 
 # ---------------------------------------------------------------- convenience
