@@ -285,11 +285,162 @@ def run_ours(args):
         }
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(frames[0], w, args.cpu_sample)
+        if not args.no_mlp:
+            line["mlp_fallback"] = mlp_leg(frames, cfg)
+        if not args.no_batched:
+            del frames
+            line["batched"] = batched_leg()
         print(json.dumps(line), flush=True)
     tab.close()
     if ws > 1:
         dist.barrier()
         dist.destroy_process_group()
+
+
+MLP_FWD_FLOP = 2 * (80 * 64 + 64 * 64 + 64 * 64 + 64 * 3)  # per sample, algorithmic
+
+
+def mlp_leg(frames, cfg, steps_timed=8):
+    """The learned-fallback workload on the resident HD frames: per frame the
+    temporal filter, 4 Adam steps of 16,384 samples on cells with count >= 8,
+    and inference for vertices with count < 4.  Times each part with CUDA
+    events; RMSE of the GPU predictions against the FP64 oracle network with
+    the same trained weights, on sampled low-count vertices of the last frame."""
+    import numpy as np
+    import torch
+    from oracle import mlp_oracle as M
+    from paper_1902_05942_gb300 import pps
+    tab = pps.Table(cfg)
+    net = pps.MLP(pps.mlp_params())
+    n_max = max(fr[0]["px"].numel() for fr in frames)
+    out = pps.empty_output(n_max, frames[0][0]["px"].device)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    t_f = t_t = t_i = 0.0
+    n_low = 0
+    warm = 4
+    for i in range(warm + steps_timed):
+        v, eye = frames[i % len(frames)]
+        n = v["px"].numel()
+        o = {k: t[:n] for k, t in out.items()}
+        ev[0].record()
+        tab.filter(v, eye, i, blend=True, alpha=cfg.alpha, out=o)
+        ev[1].record()
+        net.train(v, o, i)
+        ev[2].record()
+        net.infer(v, o)
+        ev[3].record()
+        torch.cuda.synchronize()
+        if i >= warm:
+            t_f += ev[0].elapsed_time(ev[1])
+            t_t += ev[1].elapsed_time(ev[2])
+            t_i += ev[2].elapsed_time(ev[3])
+            n_low += int((o["status"] == pps.STATUS_MLP).sum().item())
+    k = steps_timed
+    train_flop = 4 * 16384 * 3 * MLP_FWD_FLOP
+    infer_flop = (n_low / k) * MLP_FWD_FLOP
+    # accuracy against the FP64 oracle network with the same weights
+    w = net.get_weights().astype(np.float64)
+    low = torch.nonzero(o["status"] == pps.STATUS_MLP).flatten()
+    pick = low[torch.randperm(low.numel(), device=low.device)[:50000]].cpu().numpy()
+    vn = {c: v[c][:n].cpu().numpy() for c in ("px", "py", "pz", "nx", "ny", "nz")}
+    P = np.column_stack([vn["px"][pick], vn["py"][pick], vn["pz"][pick]])
+    Nn = np.column_stack([vn["nx"][pick], vn["ny"][pick], vn["nz"][pick]])
+    X = M.encode(P, Nn, (-100.0,) * 3, (100.0,) * 3)
+    gpu = np.column_stack([o[c][:n].cpu().numpy()[pick] for c in "rgb"]).astype(np.float64)
+    ref_model = M.forward(w, X, bf16=True).y
+    ref_fp64 = M.forward(w, X, bf16=False).y
+    rmse = lambda a, b: [float(np.sqrt(((a[:, j] - b[:, j]) ** 2).mean())) for j in range(3)]
+    tab.close()
+    net.close()
+    peak = 1915.4
+    return {
+        "workload": "hd temporal + learned fallback (count < 4), 4 x 16384 samples/frame",
+        "ms_filter": t_f / k, "ms_train": t_t / k, "ms_infer": t_i / k,
+        "ms_frame": (t_f + t_t + t_i) / k,
+        "lowcount_vertices_per_frame": n_low / k,
+        "train_tflops": train_flop / (t_t / k * 1e-3) / 1e12,
+        "infer_tflops": infer_flop / (t_i / k * 1e-3) / 1e12 if t_i > 0 else None,
+        "bf16_peak_tflops": peak,
+        "rmse_vs_fp64_oracle_rgb": rmse(gpu, ref_fp64),
+        "rmse_vs_oracle_bf16_model_rgb": rmse(gpu, ref_model),
+        "rms_prediction_rgb": [float(np.sqrt((ref_fp64[:, j] ** 2).mean())) for j in range(3)],
+    }
+
+
+def batched_leg(steps_timed=8, tune=True):
+    """The batched workload: 8 views of uneven resolution (2x each 1280x720,
+    1920x1080, 2560x1440, 3840x2160), 1 path per pixel, 2 bounces, each view
+    with its own table; table size and probe limit per view and the batch
+    width chosen by the autotuner on the first frame (off the timed path);
+    then graph replays of the one persistent launch, timed with CUDA events,
+    against the same views filtered one pps_filter call at a time."""
+    import torch
+    from paper_1902_05942_gb300 import autotune, configs, pps, scene
+    w = configs.batched()
+    views = []
+    for i, spec in enumerate(w.streams):
+        v = scene.trace_stream(spec, 0, "cuda")
+        views.append(({k: v[k] for k in scene.STREAMS}, tuple(spec.view.eye)))
+    torch.cuda.synchronize()
+    cfgs, tuned = [], []
+    for i, (v, eye) in enumerate(views):
+        cfg = w.filters[i]
+        if tune:
+            cfg, trials = autotune.tune_view(cfg, v, eye, log2_range=(21, 24), probes=(8, 16, 32))
+        cfgs.append(cfg)
+        tuned.append({"view": f"{w.streams[i].view.width}x{w.streams[i].view.height}",
+                      "vertices": v["px"].numel(), "log2_slots": cfg.log2_slots,
+                      "max_probes": cfg.max_probes})
+    outs = [pps.empty_output(v["px"].numel(), "cuda", count=False) for v, _ in views]
+    cams = [eye for _, eye in views]
+
+    def make(width):
+        tabs = []
+        for cfg in cfgs:
+            t = pps.Table(cfg)
+            t.tune(width)
+            tabs.append(t)
+        b = pps.Batch([(tabs[i], views[i][0], outs[i]) for i in range(len(views))])
+        b._tables = tabs
+        return b
+
+    width, wt = autotune.tune_batch_width(make, cams) if tune else (2, {})
+    batch = make(width)
+    total = sum(v["px"].numel() for v, _ in views)
+    for i in range(3):
+        batch.run(cams, i)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for i in range(steps_timed):
+        batch.run(cams, 3 + i)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps_timed
+    # the same views, one call per view
+    tabs = [pps.Table(c) for c in cfgs]
+    for t in tabs:
+        t.tune(width)
+    def seq(f):
+        for i, (v, eye) in enumerate(views):
+            tabs[i].filter(v, eye, f, out=outs[i])
+    seq(0)
+    torch.cuda.synchronize()
+    e0.record()
+    for i in range(steps_timed):
+        seq(1 + i)
+    e1.record()
+    torch.cuda.synchronize()
+    ms_seq = e0.elapsed_time(e1) / steps_timed
+    batch.close()
+    for t in tabs + batch._tables:
+        t.close()
+    return {"workload": "8 views (2x 720p/1080p/1440p/2160p), 2 bounces, one persistent launch "
+                        "replayed from a CUDA graph",
+            "vertices_per_frame": total, "ms_per_frame": ms,
+            "vertices_per_s": total / (ms * 1e-3),
+            "ms_per_frame_one_call_per_view": ms_seq,
+            "batch_width": width, "batch_width_trials_ms": wt, "views": tuned}
 
 
 def _oracle_step(v_np, w, frame, eye, hist):
@@ -403,6 +554,8 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=1_500_000)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mlp", action="store_true", help="skip the learned-fallback leg")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched-views leg")
     ap.add_argument("--ncu-case", action="store_true", help="small fixed case for profilers")
     ap.add_argument("--rates", action="store_true", help="random memory-operation rates")
     ap.add_argument("--hist", type=int, default=1, help="--ncu-case: history mode")

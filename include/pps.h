@@ -309,6 +309,39 @@ int pps_stats(pps_table *t, pps_stats_t *out, void *stream);
  */
 int pps_table_dump(pps_table *t, uint32_t *fp_host, void *acc_host, void *stream);
 
+/* ---- batched views ------------------------------------------------------ */
+/*
+ * Several views (cameras) filtered in one persistent launch: every view keeps
+ * its own table (own size, probe limit, history), camera and vertex batch
+ * (Sec. 3 per view); the tiles of all views are handed out from one counter so
+ * that views of uneven size share the GPU, and the launch is replayed from a
+ * CUDA graph.
+ *
+ *  pps_view   table: the view's table; v, n: its vertices (device); out: its
+ *             results (device; count and status optional).
+ *
+ * pps_batch_create records the launch for these arrays (pointers and sizes are
+ * fixed from then on); blend != 0 blends the views whose table keeps a history
+ * (alpha as in pps_blend).  While the batch exists, use its tables only
+ * through pps_batch_run (and pps_stats / pps_table_dump between runs).
+ * pps_batch_run filters one frame of every view: cams[i] is view i's camera,
+ * `frame` the jitter key word; it may wait for the run two calls back.
+ * Errors: PPS_EINVAL, PPS_ESTATE, PPS_ENOMEM, PPS_ECUDA.
+ */
+typedef struct pps_view {
+  pps_table *table;
+  pps_vertices v;
+  size_t n;
+  pps_output out;
+} pps_view;
+
+typedef struct pps_batch pps_batch;
+
+int pps_batch_create(pps_batch **out, const pps_view *views, uint32_t nviews, int blend,
+                     float alpha);
+int pps_batch_run(pps_batch *b, const pps_camera *cams, uint32_t frame, void *stream);
+int pps_batch_destroy(pps_batch *b);
+
 /* ---- learned fallback --------------------------------------------------- */
 /*
  * A small network that answers for vertices whose cell holds too few samples

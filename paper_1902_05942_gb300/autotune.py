@@ -1,0 +1,60 @@
+"""Autotuner for table size, probe limit and launch shape.
+
+Off the timed path, on a sample frame of each view: for every candidate table
+size (2^lo .. 2^hi slots) and probe limit, filter the view a few times with the
+library's fused launch, time it with CUDA events and read the overflow count;
+keep the fastest candidate whose overflowing share of vertices stays below
+`max_overflow` (if none does, the one with the least overflow).  Then choose
+the batch width (vertices per thread per insert step) of a batched launch by
+timing the whole batch with each width.  The paper sizes the table in
+proportion to the image (Sec. 4); the candidate range brackets that choice.
+"""
+from __future__ import annotations
+
+import dataclasses
+from typing import Dict, List, Sequence, Tuple
+
+import torch
+
+from . import pps
+
+
+def _time(fn, reps: int) -> float:
+    fn()  # warm-up
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def tune_view(cfg, v: Dict[str, torch.Tensor], eye, log2_range=(21, 24),
+              probes: Sequence[int] = (8, 16, 32), reps: int = 3, max_overflow: float = 1e-5):
+    """Best (log2_slots, max_probes) for one view; returns (config, table of trials)."""
+    n = v["px"].numel()
+    out = pps.empty_output(n, v["px"].device, count=False)
+    trials = []
+    for lg in range(log2_range[0], log2_range[1] + 1):
+        for P in probes:
+            c = dataclasses.replace(cfg, log2_slots=lg, max_probes=P, hist_mode=0)
+            tab = pps.Table(c)
+            ms = _time(lambda: tab.filter(v, eye, 0, out=out), reps)
+            ovf = tab.stats()["overflow_vertices"] / max(n, 1)
+            tab.close()
+            trials.append({"log2_slots": lg, "max_probes": P, "ms": ms, "overflow": ovf})
+    ok = [t for t in trials if t["overflow"] <= max_overflow]
+    best = min(ok, key=lambda t: t["ms"]) if ok else min(trials, key=lambda t: (t["overflow"], t["ms"]))
+    return dataclasses.replace(cfg, log2_slots=best["log2_slots"], max_probes=best["max_probes"]), trials
+
+
+def tune_batch_width(make_batch, cams, reps: int = 3, widths: Sequence[int] = (2, 4)) -> Tuple[int, Dict[int, float]]:
+    """Fastest batch width for a batched launch; `make_batch(width)` builds it."""
+    times = {}
+    for w in widths:
+        b = make_batch(w)
+        times[w] = _time(lambda: b.run(cams, 0), reps)
+        b.close()
+    return min(times, key=times.get), times

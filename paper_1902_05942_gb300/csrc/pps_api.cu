@@ -439,6 +439,28 @@ int pps_filter_host(pps_table* t, const pps_camera* cam, uint32_t frame, const p
   return PPS_OK;
 }
 
+}  // extern "C"
+
+namespace pps {
+// For batched launches: the device description of a table about to filter n
+// vertices in one persistent launch (cell-id capacity ensured), its batch
+// width, and whether it keeps a history.  The table must be between frames.
+int table_for_batch(pps_table* t, size_t n, ViewDesc* vd, int* batch, bool* temporal_out,
+                    cudaStream_t st) {
+  if (int rc = check_table(t)) return rc;
+  if (t->state != kClean) return fail(PPS_ESTATE, "a table of a batch is in the middle of a frame");
+  const size_t ftile = static_cast<size_t>(fused_tile_size());
+  if (int rc = ensure_dense(t, (n + ftile - 1) / ftile * ftile, 0, st)) return rc;
+  vd->kc = t->kc;
+  vd->t = t->dev;
+  *batch = batch_of(t);
+  *temporal_out = temporal(t);
+  return PPS_OK;
+}
+}  // namespace pps
+
+extern "C" {
+
 int pps_set_tuning(pps_table* t, const pps_tuning* tune) {
   if (int rc = check_table(t)) return rc;
   if (!tune) return fail(PPS_EINVAL, "tuning is NULL");

@@ -19,6 +19,40 @@ struct FusedPlan {
   bool global_stash = false;
 };
 
+// One view of a batched launch: its table, key constants, vertices and
+// outputs, and its place in the batch's tile space.
+struct ViewDesc {
+  KeyConst kc;
+  TableDev t;
+  VertexPtrs v;
+  OutPtrs o;
+  unsigned long long n;
+  uint32_t tile_base;  // first tile of this view in the batch
+  uint32_t ntiles;
+  int vec, ovec;
+  int blended;  // blend this view's cells (temporal table and blending requested)
+  int sweep;    // zero this view's slot table by a sweep at the end
+};
+
+struct MultiPlan {
+  int grid = 0, block = 0, batch = 2;
+  uint32_t cap_tiles = 0;
+  size_t smem = 0;
+  bool global_stash = false;
+};
+
+// Plan / launch the batched persistent kernel over `total_tiles` tiles of the
+// views in device memory (`views`, nviews entries); `ctrl` carries the grid
+// barrier and the tile counter; `gstash` (total_tiles tiles) is used when the
+// stash does not fit on chip.
+cudaError_t plan_multi(size_t total_tiles, bool temporal, int batch, MultiPlan* plan);
+cudaError_t launch_multi(const ViewDesc* views, uint32_t nviews, uint32_t total_tiles, Ctrl* ctrl,
+                         bool temporal, float alpha, const MultiPlan& plan, uint32_t* gstash,
+                         cudaStream_t st);
+bool vec_inputs_host(const VertexPtrs& v);
+bool vec_outputs_host(const OutPtrs& o);
+bool sweep_pays_host(const TableDev& t, size_t vertices);
+
 cudaError_t launch_insert(const KeyConst& kc, const TableDev& t, const VertexPtrs& v, size_t n,
                           uint32_t* id_out, uint32_t tile_base, int batch, cudaStream_t st);
 cudaError_t launch_query(const KeyConst& kc, const TableDev& t, const VertexPtrs& v, size_t n,
@@ -40,5 +74,13 @@ int fused_tile_size();  // vertices (and cell ids) per tile of the persistent ke
 bool aligned16(const void* p);
 
 int record_error(int code, const char* msg);  // message for pps_last_error()
+
+}  // namespace pps
+
+struct pps_table;
+
+namespace pps {
+int table_for_batch(pps_table* t, size_t n, ViewDesc* vd, int* batch, bool* temporal,
+                    cudaStream_t st);
 
 }  // namespace pps

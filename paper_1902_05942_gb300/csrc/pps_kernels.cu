@@ -652,6 +652,155 @@ __global__ void __launch_bounds__(kFusedBlock, W == 4 ? 1 : 2) k_fused(FusedArgs
                 static_cast<size_t>(gridDim.x) * blockDim.x);
 }
 
+// The batched persistent kernel: the same phases as k_fused over the tiles of
+// several views, each with its own table.  Tiles are numbered across views
+// (view v owns tiles [tile_base, tile_base + ntiles)) and handed out from one
+// counter; a CTA copies the descriptor of the view of each tile it takes into
+// shared memory and remembers (view, tile) for the later phases.
+struct MultiArgs {
+  const ViewDesc* views;
+  Ctrl* ctrl;  // grid barrier and tile counter of the batch
+  uint32_t* gstash;
+  uint32_t nviews, total_tiles, cap_tiles;
+  float alpha;
+};
+
+__device__ __forceinline__ void copy_view(ViewDesc* dst, const ViewDesc* src) {
+  const int words = static_cast<int>(sizeof(ViewDesc) / sizeof(uint32_t));
+  for (int i = threadIdx.x; i < words; i += blockDim.x)
+    reinterpret_cast<uint32_t*>(dst)[i] = reinterpret_cast<const uint32_t*>(src)[i];
+}
+
+template <bool TEMPORAL, int W>
+__global__ void __launch_bounds__(kFusedBlock, W == 4 ? 1 : 2) k_fused_multi(MultiArgs a) {
+  extern __shared__ __align__(16) uint32_t s_stash[];
+  __shared__ uint32_t s_tile[kMaxTilesPerCta];
+  __shared__ uint32_t s_claims[kMaxTilesPerCta];
+  __shared__ uint16_t s_view[kMaxTilesPerCta];
+  __shared__ __align__(16) ViewDesc s_vd;
+  __shared__ uint32_t s_next, s_taken;
+  __shared__ unsigned long long s_ovf, s_cells;
+  if (threadIdx.x == 0) s_taken = 0;
+
+  // Phase A: keys, probing insert, accumulation, tile by tile across views.
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      uint32_t gt = a.total_tiles;
+      if (s_taken < a.cap_tiles) gt = static_cast<uint32_t>(atomicAdd(&a.ctrl->tile_next, 1ull));
+      s_next = gt;
+      if (gt < a.total_tiles) {
+        uint32_t v = 0;
+        while (v + 1 < a.nviews && a.views[v + 1].tile_base <= gt) ++v;
+        s_view[s_taken] = static_cast<uint16_t>(v);
+        s_tile[s_taken] = gt - a.views[v].tile_base;
+        s_claims[s_taken] = 0;
+      }
+      s_ovf = 0;
+      s_cells = 0;
+    }
+    __syncthreads();
+    const uint32_t gt = s_next;
+    if (gt >= a.total_tiles) break;
+    const uint32_t k = s_taken;
+    copy_view(&s_vd, a.views + s_view[k]);
+    __syncthreads();
+    const size_t t0 = static_cast<size_t>(s_tile[k]) * kFusedTile;
+    const size_t end = min(static_cast<size_t>(s_vd.n), t0 + kFusedTile);
+    uint32_t* stash = a.gstash ? a.gstash + static_cast<size_t>(gt) * kFusedTile
+                               : s_stash + static_cast<size_t>(k) * kFusedTile;
+    Counters c;
+#pragma unroll 1
+    for (int sub = 0; sub < 4; sub += W) {
+      const size_t j = t0 + threadIdx.x * 4 + sub;
+      if (j < end) {
+        const Batch<W> b = insert_batch<W>(s_vd.kc, s_vd.t, s_vd.v, j, end, s_vd.vec != 0,
+                                           static_cast<uint32_t>(t0), &s_claims[k], c);
+#pragma unroll
+        for (int q = 0; q < W; ++q) stash[j - t0 + q] = b.id[q];
+      }
+    }
+    // per-view counters of this tile
+    unsigned long long o = c.ovf, cl = c.cells;
+    for (int off = 16; off > 0; off >>= 1) {
+      o += __shfl_xor_sync(0xFFFFFFFFu, o, off);
+      cl += __shfl_xor_sync(0xFFFFFFFFu, cl, off);
+    }
+    if ((threadIdx.x & 31) == 0) {
+      if (o) atomicAdd(&s_ovf, o);
+      if (cl) atomicAdd(&s_cells, cl);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      if (s_ovf) atomicAdd(&s_vd.t.ctrl->overflow_vertices, s_ovf);
+      if (s_cells) atomicAdd(&s_vd.t.ctrl->frame_cells, s_cells);
+      atomicAdd(&s_vd.t.ctrl->vertices, static_cast<unsigned long long>(end - t0));
+      ++s_taken;
+    }
+  }
+  if (!grid_barrier(a.ctrl, gridDim.x)) return;
+  const uint32_t taken = s_taken;
+
+  // Phase B: temporal blend of the cells this CTA's tiles created.
+  if (TEMPORAL) {
+    for (uint32_t k = 0; k < taken; ++k) {
+      __syncthreads();
+      copy_view(&s_vd, a.views + s_view[k]);
+      __syncthreads();
+      if (!s_vd.blended) continue;
+      unsigned long long n_hovf = 0;
+      blend_range<W>(s_vd.t, s_tile[k] * static_cast<uint32_t>(kFusedTile), s_claims[k],
+                     threadIdx.x, blockDim.x, a.alpha, n_hovf);
+      if (n_hovf) atomicAdd(&s_vd.t.ctrl->hist_overflow, n_hovf);
+    }
+    if (!grid_barrier(a.ctrl, gridDim.x)) return;
+  }
+
+  // Phase C: one lookup per vertex of this CTA's tiles.
+  for (uint32_t k = 0; k < taken; ++k) {
+    __syncthreads();
+    copy_view(&s_vd, a.views + s_view[k]);
+    __syncthreads();
+    const size_t t0 = static_cast<size_t>(s_tile[k]) * kFusedTile;
+    const size_t end = min(static_cast<size_t>(s_vd.n), t0 + kFusedTile);
+    const size_t gt = static_cast<size_t>(s_vd.tile_base) + s_tile[k];
+    const uint32_t* stash = a.gstash ? a.gstash + gt * kFusedTile
+                                     : s_stash + static_cast<size_t>(k) * kFusedTile;
+    const bool blended = TEMPORAL && s_vd.blended;
+#pragma unroll 1
+    for (int sub = 0; sub < 4; sub += W) {
+      const size_t j = t0 + threadIdx.x * 4 + sub;
+      if (j < end) {
+        uint32_t id[W];
+#pragma unroll
+        for (int q = 0; q < W; ++q) id[q] = stash[j - t0 + q];
+        Result res[W];
+        resolve_batch<W>(s_vd.t, s_vd.v, j, end, id, blended, res);
+        store_batch<W>(s_vd.o, j, end, s_vd.ovec != 0, res);
+      }
+    }
+  }
+  if (!grid_barrier(a.ctrl, gridDim.x)) return;
+
+  // Phase D: empty the cells this CTA's tiles created; sweep the slot tables
+  // of the views that are swept.
+  for (uint32_t k = 0; k < taken; ++k) {
+    __syncthreads();
+    copy_view(&s_vd, a.views + s_view[k]);
+    __syncthreads();
+    clear_range(s_vd.t, s_tile[k] * static_cast<uint32_t>(kFusedTile), s_claims[k], threadIdx.x,
+                blockDim.x, s_vd.sweep != 0);
+  }
+  for (uint32_t v = 0; v < a.nviews; ++v) {
+    __syncthreads();
+    copy_view(&s_vd, a.views + v);
+    __syncthreads();
+    if (s_vd.sweep)
+      sweep_slots(s_vd.t, blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x,
+                  static_cast<size_t>(gridDim.x) * blockDim.x);
+  }
+}
+
 int sm_count() {
   static int cached = 0;
   if (!cached) {
@@ -758,9 +907,9 @@ static const void* fused_kernel(bool temporal, int batch) {
 // Largest dynamic shared memory a k_fused CTA may request: the opt-in limit
 // per block minus the kernel's static shared memory (set once per kernel).
 static cudaError_t fused_dyn_smem_limit(const void* fn, size_t* limit) {
-  static const void* done[4] = {nullptr, nullptr, nullptr, nullptr};
-  static size_t lims[4] = {0, 0, 0, 0};
-  for (int i = 0; i < 4; ++i)
+  static const void* done[8] = {nullptr};
+  static size_t lims[8] = {0};
+  for (int i = 0; i < 8; ++i)
     if (done[i] == fn) {
       *limit = lims[i];
       return cudaSuccess;
@@ -774,7 +923,7 @@ static cudaError_t fused_dyn_smem_limit(const void* fn, size_t* limit) {
   const size_t lim = static_cast<size_t>(maxopt) - fa.sharedSizeBytes;
   e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(lim));
   if (e != cudaSuccess) return e;
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < 8; ++i)
     if (!done[i]) {
       done[i] = fn;
       lims[i] = lim;
@@ -845,6 +994,75 @@ cudaError_t launch_fused(const KeyConst& kc, const TableDev& t, const VertexPtrs
   a.sweep = sweep_pays(t, n) ? 1 : 0;
   void* args[] = {&a};
   return cudaLaunchCooperativeKernel(fused_kernel(temporal, plan.batch), dim3(plan.grid),
+                                     dim3(plan.block), args, plan.smem, st);
+}
+
+bool vec_inputs_host(const VertexPtrs& v) { return vec_inputs(v); }
+bool vec_outputs_host(const OutPtrs& o) { return vec_outputs(o); }
+bool sweep_pays_host(const TableDev& t, size_t vertices) { return sweep_pays(t, vertices); }
+
+template <bool TEMPORAL, int W>
+static const void* multi_fn() {
+  return reinterpret_cast<const void*>(k_fused_multi<TEMPORAL, W>);
+}
+
+static const void* multi_kernel(bool temporal, int batch) {
+  if (temporal) return batch == 2 ? multi_fn<true, 2>() : multi_fn<true, 4>();
+  return batch == 2 ? multi_fn<false, 2>() : multi_fn<false, 4>();
+}
+
+cudaError_t plan_multi(size_t total_tiles, bool temporal, int batch, MultiPlan* plan) {
+  const void* fn = multi_kernel(temporal, batch);
+  const int sms = sm_count();
+  size_t maxdyn = 0;
+  cudaError_t e = fused_dyn_smem_limit(fn, &maxdyn);
+  if (e != cudaSuccess) return e;
+  int b0 = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b0, fn, kFusedBlock, 0);
+  if (e != cudaSuccess) return e;
+  if (b0 < 1) return cudaErrorInvalidConfiguration;
+  int dev = 0, smem_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  const size_t tile_bytes = kFusedTile * sizeof(uint32_t);
+  plan->block = kFusedBlock;
+  plan->batch = batch;
+  for (int b = b0; b >= 1; --b) {
+    const size_t per = std::min(maxdyn, static_cast<size_t>(smem_sm) / b - 12 * 1024);
+    const size_t cap = std::min<size_t>(per / tile_bytes, kMaxTilesPerCta);
+    if (cap == 0 || cap * static_cast<size_t>(sms) * b < total_tiles) continue;
+    int nb = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, kFusedBlock, cap * tile_bytes);
+    if (e != cudaSuccess) return e;
+    if (nb >= b) {
+      plan->grid = sms * b;
+      plan->cap_tiles = static_cast<uint32_t>(cap);
+      plan->smem = cap * tile_bytes;
+      plan->global_stash = false;
+      return cudaSuccess;
+    }
+  }
+  plan->grid = sms * b0;
+  plan->cap_tiles = kMaxTilesPerCta;
+  plan->smem = 0;
+  plan->global_stash = true;
+  if (static_cast<size_t>(plan->grid) * kMaxTilesPerCta < total_tiles) return cudaErrorInvalidValue;
+  return cudaSuccess;
+}
+
+cudaError_t launch_multi(const ViewDesc* views, uint32_t nviews, uint32_t total_tiles, Ctrl* ctrl,
+                         bool temporal, float alpha, const MultiPlan& plan, uint32_t* gstash,
+                         cudaStream_t st) {
+  MultiArgs a;
+  a.views = views;
+  a.ctrl = ctrl;
+  a.gstash = plan.global_stash ? gstash : nullptr;
+  a.nviews = nviews;
+  a.total_tiles = total_tiles;
+  a.cap_tiles = plan.cap_tiles;
+  a.alpha = alpha;
+  void* args[] = {&a};
+  return cudaLaunchCooperativeKernel(multi_kernel(temporal, plan.batch), dim3(plan.grid),
                                      dim3(plan.block), args, plan.smem, st);
 }
 

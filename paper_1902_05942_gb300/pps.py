@@ -65,6 +65,10 @@ class pps_stats_t(ctypes.Structure):
                 ("device_error", _u32), ("frame", _u32)]
 
 
+class pps_view(ctypes.Structure):
+    _fields_ = [("table", _vp), ("v", pps_vertices), ("n", ctypes.c_size_t), ("out", pps_output)]
+
+
 class pps_mlp_params(ctypes.Structure):
     _fields_ = [("box_min", _f32 * 3), ("box_max", _f32 * 3), ("lr", _f32), ("beta1", _f32),
                 ("beta2", _f32), ("eps", _f32), ("batch", _u32), ("steps", _u32),
@@ -110,6 +114,10 @@ SIGNATURES = {
                         ctypes.c_int),
     "pps_mlp_gradient": ([_vp, ctypes.POINTER(pps_vertices), _vp, _vp, _vp, _vp, _u32, _vp, _vp],
                          ctypes.c_int),
+    "pps_batch_create": ([ctypes.POINTER(_vp), ctypes.POINTER(pps_view), _u32, ctypes.c_int, _f32],
+                         ctypes.c_int),
+    "pps_batch_run": ([_vp, ctypes.POINTER(pps_camera), _u32, _vp], ctypes.c_int),
+    "pps_batch_destroy": ([_vp], ctypes.c_int),
     "pps_bench_rate": ([ctypes.c_int, ctypes.c_size_t, ctypes.c_size_t, _vp, _vp,
                         ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
 }
@@ -301,6 +309,41 @@ def pps_bench_rate(kind: str, region: torch.Tensor, ops: int, stream=None) -> fl
     if rc:
         raise PPSError(rc, "pps_bench_rate failed")
     return out.value
+
+
+# ---------------------------------------------------------------- batched views
+class Batch:
+    """Several views in one persistent launch replayed from a CUDA graph.
+
+    views: list of (Table, vertex dict, output dict).  The arrays must stay
+    alive (and in place) for the batch's lifetime."""
+
+    def __init__(self, views, blend=False, alpha=0.2):
+        self._keep = views
+        arr = (pps_view * len(views))()
+        for i, (tab, v, out) in enumerate(views):
+            n = v["px"].numel()
+            arr[i] = pps_view(tab.handle, make_vertices(v, n), n, make_output(out, n))
+        h = _vp()
+        _check(lib().pps_batch_create(ctypes.byref(h), arr, len(views), 1 if blend else 0,
+                                      float(alpha)))
+        self.handle = h.value
+        self.n = len(views)
+
+    def run(self, cams, frame, stream=None):
+        c = (pps_camera * self.n)(*[camera(x) for x in cams])
+        _check(lib().pps_batch_run(self.handle, c, frame & 0xFFFFFFFF, _stream(stream)))
+
+    def close(self):
+        if self.handle:
+            lib().pps_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # ---------------------------------------------------------------- learned fallback

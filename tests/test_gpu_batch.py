@@ -1,0 +1,89 @@
+"""Batched views: one persistent launch over several tables equals filtering
+each view on its own (bit-exact in fixed-point mode), frame after frame."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import pps_oracle as O
+from paper_1902_05942_gb300 import configs, pps, scene
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1902_05942_gb300 import build
+    build.build()
+    torch.cuda.set_device(0)
+    yield
+
+
+SIZES = [(96, 80, 17), (200, 150, 18), (64, 48, 16), (150, 100, 19)]
+
+
+def _view(i, w, h, frame):
+    eye = (3.0 * np.sin(i), 3.0, -12.0 * np.cos(0.3 * i))
+    spec = scene.StreamSpec(view=scene.View(w, h, eye=eye, target=(0.0, 0.5, 0.0)), bounces=2,
+                            survival=0.6, path_seed=2 + 7 * i, radiance_seed=3 + 7 * i)
+    v = scene.trace_stream(spec, frame, "cuda")
+    return spec, {k: v[k] for k in scene.STREAMS}
+
+
+@pytest.mark.parametrize("hist,blend", [(0, False), (1, True)])
+def test_batch_equals_separate_views(hist, blend):
+    frames = 3
+    cfgs, tabs_b, tabs_s, data, outs = [], [], [], [], []
+    for i, (w, h, lg) in enumerate(SIZES):
+        cfg = configs.FilterConfig(log2_slots=lg, max_probes=16, voxel_scale=4.0,
+                                   pixel_angle=scene.View(w, h).pixel_angle(), accum_fixed=True,
+                                   hist_mode=hist, log2_hist_slots=lg + 1)
+        cfgs.append(cfg)
+        tabs_b.append(pps.Table(cfg))
+        tabs_s.append(pps.Table(cfg))
+        spec, d = _view(i, w, h, 0)
+        # the batch reads fixed arrays: refresh their contents in place per frame
+        data.append((spec, {k: t.clone() for k, t in d.items()}))
+        outs.append(pps.empty_output(d["px"].numel(), "cuda"))
+    batch = pps.Batch([(tabs_b[i], data[i][1], outs[i]) for i in range(len(SIZES))],
+                      blend=blend, alpha=0.2)
+    for f in range(frames):
+        cams = []
+        for i, (w, h, _) in enumerate(SIZES):
+            spec, d = _view(i, w, h, f)
+            n = min(d["px"].numel(), data[i][1]["px"].numel())
+            for k in scene.STREAMS:
+                data[i][1][k][:n].copy_(d[k][:n])
+            cams.append(spec.view.eye)
+        batch.run(cams, f)
+        torch.cuda.synchronize()
+        for i in range(len(SIZES)):
+            ref = tabs_s[i].filter(data[i][1], cams[i], f, blend=blend, alpha=0.2)
+            for c in ("r", "g", "b", "count", "status"):
+                assert torch.equal(outs[i][c], ref[c]), (f, i, c)
+            st = tabs_b[i].stats()
+            assert st["vertices"] == data[i][1]["px"].numel()
+    # one view against the oracle (last frame, no history)
+    if hist == 0:
+        spec, d = data[1]
+        fr = O.filter_frame(O.KeyParams(**cfgs[1].oracle_kwargs()), cams[1], frames - 1,
+                            {k: t.cpu().numpy() for k, t in d.items()})
+        st = outs[1]["status"].cpu().numpy()
+        ok = st != 2
+        assert np.array_equal(outs[1]["count"].cpu().numpy()[ok].astype(np.int64), fr.count[ok])
+        assert np.array_equal(torch.stack([outs[1][c] for c in "rgb"], 1).cpu().numpy()[ok],
+                              fr.mean_fixed[ok])
+    batch.close()
+    for t in tabs_b + tabs_s:
+        t.close()
+
+
+def test_batch_rejects_a_table_in_the_middle_of_a_frame():
+    cfg = configs.small().filters[0]
+    tab = pps.Table(cfg)
+    _, d = _view(0, 32, 32, 0)
+    tab.build((0, 3, -12), 0)
+    tab.insert(d)
+    with pytest.raises(pps.PPSError) as e:
+        pps.Batch([(tab, d, pps.empty_output(d["px"].numel(), "cuda"))])
+    assert e.value.code == pps.PPS_ESTATE
+    tab.close()
