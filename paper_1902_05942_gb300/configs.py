@@ -84,7 +84,7 @@ class Workload:
 
 HD_VOXEL_SCALE = 4.0
 SMALL_VOXEL_SCALE = 4.0
-STRESS_VOXEL_SCALE = 2.0
+STRESS_VOXEL_SCALE = 0.5  # load 0.70 at 2^26 slots (47.1 M cells of 61.2 M vertices)
 
 
 def _pixel_angle(v: View) -> float:
