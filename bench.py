@@ -129,6 +129,20 @@ class ClockSampler:
                 "samples": len(self.rows)}
 
 
+def reduce_ranks(ms: float, vertices: float, device=None):
+    """Across ranks: the slowest rank's time and all ranks' vertices (weak
+    scaling; value = total vertices / slowest time).  One rank: unchanged."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return ms, vertices
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    v = torch.tensor([vertices], dtype=torch.float64, device=device)
+    dist.all_reduce(v)
+    return float(t.item()), float(v.item())
+
+
 def make_frames(rank: int, device):
     import torch
     from paper_1902_05942_gb300 import configs, scene
@@ -207,15 +221,7 @@ def run_ours(args):
     for i in range(min(args.steps, FRAMES)):
         step(args.warmup + i)
         cells.append(tab.stats()["frame_cells"])
-    if ws > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-        tn = torch.tensor([total_n], device=dev, dtype=torch.float64)
-        dist.all_reduce(tn)
-        job_n = float(tn.item())
-    else:
-        job_n = float(total_n)
+    ms, job_n = reduce_ranks(ms, float(total_n), dev)
     value = job_n / (ms / 1e3)
     ms_step = ms / args.steps
     # roofline of the dominant (only) kernel: k_fused, one launch per step
@@ -252,13 +258,7 @@ def run_ours(args):
         t0 = time.perf_counter()
         hn = sum(hstep(args.warmup + i) for i in range(args.steps))
         dt = time.perf_counter() - t0
-        if ws > 1:
-            t = torch.tensor([dt], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dt = float(t.item())
-            tn = torch.tensor([hn], device=dev, dtype=torch.float64)
-            dist.all_reduce(tn)
-            hn = float(tn.item())
+        dt, hn = reduce_ranks(dt, float(hn), dev)
         e2e = {"value": hn / dt, "unit": UNIT,
                "h2d_bytes_per_step": int(36 * mean_n), "d2h_bytes_per_step": int(13 * mean_n),
                "ms_per_step": 1e3 * dt / args.steps}
