@@ -26,6 +26,11 @@ What it computes, and from which passage
   integrating weight alpha = N_old / (N_old + N_new).
 * Overflow audit (Sec. 3.2: the probe limit, after which a vertex keeps its
   own unfiltered contribution): a helper that checks a table dump.
+* Fallbacks for cells with few vertices (Sec. 3.3.2 neighborhood search,
+  Sec. 3.3.3 multi-level accumulation): the pooled average of the 3x3x3
+  block of cells around a vertex's cell, and the average of the next coarser
+  resolution, both taken only where the vertex's own cell has fewer than a
+  threshold of members.
 
 Readings where the paper is silent (all listed in the design doc):
 * LOD: l(d) = floor(log2(s * theta_px * d)) read from the exponent bits of the
@@ -47,6 +52,7 @@ Sums are FP64 (the reference value) and, separately, fixed point
 """
 from __future__ import annotations
 
+import dataclasses
 from dataclasses import dataclass
 from typing import Dict, Optional, Sequence, Tuple
 
@@ -488,3 +494,118 @@ def simulate_linear_probing(home: np.ndarray, fp: np.ndarray, log2_slots: int,
         else:
             probes[j] = max_probes
     return slot, probes, table
+
+
+# ----------------------------------------------------------------------------
+# Fallbacks for cells with few vertices (Sec. 3.3): neighborhood search
+# (Sec. 3.3.2) and multi-level accumulation (Sec. 3.3.3).  Both replace the
+# value of a vertex only where its own cell has fewer than `threshold`
+# members.
+# ----------------------------------------------------------------------------
+STATUS_OK = 0
+STATUS_LOWCOUNT = 1
+STATUS_COARSE = 4
+STATUS_NEIGHBORS = 5
+
+
+def coarse_params(p: KeyParams) -> KeyParams:
+    """The next coarser resolution: the footprint scale s doubled.
+
+    fl32(2 s * theta) = 2 fl32(s * theta) exactly, so every level of detail
+    grows by exactly one (before the clamp), the jitter draw (u, w) stays the
+    same and its offset is scaled by the coarser voxel edge 2^(l+1)."""
+    return dataclasses.replace(p, voxel_scale=float(F32(2.0) * F32(p.voxel_scale)))
+
+
+def multilevel_select(fine_value, fine_count, coarse_value, coarse_count, threshold: int):
+    """Multi-level accumulation (Sec. 3.3.3): every vertex is accumulated at
+    its own resolution and at the next coarser one; a vertex whose own cell
+    has fewer than `threshold` members takes the coarser cell's value and
+    count instead (status COARSE).  Works on per-vertex arrays, so the
+    values may be plain averages or temporally blended ones.
+
+    Returns (value (N, 3), count (N,), status (N,) uint8)."""
+    low = np.asarray(fine_count) < threshold
+    value = np.where(low[:, None], coarse_value, fine_value)
+    count = np.where(low, coarse_count, fine_count)
+    status = np.where(low, STATUS_COARSE, STATUS_OK).astype(np.uint8)
+    return value, count, status
+
+
+NEIGHBOR_OFFSETS = np.array([(dx, dy, dz) for dx in (-1, 0, 1) for dy in (-1, 0, 1)
+                             for dz in (-1, 0, 1)], dtype=np.int64)
+
+
+def _row_keys(t: np.ndarray) -> np.ndarray:
+    return np.ascontiguousarray(t, dtype=np.int64).view(np.dtype((np.void, 8 * t.shape[1]))).ravel()
+
+
+def neighbor_cells(tuples: np.ndarray, centers: np.ndarray) -> np.ndarray:
+    """For each center tuple (x~x, x~y, x~z, l', qx, qy, qz) the indices of the
+    27 cells (x~ + o, l', q), o in {-1, 0, 1}^3, among `tuples` (-1 where no
+    such cell exists)."""
+    keys = _row_keys(tuples)
+    order = np.argsort(keys, kind="stable")
+    sk = keys[order]
+    out = np.full((centers.shape[0], NEIGHBOR_OFFSETS.shape[0]), -1, dtype=np.int64)
+    for i, o in enumerate(NEIGHBOR_OFFSETS):
+        q = centers.copy()
+        q[:, :3] += o
+        qk = _row_keys(q)
+        pos = np.searchsorted(sk, qk)
+        posc = np.minimum(pos, sk.shape[0] - 1)
+        hit = (pos < sk.shape[0]) & (sk[posc] == qk)
+        out[hit, i] = order[posc[hit]]
+    return out
+
+
+def neighborhood(fr: FrameResult, threshold: int, cell_value=None, cell_weight=None):
+    """Neighborhood search (Sec. 3.3.2): a vertex whose own cell has fewer
+    than `threshold` members takes the pooled average of the 3 x 3 x 3 block of
+    cells around its cell at the same level and with the same quantized
+    normal, i.e. the members of all those cells averaged together (cells that
+    hold no vertex add nothing); its count becomes the block's member count
+    and its status NEIGHBORS.
+
+    Without `cell_value` the pooled average is (sum of the block's sums) /
+    (sum of its counts), in FP64 and in the fixed-point reading
+    fl32(fl32(sum of fixed sums) * 2^-24) / fl32(count).  With per-cell
+    `cell_value` (C, 3) and `cell_weight` (C,) -- blended values and their
+    counts N after a temporal blend -- it is sum(N c) / sum(N) in FP64, and
+    the low-count test reads N.
+
+    Returns (value64 (N, 3), value_fixed (N, 3) or None, count (N,), status)."""
+    if cell_value is None:
+        w = fr.cell_count
+    else:
+        w = np.asarray(cell_weight, dtype=np.int64)
+    own = w[fr.cell]
+    low = own < threshold
+    if cell_value is None:
+        value64 = fr.mean64.copy()
+        value_fx = fr.mean_fixed.copy()
+    else:
+        value64 = np.asarray(cell_value, dtype=np.float64)[fr.cell].copy()
+        value_fx = None
+    count = own.copy()
+    status = np.zeros(fr.cell.shape[0], dtype=np.uint8)
+    status[low] = STATUS_NEIGHBORS
+    idx = np.nonzero(low)[0]
+    if idx.size == 0:
+        return value64, value_fx, count, status
+    nb = neighbor_cells(fr.tuples, fr.tuples[fr.cell[idx]])
+    ok = nb >= 0
+    nbc = np.where(ok, nb, 0)
+    wn = np.where(ok, w[nbc], 0)
+    tot = wn.sum(axis=1)
+    count[idx] = tot
+    if cell_value is None:
+        s64 = np.where(ok[:, :, None], fr.cell_sum64[nbc], 0.0).sum(axis=1)
+        sfx = np.where(ok[:, :, None], fr.cell_fixed[nbc], 0).sum(axis=1)
+        value64[idx] = s64 / tot[:, None]
+        value_fx[idx] = fixed_mean_f32(sfx, tot)
+    else:
+        cv = np.asarray(cell_value, dtype=np.float64)
+        s64 = np.where(ok[:, :, None], cv[nbc] * wn[:, :, None], 0.0).sum(axis=1)
+        value64[idx] = s64 / tot[:, None]
+    return value64, value_fx, count, status
