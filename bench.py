@@ -221,6 +221,13 @@ def run_ours(args):
     for i in range(min(args.steps, FRAMES)):
         step(args.warmup + i)
         cells.append(tab.stats()["frame_cells"])
+    plain = plain_leg(frames, cfg, calls, args.steps, args.warmup)
+    fallbacks = {}
+    if not args.no_fallbacks:
+        fsteps = min(args.steps, 16)
+        for fb in ("coarse", "neighbors"):
+            fallbacks[fb] = fallback_leg(frames, cfg, calls, fsteps, args.warmup, fb,
+                                         out["status"])
     ms, job_n = reduce_ranks(ms, float(total_n), dev)
     value = job_n / (ms / 1e3)
     ms_step = ms / args.steps
@@ -282,7 +289,13 @@ def run_ours(args):
             "gpu_launches": args.steps,
             "clocks": clk.summary(),
             "e2e": e2e,
+            "plain": dict(plain, temporal_over_plain=ms_step / plain["ms_per_frame"]),
         }
+        if fallbacks:
+            line["fallbacks"] = {
+                "workload": "the headline temporal HD frames with a low-count fallback "
+                            "(count < 4): coarse = multi-level accumulation, neighbors = "
+                            "3x3x3 neighborhood search", **fallbacks}
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(frames[0], w, args.cpu_sample)
         if not args.no_mlp:
@@ -295,6 +308,79 @@ def run_ours(args):
     if ws > 1:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def plain_leg(frames, cfg, calls, steps, warmup):
+    """The same resident HD frames through the plain filter (no history, no
+    blend): one k_fused launch per frame, timed with CUDA events like the
+    headline."""
+    import ctypes
+    import torch
+    from paper_1902_05942_gb300 import pps
+    tab = pps.Table(cfg, hist_mode=0)
+    L = pps.lib()
+    stream = torch.cuda.current_stream()
+
+    def step(i):
+        cam, vs, n, os_ = calls[i % len(calls)]
+        rc = L.pps_filter(tab.handle, ctypes.byref(cam), i, ctypes.byref(vs), n, 0, 0.0,
+                          ctypes.byref(os_), stream.cuda_stream)
+        if rc:
+            raise pps.PPSError(rc, pps.last_error())
+        return n
+
+    for i in range(warmup):
+        step(i)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    total = sum(step(warmup + i) for i in range(steps))
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / steps
+    tab.close()
+    return {"workload": "the same HD frames, plain filter (no temporal blend)",
+            "ms_per_frame": ms, "vertices_per_s": total / steps / (ms * 1e-3)}
+
+
+def fallback_leg(frames, cfg, calls, steps, warmup, fallback, status):
+    """The headline workload (temporal HD frames) with a low-count fallback:
+    "coarse" = multi-level accumulation (a second table one level coarser,
+    Sec. 3.3.3), "neighbors" = neighborhood search over the 3x3x3 block
+    (Sec. 3.3.2).  Same timing as the headline; reports the share of vertices
+    that took the fallback in the last frame."""
+    import ctypes
+    import torch
+    from paper_1902_05942_gb300 import pps
+    tab = pps.Table(cfg, fallback=fallback)
+    L = pps.lib()
+    stream = torch.cuda.current_stream()
+
+    def step(i):
+        cam, vs, n, os_ = calls[i % len(calls)]
+        rc = L.pps_filter(tab.handle, ctypes.byref(cam), i, ctypes.byref(vs), n, 1, cfg.alpha,
+                          ctypes.byref(os_), stream.cuda_stream)
+        if rc:
+            raise pps.PPSError(rc, pps.last_error())
+        return n
+
+    for i in range(warmup):
+        step(i)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    total = sum(step(warmup + i) for i in range(steps))
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / steps
+    # share of the vertices of one more (steady-state) frame that took the fallback
+    n = step(warmup + steps)
+    torch.cuda.synchronize()
+    code = pps.STATUS_COARSE if fallback == "coarse" else pps.STATUS_NEIGHBORS
+    share = float((status[:n] == code).float().mean().item())
+    tab.close()
+    return {"ms_per_frame": ms, "vertices_per_s": total / steps / (ms * 1e-3),
+            "fallback_share": share}
 
 
 MLP_FWD_FLOP = 2 * (80 * 64 + 64 * 64 + 64 * 64 + 64 * 3)  # per sample, algorithmic
@@ -556,6 +642,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mlp", action="store_true", help="skip the learned-fallback leg")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-views leg")
+    ap.add_argument("--no-fallbacks", action="store_true", help="skip the low-count fallback legs")
     ap.add_argument("--ncu-case", action="store_true", help="small fixed case for profilers")
     ap.add_argument("--rates", action="store_true", help="random memory-operation rates")
     ap.add_argument("--hist", type=int, default=1, help="--ncu-case: history mode")

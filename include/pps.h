@@ -49,6 +49,10 @@ extern "C" {
 #define PPS_STATUS_OVERFLOW 2 /* probe limit exceeded: the vertex's own,       */
                               /* unfiltered contribution returned (Sec. 3.2)   */
 #define PPS_STATUS_MLP 3      /* low count: the learned fallback's prediction  */
+#define PPS_STATUS_COARSE 4   /* low count: the next coarser resolution's cell */
+                              /* average (multi-level accumulation, 3.3.3)     */
+#define PPS_STATUS_NEIGHBORS 5 /* low count: pooled average of the 3x3x3 block */
+                              /* of cells around the vertex's (Sec. 3.3.2)     */
 
 /* ---- modes -------------------------------------------------------------- */
 #define PPS_ACCUM_FP32 0  /* FP32 sums, FP32 count lane: red.add.v4.f32         */
@@ -56,6 +60,9 @@ extern "C" {
 #define PPS_HIST_NONE 0   /* no temporal state: every frame starts empty        */
 #define PPS_HIST_FP32 1   /* history average FP32, count uint32                 */
 #define PPS_HIST_FP16 2   /* history average binary16, count uint16 saturating  */
+#define PPS_FALLBACK_NONE 0      /* low-count vertices keep their cell average  */
+#define PPS_FALLBACK_COARSE 1    /* multi-level accumulation (Sec. 3.3.3)       */
+#define PPS_FALLBACK_NEIGHBORS 2 /* neighborhood search (Sec. 3.3.2)            */
 
 /*
  * Table and key parameters (Algorithm 1; Sec. 3.1.1, 3.2, 3.2.1; Sec. 4).
@@ -88,6 +95,29 @@ extern "C" {
  *  lowcount_threshold a returned count below it is flagged LOWCOUNT (Sec. 3.3).
  *  log2_hist_slots    history table size Th = 2^log2_hist_slots (0: same as T),
  *                     4..30; probed with the same limit P.
+ *  fallback           what a vertex whose cell holds fewer than
+ *                     lowcount_threshold members (after a blend: N) receives
+ *                     instead of its cell's average (Sec. 3.3):
+ *                     PPS_FALLBACK_NONE       the cell average, status LOWCOUNT;
+ *                     PPS_FALLBACK_COARSE     multi-level accumulation (3.3.3):
+ *                        the table keeps a second table for the next coarser
+ *                        resolution (voxel_scale doubled, so every level of
+ *                        detail grows by exactly one; same T, P, seeds, modes
+ *                        and its own history), every vertex is inserted into
+ *                        both, and a low-count vertex gets the coarser cell's
+ *                        value and count, status COARSE (unless its coarse
+ *                        insert overflowed: then LOWCOUNT as before);
+ *                     PPS_FALLBACK_NEIGHBORS  neighborhood search (3.3.2): a
+ *                        low-count vertex gets the pooled average of the
+ *                        3 x 3 x 3 block of cells around its own (same level,
+ *                        same quantized normal): the block's summed sums over
+ *                        its summed counts, or after a blend the blended values
+ *                        weighted by their N; count = the block's members,
+ *                        status NEIGHBORS.
+ *                     Fallback tables work with pps_filter and the split calls;
+ *                     pps_batch_create and pps_filter_noalloc reject them, and
+ *                     pps_stats / pps_table_dump / pps_keys describe the
+ *                     table's own (finest) resolution.
  *  reserved           must be zero.
  */
 typedef struct pps_params {
@@ -106,7 +136,8 @@ typedef struct pps_params {
   uint32_t hist_mode;
   uint32_t lowcount_threshold;
   uint32_t log2_hist_slots;
-  uint32_t reserved[3];
+  uint32_t fallback;
+  uint32_t reserved[2];
 } pps_params;
 
 /* Camera position p_cam of Algorithm 1 (world space). */

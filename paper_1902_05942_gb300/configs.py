@@ -60,6 +60,7 @@ class FilterConfig:
     log2_hist_slots: int = 0
     lowcount_threshold: int = 4
     alpha: Optional[float] = None  # temporal blend weight of the old value (< 0: integrate)
+    fallback: str = "none"  # low-count vertices: "none", "coarse" (Sec. 3.3.3), "neighbors" (3.3.2)
 
     def oracle_kwargs(self) -> dict:
         """Plain keyword arguments for the oracle's key parameters."""

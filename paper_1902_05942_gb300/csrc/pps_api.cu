@@ -58,6 +58,9 @@ struct pps_table {
   void* stage = nullptr;  // pps_filter_host device staging
   size_t stage_cap = 0;
   unsigned long long* scratch_u64 = nullptr;  // 1 word for occupancy counting
+  pps_table* coarse = nullptr;  // multi-level accumulation: the next coarser resolution
+  void* fb = nullptr;           // multi-level scratch: coarse results and fine status
+  size_t fb_cap = 0;            // vertices the scratch holds
 };
 
 namespace {
@@ -81,6 +84,9 @@ int check_params(const pps_params* p) {
     return fail(PPS_EINVAL, "log2_hist_slots must be 0 or in [4, 30]");
   if (p->log2_hist_slots != 0 && p->max_probes > (1ull << p->log2_hist_slots))
     return fail(PPS_EINVAL, "max_probes exceeds the history table size");
+  if (p->fallback > PPS_FALLBACK_NEIGHBORS) return fail(PPS_EINVAL, "bad fallback");
+  if (p->fallback == PPS_FALLBACK_COARSE && !std::isfinite(2.0f * p->voxel_scale))
+    return fail(PPS_EINVAL, "voxel_scale too large for a coarser level");
   for (uint32_t r : p->reserved)
     if (r) return fail(PPS_EINVAL, "reserved fields must be zero");
   return PPS_OK;
@@ -216,6 +222,32 @@ void free_all(pps_table* t) {
   cudaFree(t->gstash);
   cudaFree(t->stage);
   cudaFree(t->scratch_u64);
+  cudaFree(t->fb);
+}
+
+// Multi-level scratch for n vertices: the coarse pass's r, g, b, count and
+// status, and a fine status array for callers that pass none.
+int fallback_scratch(pps_table* t, size_t n, pps::OutPtrs* coarse, uint8_t** fine_status) {
+  const size_t nn = (n + 15) & ~static_cast<size_t>(15);
+  if (t->fb_cap < nn) {
+    cudaFree(t->fb);
+    t->fb = nullptr;
+    t->fb_cap = 0;
+    cudaError_t e = cudaMalloc(&t->fb, nn * (4 * sizeof(float) + 2));
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(PPS_ENOMEM, "fallback scratch allocation failed");
+    }
+    t->fb_cap = nn;
+  }
+  float* base = static_cast<float*>(t->fb);
+  coarse->r = base;
+  coarse->g = base + t->fb_cap;
+  coarse->b = base + 2 * t->fb_cap;
+  coarse->count = reinterpret_cast<uint32_t*>(base + 3 * t->fb_cap);
+  coarse->status = reinterpret_cast<uint8_t*>(base + 4 * t->fb_cap);
+  *fine_status = coarse->status + t->fb_cap;
+  return PPS_OK;
 }
 
 }  // namespace
@@ -283,6 +315,18 @@ int pps_create(pps_table** out, const pps_params* p) {
   t->kc.lod_max = p->lod_max;
   t->kc.jitter = p->jitter;
   t->kc.nih = p->normal_in_home_hash;
+  t->dev.neighbors = p->fallback == PPS_FALLBACK_NEIGHBORS ? 1 : 0;
+  if (p->fallback == PPS_FALLBACK_COARSE) {
+    // the next coarser resolution: s doubled, so every level grows by one
+    pps_params pc = *p;
+    pc.voxel_scale = 2.0f * p->voxel_scale;
+    pc.fallback = PPS_FALLBACK_NONE;
+    if (int rc = pps_create(&t->coarse, &pc)) {
+      free_all(t);
+      delete t;
+      return rc;
+    }
+  }
   *out = t;
   return PPS_OK;
 }
@@ -293,6 +337,7 @@ int pps_destroy(pps_table* t) {
   cudaGetDevice(&prev);
   cudaSetDevice(t->device);
   cudaDeviceSynchronize();
+  pps_destroy(t->coarse);
   free_all(t);
   delete t;
   if (prev >= 0) cudaSetDevice(prev);
@@ -306,6 +351,7 @@ int pps_build(pps_table* t, const pps_camera* cam, uint32_t frame, void* stream)
   if (int rc = reset_frame(t, st)) return rc;
   set_camera(t, cam, frame);
   t->state = kOpen;
+  if (t->coarse) return pps_build(t->coarse, cam, frame, stream);
   return PPS_OK;
 }
 
@@ -320,6 +366,7 @@ int pps_insert(pps_table* t, const pps_vertices* v, size_t n, uint32_t* slot_out
   PPS_CUDA(pps::launch_insert(t->kc, t->dev, to_dev(v), n, slot_out, t->frame_tiles,
                               batch_of(t), st));
   t->frame_tiles += static_cast<uint32_t>(tiles);
+  if (t->coarse) return pps_insert(t->coarse, v, n, nullptr, stream);
   return PPS_OK;
 }
 
@@ -330,6 +377,7 @@ int pps_blend(pps_table* t, float alpha, void* stream) {
   if (t->state != kOpen) return fail(PPS_ESTATE, "pps_blend needs an open frame (pps_build, pps_insert)");
   PPS_CUDA(pps::launch_blend(t->dev, t->frame_tiles, alpha, static_cast<cudaStream_t>(stream)));
   t->state = kBlended;
+  if (t->coarse) return pps_blend(t->coarse, alpha, stream);
   return PPS_OK;
 }
 
@@ -339,22 +387,35 @@ int pps_query(pps_table* t, const pps_vertices* v, size_t n, const uint32_t* slo
   if (int rc = check_vertices(v, n)) return rc;
   if (int rc = check_output(out, n)) return rc;
   if (t->state == kClean) return fail(PPS_ESTATE, "pps_query needs an open frame");
+  const cudaStream_t st = static_cast<cudaStream_t>(stream);
   const uint32_t id_limit = t->frame_tiles * static_cast<uint32_t>(pps::tile_size());
-  PPS_CUDA(pps::launch_query(t->kc, t->dev, to_dev(v), n, slot_in, to_dev(out),
-                             t->state == kBlended, id_limit, static_cast<cudaStream_t>(stream)));
+  if (!t->coarse) {
+    PPS_CUDA(pps::launch_query(t->kc, t->dev, to_dev(v), n, slot_in, to_dev(out),
+                               t->state == kBlended, id_limit, st));
+    return PPS_OK;
+  }
+  // multi-level: the fine lookup, the coarse lookup (re-probed), the choice
+  pps::OutPtrs c{}, o = to_dev(out);
+  uint8_t* fstat = nullptr;
+  if (int rc = fallback_scratch(t, n, &c, &fstat)) return rc;
+  pps::OutPtrs f = o;
+  if (!f.status) f.status = fstat;
+  PPS_CUDA(pps::launch_query(t->kc, t->dev, to_dev(v), n, slot_in, f, t->state == kBlended,
+                             id_limit, st));
+  const pps_table* k = t->coarse;
+  PPS_CUDA(pps::launch_query(k->kc, k->dev, to_dev(v), n, nullptr, c, k->state == kBlended,
+                             k->frame_tiles * static_cast<uint32_t>(pps::tile_size()), st));
+  PPS_CUDA(pps::launch_combine_coarse(n, f.status, c, o, st));
   return PPS_OK;
 }
 
-int pps_filter(pps_table* t, const pps_camera* cam, uint32_t frame, const pps_vertices* v,
-               size_t n, int blend, float alpha, const pps_output* out, void* stream) {
-  if (int rc = check_table(t)) return rc;
-  if (!cam) return fail(PPS_EINVAL, "camera is NULL");
-  if (int rc = check_vertices(v, n)) return rc;
-  if (int rc = check_output(out, n)) return rc;
-  if (blend && !temporal(t)) return fail(PPS_EINVAL, "blend needs a table with hist_mode != NONE");
-  if (blend && (!std::isfinite(alpha) || alpha > 1.0f))
-    return fail(PPS_EINVAL, "alpha must be finite and <= 1");
-  const cudaStream_t st = static_cast<cudaStream_t>(stream);
+}  // extern "C"
+
+namespace {
+
+// One resolution of pps_filter: the persistent launch over all n vertices.
+int filter_one(pps_table* t, const pps_camera* cam, uint32_t frame, const pps_vertices* v,
+               size_t n, int blend, float alpha, const pps::OutPtrs& out, cudaStream_t st) {
   if (int rc = reset_frame(t, st)) return rc;
   set_camera(t, cam, frame);
   if (n == 0) return PPS_OK;
@@ -375,11 +436,40 @@ int pps_filter(pps_table* t, const pps_camera* cam, uint32_t frame, const pps_ve
     }
     t->gstash_cap = stash_need;
   }
-  PPS_CUDA(pps::launch_fused(t->kc, t->dev, to_dev(v), n, to_dev(out), temporal(t), blend != 0,
-                             alpha, plan, t->gstash, st));
+  PPS_CUDA(pps::launch_fused(t->kc, t->dev, to_dev(v), n, out, temporal(t), blend != 0, alpha,
+                             plan, t->gstash, st));
   t->state = kClean;
   return PPS_OK;
 }
+
+}  // namespace
+
+extern "C" {
+
+int pps_filter(pps_table* t, const pps_camera* cam, uint32_t frame, const pps_vertices* v,
+               size_t n, int blend, float alpha, const pps_output* out, void* stream) {
+  if (int rc = check_table(t)) return rc;
+  if (!cam) return fail(PPS_EINVAL, "camera is NULL");
+  if (int rc = check_vertices(v, n)) return rc;
+  if (int rc = check_output(out, n)) return rc;
+  if (blend && !temporal(t)) return fail(PPS_EINVAL, "blend needs a table with hist_mode != NONE");
+  if (blend && (!std::isfinite(alpha) || alpha > 1.0f))
+    return fail(PPS_EINVAL, "alpha must be finite and <= 1");
+  const cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (!t->coarse) return filter_one(t, cam, frame, v, n, blend, alpha, to_dev(out), st);
+  // multi-level: both resolutions, then the choice per vertex
+  pps::OutPtrs c{}, o = to_dev(out);
+  uint8_t* fstat = nullptr;
+  if (n && fallback_scratch(t, n, &c, &fstat)) return PPS_ENOMEM;
+  pps::OutPtrs f = o;
+  if (!f.status) f.status = fstat;
+  if (int rc = filter_one(t, cam, frame, v, n, blend, alpha, f, st)) return rc;
+  if (int rc = filter_one(t->coarse, cam, frame, v, n, blend, alpha, c, st)) return rc;
+  if (n) PPS_CUDA(pps::launch_combine_coarse(n, f.status, c, o, st));
+  return PPS_OK;
+}
+
+
 
 int pps_filter_host(pps_table* t, const pps_camera* cam, uint32_t frame, const pps_vertices* vh,
                     size_t n, int blend, float alpha, const pps_output* oh, void* stream) {
@@ -449,6 +539,8 @@ int table_for_batch(pps_table* t, size_t n, ViewDesc* vd, int* batch, bool* temp
                     cudaStream_t st) {
   if (int rc = check_table(t)) return rc;
   if (t->state != kClean) return fail(PPS_ESTATE, "a table of a batch is in the middle of a frame");
+  if (t->p.fallback != PPS_FALLBACK_NONE)
+    return fail(PPS_EINVAL, "batched views take tables without a low-count fallback");
   const size_t ftile = static_cast<size_t>(fused_tile_size());
   if (int rc = ensure_dense(t, (n + ftile - 1) / ftile * ftile, 0, st)) return rc;
   vd->kc = t->kc;
@@ -469,6 +561,7 @@ int pps_set_tuning(pps_table* t, const pps_tuning* tune) {
   for (uint32_t r : tune->reserved)
     if (r) return fail(PPS_EINVAL, "reserved fields must be zero");
   t->tune = *tune;
+  if (t->coarse) t->coarse->tune = *tune;
   return PPS_OK;
 }
 

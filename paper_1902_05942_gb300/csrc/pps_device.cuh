@@ -88,6 +88,7 @@ struct TableDev {
   uint32_t lowcount;
   int fixed;                  // accumulation mode
   int hist_mode;              // 0 none, 1 FP32, 2 FP16
+  int neighbors;              // low-count vertices take the 3x3x3 pooled average
 };
 
 constexpr uint32_t kNoSlot = 0xFFFFFFFFu;  // info.x of an id reserved but not used
@@ -181,9 +182,15 @@ struct Key {
   uint32_t fp;
 };
 
-__device__ __forceinline__ Key vertex_key(const KeyConst& kc, float px, float py, float pz,
-                                          float nx, float ny, float nz, uint32_t id,
-                                          uint32_t stream_id) {
+// The words a key is hashed from: the quantized position x~ (three int32 as
+// bits), the level l' and the packed quantized normal.
+struct KeyWords {
+  uint32_t X, Y, Z, L, NQ;
+};
+
+__device__ __forceinline__ KeyWords key_words(const KeyConst& kc, float px, float py, float pz,
+                                              float nx, float ny, float nz, uint32_t id,
+                                              uint32_t stream_id) {
   const int l0 = level_of_detail(kc, px, py, pz);
   float xj = px, yj = py, zj = pz;
   int l1 = l0;
@@ -209,36 +216,72 @@ __device__ __forceinline__ Key vertex_key(const KeyConst& kc, float px, float py
     l1 = level_of_detail(kc, xj, yj, zj);
   }
   const float inv = pow2_int(-l1);
-  const uint32_t X = static_cast<uint32_t>(quantize_coord(xj, inv));
-  const uint32_t Y = static_cast<uint32_t>(quantize_coord(yj, inv));
-  const uint32_t Z = static_cast<uint32_t>(quantize_coord(zj, inv));
-  const uint32_t L = static_cast<uint32_t>(l1);
-  const uint32_t NQ = quantize_normal(nx) | (quantize_normal(ny) << 8) | (quantize_normal(nz) << 16);
+  KeyWords kw;
+  kw.X = static_cast<uint32_t>(quantize_coord(xj, inv));
+  kw.Y = static_cast<uint32_t>(quantize_coord(yj, inv));
+  kw.Z = static_cast<uint32_t>(quantize_coord(zj, inv));
+  kw.L = static_cast<uint32_t>(l1);
+  kw.NQ = quantize_normal(nx) | (quantize_normal(ny) << 8) | (quantize_normal(nz) << 16);
+  return kw;
+}
+
+// hash (home) and hash2 (fingerprint, 0 remapped to 1) of the key words.
+__device__ __forceinline__ Key key_hash(const KeyConst& kc, const KeyWords& kw) {
   uint32_t h = kc.hseed_home;
-  h = mm_body(h, X);
-  h = mm_body(h, Y);
-  h = mm_body(h, Z);
-  h = mm_body(h, L);
+  h = mm_body(h, kw.X);
+  h = mm_body(h, kw.Y);
+  h = mm_body(h, kw.Z);
+  h = mm_body(h, kw.L);
   if (kc.nih) {
-    h = mm_body(h, NQ);
+    h = mm_body(h, kw.NQ);
     h = mm_final(h, 20u);
   } else {
     h = mm_final(h, 16u);
   }
   uint32_t f = kc.hseed_fp;
-  f = mm_body(f, X);
-  f = mm_body(f, Y);
-  f = mm_body(f, Z);
-  f = mm_body(f, L);
-  f = mm_body(f, NQ);
+  f = mm_body(f, kw.X);
+  f = mm_body(f, kw.Y);
+  f = mm_body(f, kw.Z);
+  f = mm_body(f, kw.L);
+  f = mm_body(f, kw.NQ);
   f = mm_final(f, 20u);
   return Key{h, f ? f : 1u};
 }
 
+__device__ __forceinline__ Key vertex_key(const KeyConst& kc, float px, float py, float pz,
+                                          float nx, float ny, float nz, uint32_t id,
+                                          uint32_t stream_id) {
+  return key_hash(kc, key_words(kc, px, py, pz, nx, ny, nz, id, stream_id));
+}
+
 // ---------------------------------------------------------------- memory helpers
-__device__ __forceinline__ void red_add_v4(float4* p, float a, float b, float c, float d) {
-  asm volatile("red.relaxed.gpu.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a),
-               "f"(b), "f"(c), "f"(d)
+// L2 eviction priority "evict last" for the lines the next frame touches
+// again (slot index, accumulators): the vertex streams and outputs pass
+// through L2 with evict-first loads and stores (.cs), these stay behind them.
+__device__ __forceinline__ unsigned long long l2_evict_last() {
+  unsigned long long pol;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+
+__device__ __forceinline__ unsigned long long ld_relaxed_u64_keep(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.L2::cache_hint.u64 %0, [%1], %2;"
+               : "=l"(v)
+               : "l"(p), "l"(l2_evict_last())
+               : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void red_add_v4_keep(float4* p, float a, float b, float c, float d) {
+  asm volatile("red.relaxed.gpu.global.add.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(p),
+               "f"(a), "f"(b), "f"(c), "f"(d), "l"(l2_evict_last())
+               : "memory");
+}
+
+__device__ __forceinline__ void st_zero16_keep(void* p) {
+  asm volatile("st.global.L2::cache_hint.v4.u32 [%0], {%1, %1, %1, %1}, %2;" ::"l"(p), "r"(0u),
+               "l"(l2_evict_last())
                : "memory");
 }
 
@@ -337,7 +380,7 @@ __device__ __forceinline__ uint32_t hist_probe_rest(const TableDev& t, uint32_t 
 __device__ __forceinline__ void accumulate(const TableDev& t, uint32_t id, float r, float g, float b,
                                            long long fr, long long fg, long long fb, uint32_t cnt) {
   if (!t.fixed) {
-    red_add_v4(t.acc + id, r, g, b, static_cast<float>(cnt));
+    red_add_v4_keep(t.acc + id, r, g, b, static_cast<float>(cnt));
     return;
   }
   unsigned long long* a = t.acc64 + 4 * static_cast<size_t>(id);
@@ -485,10 +528,9 @@ __device__ __forceinline__ AccRaw load_value(const TableDev& t, uint32_t id, boo
 
 // Empty cell `id` (its accumulator and its slot) for the next frame.
 __device__ __forceinline__ void clear_cell(const TableDev& t, uint32_t id, uint32_t slot) {
-  const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
   float4* p = value_ptr(t, id);
-  __stcg(p, z);
-  if (t.fixed) __stcg(p + 1, z);
+  st_zero16_keep(p);
+  if (t.fixed) st_zero16_keep(p + 1);
   if (slot != kNoSlot) __stcg(t.slots + slot, 0ull);
 }
 

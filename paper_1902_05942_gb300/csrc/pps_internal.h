@@ -62,6 +62,11 @@ cudaError_t launch_keys(const KeyConst& kc, const VertexPtrs& v, size_t n, uint3
                         uint32_t* f_out, cudaStream_t st);
 cudaError_t launch_blend(const TableDev& t, uint32_t ntiles, float alpha, cudaStream_t st);
 cudaError_t launch_clear(const TableDev& t, uint32_t ntiles, cudaStream_t st);
+// Multi-level accumulation: vertices with fine status LOWCOUNT take the
+// coarse resolution's value, count and status COARSE (unless the coarse
+// insert overflowed).  `fine_status` may alias o.status.
+cudaError_t launch_combine_coarse(size_t n, const uint8_t* fine_status, const OutPtrs& coarse,
+                                  const OutPtrs& o, cudaStream_t st);
 cudaError_t launch_count_nonzero(const void* base, uint32_t stride, uint32_t off, uint32_t width,
                                  uint64_t n, unsigned long long* out, cudaStream_t st);
 cudaError_t plan_fused(size_t n, bool temporal, int batch, FusedPlan* plan);

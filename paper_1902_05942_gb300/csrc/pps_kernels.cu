@@ -85,7 +85,7 @@ __device__ __forceinline__ T block_sum(T x) {
 }
 
 struct Counters {
-  unsigned long long ovf = 0, cells = 0;
+  uint32_t ovf = 0, cells = 0;  // per thread (summed to 64 bits per CTA)
 };
 
 // The rare continuation of a probe whose home slot held another key, kept out
@@ -122,6 +122,11 @@ __device__ __noinline__ MoreProbe probe_more(unsigned long long* slots, uint32_t
   return r;
 }
 
+template <int W>
+struct Batch {
+  uint32_t id[W];
+};
+
 // Insert the W vertices j..j+W-1 (those below `end`) and return their cell
 // ids (kOverflowSlot on probe overflow).  New cells take ids id_base + k, k
 // drawn from the tile's claim counter *claims (shared memory).
@@ -131,16 +136,14 @@ __device__ __noinline__ MoreProbe probe_more(unsigned long long* slots, uint32_t
 // contributions are summed in registers and sent with one atomic); the first
 // probe of every distinct key (W loads in flight, then the compare-and-swaps
 // for empty slots); the rare longer probes; the accumulating reductions.
-template <int W>
-struct Batch {
-  uint32_t id[W];
-};
-
+//
+// `rec`: write each new cell's record (t.info) for the later blend and clear;
+// a frame that neither blends nor clears slot by slot never reads it.
 template <int W>
 __device__ __forceinline__ Batch<W> insert_batch(const KeyConst& kc, const TableDev& t,
                                                  const VertexPtrs& v, size_t j, size_t end,
                                                  bool vec, uint32_t id_base, uint32_t* claims,
-                                                 Counters& cnt_out) {
+                                                 Counters& cnt_out, bool rec = true) {
   float PX[W], PY[W], PZ[W], NX[W], NY[W], NZ[W];
   loadw<W>(PX, v.px, j, end, vec);
   loadw<W>(PY, v.py, j, end, vec);
@@ -210,7 +213,7 @@ __device__ __forceinline__ Batch<W> insert_batch(const KeyConst& kc, const Table
   unsigned long long w[W];
 #pragma unroll
   for (int q = 0; q < W; ++q)
-    w[q] = lead[q] ? ld_relaxed_u64(t.slots + (h1[q] & t.mask)) : 1ull;
+    w[q] = lead[q] ? ld_relaxed_u64_keep(t.slots + (h1[q] & t.mask)) : 1ull;
   // an empty home needs a cell id to publish with the fingerprint
   uint32_t my[W];
 #pragma unroll
@@ -248,7 +251,7 @@ __device__ __forceinline__ Batch<W> insert_batch(const KeyConst& kc, const Table
       claimed[q] = m.claimed;
     }
     // record the cell, or mark a reserved id that ended up unused
-    if (my[q] != kOverflowSlot)
+    if (rec && my[q] != kOverflowSlot)
       __stcg(t.info + my[q], claimed[q] ? make_uint4(slot[q], h1[q], f[q], kOverflowSlot)
                                         : make_uint4(kNoSlot, 0u, 0u, kOverflowSlot));
   }
@@ -265,7 +268,7 @@ __device__ __forceinline__ Batch<W> insert_batch(const KeyConst& kc, const Table
       if (of[q] == p) d = id[p];
     out.id[q] = f[q] == 0u ? kOverflowSlot : d;
     if (f[q] != 0u && out.id[q] == kOverflowSlot) ++cnt_out.ovf;
-    cnt_out.cells += claimed[q] ? 1ull : 0ull;
+    cnt_out.cells += claimed[q] ? 1u : 0u;
   }
   return out;
 }
@@ -275,6 +278,86 @@ struct Result {
   uint32_t n;
   uint8_t status;
 };
+
+// Neighborhood search (Sec. 3.3.2) for vertex j, whose own cell holds fewer
+// than t.lowcount members: the pooled average of the 3 x 3 x 3 block of cells
+// around its cell at the same level and with the same quantized normal.  A
+// plain frame pools the cells' sums and counts (FP32 sums, or exact int64
+// fixed-point sums with one rounding at the end); after a blend it pools the
+// blended values weighted by their counts N.  Cells are visited in a fixed
+// order (dx, dy, dz each -1, 0, +1, dz fastest), each found by a read-only
+// probe.  Kept out of line: only low-count vertices pay for it.
+__device__ __noinline__ Result neighbor_pool(const KeyConst& kc, const TableDev& t,
+                                             const VertexPtrs& v, size_t j, bool blended,
+                                             Result own) {
+  const KeyWords w0 =
+      key_words(kc, __ldg(v.px + j), __ldg(v.py + j), __ldg(v.pz + j), __ldg(v.nx + j),
+                __ldg(v.ny + j), __ldg(v.nz + j), vertex_id(v, j), v.stream_id);
+  float sr = 0.f, sg = 0.f, sb = 0.f;
+  long long fr = 0, fg = 0, fb = 0;
+  unsigned long long n = 0;
+  for (int o = 0; o < 27; ++o) {
+    KeyWords w = w0;
+    w.X += static_cast<uint32_t>(o / 9 - 1);
+    w.Y += static_cast<uint32_t>(o / 3 % 3 - 1);
+    w.Z += static_cast<uint32_t>(o % 3 - 1);
+    const Key k = key_hash(kc, w);
+    const uint32_t id = probe_find(t, k.h1 & t.mask, k.fp);
+    if (id == kOverflowSlot) continue;
+    if (blended) {
+      const float4 c = __ldcg(value_ptr(t, id));
+      const uint32_t N = __float_as_uint(c.w);
+      const float fN = __uint2float_rn(N);
+      sr = __fadd_rn(sr, __fmul_rn(fN, c.x));
+      sg = __fadd_rn(sg, __fmul_rn(fN, c.y));
+      sb = __fadd_rn(sb, __fmul_rn(fN, c.z));
+      n += N;
+    } else if (!t.fixed) {
+      const float4 a = __ldcg(t.acc + id);
+      sr = __fadd_rn(sr, a.x);
+      sg = __fadd_rn(sg, a.y);
+      sb = __fadd_rn(sb, a.z);
+      n += static_cast<unsigned long long>(a.w);
+    } else {
+      const unsigned long long* a = t.acc64 + 4 * static_cast<size_t>(id);
+      fr += static_cast<long long>(__ldcg(a + 0));
+      fg += static_cast<long long>(__ldcg(a + 1));
+      fb += static_cast<long long>(__ldcg(a + 2));
+      n += __ldcg(a + 3);
+    }
+  }
+  if (n == 0) return own;  // the own cell is always found; kept as a guard
+  Result r;
+  const float fn = __ull2float_rn(n);
+  if (t.fixed && !blended) {
+    r.r = __fdiv_rn(__fmul_rn(__ll2float_rn(fr), 0x1p-24f), fn);
+    r.g = __fdiv_rn(__fmul_rn(__ll2float_rn(fg), 0x1p-24f), fn);
+    r.b = __fdiv_rn(__fmul_rn(__ll2float_rn(fb), 0x1p-24f), fn);
+  } else {
+    r.r = __fdiv_rn(sr, fn);
+    r.g = __fdiv_rn(sg, fn);
+    r.b = __fdiv_rn(sb, fn);
+  }
+  r.n = static_cast<uint32_t>(min(n, 0xFFFFFFFFull));
+  r.status = 5;  // PPS_STATUS_NEIGHBORS
+  return r;
+}
+
+// Vertex j with cell `id`: if its cell is low-count, replace its outputs by
+// the neighborhood-search result.
+__device__ __forceinline__ void neighbors_of_vertex(const KeyConst& kc, const TableDev& t,
+                                                    const VertexPtrs& v, const OutPtrs& o,
+                                                    size_t j, uint32_t id, bool blended) {
+  if (id == kOverflowSlot) return;
+  const CellMean m = value_of(t, load_value(t, id, blended), blended);
+  if (m.n >= t.lowcount) return;
+  const Result r = neighbor_pool(kc, t, v, j, blended, Result{m.r, m.g, m.b, m.n, 1});
+  o.r[j] = r.r;
+  o.g[j] = r.g;
+  o.b[j] = r.b;
+  if (o.count) o.count[j] = r.n;
+  if (o.status) o.status[j] = r.status;
+}
 
 // Look up the cells id[0..W-1] (loads issued together) and resolve each vertex:
 // cell average / blended value, or its own contribution on overflow.
@@ -347,6 +430,33 @@ __device__ __forceinline__ void store_batch(const OutPtrs& o, size_t j, size_t e
   }
 }
 
+// Blend BW cells whose ids, history homes and fingerprints are known (`use`
+// false: no cell): history probes issued together, then the blends.
+template <int BW>
+__device__ __forceinline__ void blend_cells(const TableDev& t, const uint32_t (&d)[BW],
+                                            const uint32_t (&home)[BW], const uint32_t (&f)[BW],
+                                            const bool (&use)[BW], const AccRaw (&a)[BW],
+                                            float alpha, unsigned long long& n_hovf) {
+  uint32_t old[BW], h[BW];
+#pragma unroll
+  for (int q = 0; q < BW; ++q) old[q] = use[q] ? atomicCAS(hist_fp(t, home[q]), 0u, f[q]) : 0u;
+#pragma unroll
+  for (int q = 0; q < BW; ++q) {
+    h[q] = home[q];
+    if (use[q] && old[q] != 0u && old[q] != f[q]) h[q] = hist_probe_rest(t, home[q], f[q], 1u);
+    if (use[q] && h[q] == kOverflowSlot) ++n_hovf;
+  }
+  HistRaw hv[BW];
+#pragma unroll
+  for (int q = 0; q < BW; ++q) {
+    hv[q] = HistRaw{0.f, 0.f, 0.f, 0u};
+    if (use[q] && h[q] != kOverflowSlot) hv[q] = load_hist(t, h[q]);
+  }
+#pragma unroll
+  for (int q = 0; q < BW; ++q)
+    if (use[q]) blend_store(t, d[q], h[q], mean_of(t, a[q]), hv[q], alpha);
+}
+
 // Blend the cells [base, base + count): each thread takes BW cells, one from
 // each of BW consecutive runs of `stride` ids (coalesced loads), and issues
 // their history probes together.  `first` is this thread's offset.
@@ -355,7 +465,7 @@ __device__ __forceinline__ void blend_range(const TableDev& t, uint32_t base, ui
                                             uint32_t first, uint32_t stride, float alpha,
                                             unsigned long long& n_hovf) {
   for (uint32_t k0 = first; k0 < count; k0 += BW * stride) {
-    uint32_t d[BW], home[BW], f[BW], h[BW];
+    uint32_t d[BW], home[BW], f[BW];
     bool use[BW];
     AccRaw a[BW];
 #pragma unroll
@@ -373,24 +483,7 @@ __device__ __forceinline__ void blend_range(const TableDev& t, uint32_t base, ui
         if (use[q]) a[q] = load_acc(t, d[q]);
       }
     }
-    uint32_t old[BW];
-#pragma unroll
-    for (int q = 0; q < BW; ++q) old[q] = use[q] ? atomicCAS(hist_fp(t, home[q]), 0u, f[q]) : 0u;
-#pragma unroll
-    for (int q = 0; q < BW; ++q) {
-      h[q] = home[q];
-      if (use[q] && old[q] != 0u && old[q] != f[q]) h[q] = hist_probe_rest(t, home[q], f[q], 1u);
-      if (use[q] && h[q] == kOverflowSlot) ++n_hovf;
-    }
-    HistRaw hv[BW];
-#pragma unroll
-    for (int q = 0; q < BW; ++q) {
-      hv[q] = HistRaw{0.f, 0.f, 0.f, 0u};
-      if (use[q] && h[q] != kOverflowSlot) hv[q] = load_hist(t, h[q]);
-    }
-#pragma unroll
-    for (int q = 0; q < BW; ++q)
-      if (use[q]) blend_store(t, d[q], h[q], mean_of(t, a[q]), hv[q], alpha);
+    blend_cells<BW>(t, d, home, f, use, a, alpha, n_hovf);
   }
 }
 
@@ -410,7 +503,7 @@ __device__ __forceinline__ void clear_range(const TableDev& t, uint32_t base, ui
 __device__ __forceinline__ void sweep_slots(const TableDev& t, size_t gid, size_t gthreads) {
   uint4* p = reinterpret_cast<uint4*>(t.slots);
   const size_t n16 = (static_cast<size_t>(t.mask) + 1) / 2;
-  for (size_t i = gid; i < n16; i += gthreads) __stcg(p + i, make_uint4(0u, 0u, 0u, 0u));
+  for (size_t i = gid; i < n16; i += gthreads) st_zero16_keep(p + i);
 }
 
 // ------------------------------------------------------------------ split path
@@ -440,8 +533,8 @@ __global__ void __launch_bounds__(kBlock) k_insert(KeyConst kc, TableDev t, Vert
     __syncthreads();
     if (threadIdx.x == 0) t.bcount[tix] = s_claims;
   }
-  const unsigned long long a = block_sum(c.ovf);
-  const unsigned long long b = block_sum(c.cells);
+  const unsigned long long a = block_sum(static_cast<unsigned long long>(c.ovf));
+  const unsigned long long b = block_sum(static_cast<unsigned long long>(c.cells));
   if (threadIdx.x == 0) {
     if (a) atomicAdd(&t.ctrl->overflow_vertices, a);
     if (b) atomicAdd(&t.ctrl->frame_cells, b);
@@ -485,6 +578,11 @@ __global__ void __launch_bounds__(kBlock) k_query(KeyConst kc, TableDev t, Verte
     Result res[4];
     resolve_batch<4>(t, v, j, n, id, blended != 0, res);
     store_batch<4>(o, j, n, ovec != 0, res);
+    if (t.neighbors) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (j + q < n) neighbors_of_vertex(kc, t, v, o, j + q, id[q], blended != 0);
+    }
   }
 }
 
@@ -531,6 +629,12 @@ __global__ void __launch_bounds__(kBlock) k_count_nonzero(const unsigned char* b
 }
 
 // ------------------------------------------------------------------ fused path
+// Next tile of the frame's tile counter (ntiles once all are taken).
+__device__ __forceinline__ uint32_t claim_tile(Ctrl* ctrl, uint32_t ntiles) {
+  const unsigned long long k = atomicAdd(&ctrl->tile_next, 1ull);
+  return k < ntiles ? static_cast<uint32_t>(k) : ntiles;
+}
+
 struct FusedArgs {
   KeyConst kc;
   TableDev t;
@@ -555,41 +659,45 @@ __global__ void __launch_bounds__(kFusedBlock, W == 4 ? 1 : 2) k_fused(FusedArgs
   extern __shared__ __align__(16) uint32_t s_stash[];
   __shared__ uint32_t s_tile[kMaxTilesPerCta];
   __shared__ uint32_t s_claims[kMaxTilesPerCta];
-  __shared__ uint32_t s_next, s_taken;
+  __shared__ uint32_t s_cur, s_taken;
+  __shared__ unsigned long long s_nv;  // vertices of this CTA's tiles
   const TableDev& t = a.t;
   const uint32_t ntiles = static_cast<uint32_t>((a.n + kFusedTile - 1) / kFusedTile);
   const bool vec = a.vec != 0;
-  if (threadIdx.x == 0) s_taken = 0;
+  if (threadIdx.x == 0) {
+    s_taken = 0;
+    s_nv = 0;
+  }
 
   // Phase A: keys, probing insert, accumulation, tile by tile.
   Counters c;
-  unsigned long long nv = 0;
   for (;;) {
     __syncthreads();
     if (threadIdx.x == 0) {
       uint32_t tile = ntiles;
-      if (s_taken < a.cap_tiles)
-        tile = static_cast<uint32_t>(atomicAdd(&t.ctrl->tile_next, 1ull));
-      s_next = tile;
+      if (s_taken < a.cap_tiles) tile = claim_tile(t.ctrl, ntiles);
+      s_cur = tile;
       if (tile < ntiles) {
         s_tile[s_taken] = tile;
         s_claims[s_taken] = 0;
+        s_nv += min(a.n, static_cast<size_t>(tile) * kFusedTile + kFusedTile) -
+                static_cast<size_t>(tile) * kFusedTile;
       }
     }
     __syncthreads();
-    const uint32_t tile = s_next;
+    const uint32_t tile = s_cur;
     if (tile >= ntiles) break;
     const uint32_t k = s_taken;
     const size_t t0 = static_cast<size_t>(tile) * kFusedTile;
     const size_t end = min(a.n, t0 + kFusedTile);
-    nv += end - t0;
     uint32_t* stash = a.gstash ? a.gstash + t0 : s_stash + static_cast<size_t>(k) * kFusedTile;
 #pragma unroll 1
     for (int sub = 0; sub < 4; sub += W) {
       const size_t j = t0 + threadIdx.x * 4 + sub;
       if (j < end) {
         const Batch<W> b = insert_batch<W>(a.kc, t, a.v, j, end, vec, static_cast<uint32_t>(t0),
-                                           &s_claims[k], c);
+                                           &s_claims[k], c,
+                                           (TEMPORAL && a.blend) || !a.sweep);
 #pragma unroll
         for (int q = 0; q < W; ++q) stash[j - t0 + q] = b.id[q];
       }
@@ -598,12 +706,12 @@ __global__ void __launch_bounds__(kFusedBlock, W == 4 ? 1 : 2) k_fused(FusedArgs
     if (threadIdx.x == 0) ++s_taken;
   }
   {
-    const unsigned long long o = block_sum(c.ovf);
-    const unsigned long long k = block_sum(c.cells);
+    const unsigned long long o = block_sum(static_cast<unsigned long long>(c.ovf));
+    const unsigned long long k = block_sum(static_cast<unsigned long long>(c.cells));
     if (threadIdx.x == 0) {
       if (o) atomicAdd(&t.ctrl->overflow_vertices, o);
       if (k) atomicAdd(&t.ctrl->frame_cells, k);
-      if (nv) atomicAdd(&t.ctrl->vertices, threadIdx.x == 0 ? nv : 0ull);
+      if (s_nv) atomicAdd(&t.ctrl->vertices, s_nv);
     }
   }
   if (!grid_barrier(t.ctrl, gridDim.x)) return;
@@ -638,6 +746,17 @@ __global__ void __launch_bounds__(kFusedBlock, W == 4 ? 1 : 2) k_fused(FusedArgs
         resolve_batch<W>(t, a.v, j, end, id, blended, res);
         store_batch<W>(a.o, j, end, ovec, res);
       }
+    }
+  }
+  // Neighborhood search for this CTA's low-count vertices (the table is only
+  // read from phase C on, so no barrier is needed before it).
+  if (t.neighbors) {
+    for (uint32_t k = 0; k < taken; ++k) {
+      const size_t t0 = static_cast<size_t>(s_tile[k]) * kFusedTile;
+      const size_t end = min(a.n, t0 + kFusedTile);
+      const uint32_t* stash = a.gstash ? a.gstash + t0 : s_stash + static_cast<size_t>(k) * kFusedTile;
+      for (size_t j = t0 + threadIdx.x; j < end; j += blockDim.x)
+        neighbors_of_vertex(a.kc, t, a.v, a.o, j, stash[j - t0], blended);
     }
   }
   if (!grid_barrier(t.ctrl, gridDim.x)) return;
@@ -884,6 +1003,27 @@ cudaError_t launch_clear(const TableDev& t, uint32_t ntiles, cudaStream_t st) {
   const uint32_t grid = std::min<uint32_t>(std::max<uint32_t>(ntiles, sweep ? 1u << 30 : 0u),
                                            static_cast<uint32_t>(sm_count()) * 8);
   k_clear_sweep<<<grid, kBlock, 0, st>>>(t, ntiles, sweep);
+  return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(kBlock) k_combine_coarse(size_t n, const uint8_t* fine_status,
+                                                           OutPtrs c, OutPtrs o) {
+  for (size_t j = blockIdx.x * (size_t)blockDim.x + threadIdx.x; j < n;
+       j += (size_t)gridDim.x * blockDim.x) {
+    if (fine_status[j] != 1 || c.status[j] == 2) continue;
+    o.r[j] = c.r[j];
+    o.g[j] = c.g[j];
+    o.b[j] = c.b[j];
+    if (o.count) o.count[j] = c.count[j];
+    if (o.status) o.status[j] = 4;  // PPS_STATUS_COARSE
+  }
+}
+
+cudaError_t launch_combine_coarse(size_t n, const uint8_t* fine_status, const OutPtrs& coarse,
+                                  const OutPtrs& o, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  const size_t blocks = std::min<size_t>((n + kBlock - 1) / kBlock, static_cast<size_t>(sm_count()) * 8);
+  k_combine_coarse<<<static_cast<unsigned>(blocks), kBlock, 0, st>>>(n, fine_status, coarse, o);
   return cudaGetLastError();
 }
 

@@ -80,9 +80,10 @@ extern "C" int pps_filter_noalloc(const pps_params* p, const pps_camera* cam, ui
     return noalloc_fail(PPS_EINVAL, "pps_filter_noalloc: log2_slots must be in [4, 20]");
   if (n > kNoAllocMaxVertices)
     return noalloc_fail(PPS_EINVAL, "pps_filter_noalloc: at most 524288 vertices per call");
-  if (p->accum_mode != PPS_ACCUM_FP32 || p->hist_mode != PPS_HIST_NONE)
+  if (p->accum_mode != PPS_ACCUM_FP32 || p->hist_mode != PPS_HIST_NONE ||
+      p->fallback != PPS_FALLBACK_NONE)
     return noalloc_fail(PPS_EINVAL,
-                        "pps_filter_noalloc: FP32 accumulation without history only");
+                        "pps_filter_noalloc: FP32 accumulation without history or fallback only");
   for (uint32_t r : p->reserved)
     if (r) return noalloc_fail(PPS_EINVAL, "pps_filter_noalloc: reserved fields must be zero");
   if (p->max_probes < 1 || p->max_probes > (1u << p->log2_slots) || p->max_probes > 4096 ||

@@ -107,3 +107,12 @@ def test_null_arguments_are_rejected():
     assert L.pps_blend(None, 0.2, None) == pps.PPS_EINVAL
     assert L.pps_destroy(None) == pps.PPS_OK
     assert pps.pps_version().startswith("pps-gb300")
+
+
+def test_bad_fallback_is_rejected():
+    pps, L = _lib()
+    p = _params(pps)
+    p.fallback = 3
+    h = ctypes.c_void_p()
+    assert L.pps_create(ctypes.byref(h), ctypes.byref(p)) == pps.PPS_EINVAL
+    assert "fallback" in pps.last_error()

@@ -1,0 +1,180 @@
+"""GPU parity of the low-count fallbacks against the oracle: multi-level
+accumulation (Sec. 3.3.3) and neighborhood search (Sec. 3.3.2), through the
+fused launch and the split calls, with FP32 and fixed-point sums, and after
+temporal blends.
+
+Bars (per vertex): counts and statuses bit-exact; values as for the plain
+filter -- FP32: the summation bound (n + 1) 2^-24 relative (at least 1e-5),
+where a pooled neighborhood value adds up to 27 cell sums, i.e. 27 more
+roundings; fixed point: bit-exact (pooled int64 sums are exact); after a
+blend, the FP32 history bound of 8 2^-24 per blended frame on top.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import pps_oracle as O
+from paper_1902_05942_gb300 import configs, pps, scene
+
+pytestmark = pytest.mark.gpu
+
+U = 2.0 ** -24
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1902_05942_gb300 import build
+    build.build()
+    torch.cuda.set_device(0)
+    yield
+
+
+def _setup(fallback, width=128, height=128, bounces=2, **fkw):
+    w = configs.small()
+    spec = configs.frame_spec(w, 0, 0)
+    spec.view.width, spec.view.height = width, height
+    spec.bounces = bounces
+    cfg = w.filters[0]
+    cfg.pixel_angle = spec.view.pixel_angle()
+    cfg.fallback = fallback
+    for k, v in fkw.items():
+        setattr(cfg, k, v)
+    return w, spec, cfg
+
+
+def _gen(spec, frame=0):
+    v = scene.trace_stream(spec, frame, "cpu")
+    return {k: v[k] for k in scene.STREAMS}
+
+
+def _dev(v):
+    return {k: v[k].to("cuda").contiguous() for k in scene.STREAMS}
+
+
+def _np(v):
+    return {k: v[k].numpy() for k in scene.STREAMS}
+
+
+def _rgb(out):
+    return torch.stack([out[c] for c in "rgb"], 1).cpu().numpy()
+
+
+def _run(tab, d, eye, frame, fused, blend=False, alpha=0.2, out=None):
+    if fused:
+        return tab.filter(d, eye, frame, blend=blend, alpha=alpha, out=out)
+    tab.build(eye, frame)
+    slots = torch.empty(d["px"].numel(), dtype=torch.int32, device="cuda")
+    tab.insert(d, slots)
+    if blend:
+        tab.blend(alpha)
+    return tab.query(d, slots, out=out)
+
+
+def _check(got, ref, count, extra=0.0):
+    tol = np.maximum(1e-5, (count + 1) * U)[:, None] + extra
+    rel = np.abs(got.astype(np.float64) - ref) / np.abs(ref)
+    assert np.all(rel <= tol), f"{(rel > tol).sum()} values off, max rel {rel.max():.3e}"
+
+
+@pytest.mark.parametrize("fused", [True, False])
+@pytest.mark.parametrize("fixed", [False, True])
+def test_multilevel_matches_oracle(fused, fixed):
+    _, spec, cfg = _setup("coarse", accum_fixed=fixed)
+    v = _gen(spec)
+    tab = pps.Table(cfg)
+    out = _run(tab, _dev(v), spec.view.eye, 3, fused)
+    p = O.KeyParams(**cfg.oracle_kwargs())
+    fine = O.filter_frame(p, spec.view.eye, 3, _np(v))
+    coarse = O.filter_frame(O.coarse_params(p), spec.view.eye, 3, _np(v))
+    val, cnt, st = O.multilevel_select(fine.mean64, fine.count, coarse.mean64, coarse.count, 4)
+    assert (st == O.STATUS_COARSE).sum() > 1000
+    assert np.array_equal(out["count"].cpu().numpy().astype(np.int64), cnt)
+    assert np.array_equal(out["status"].cpu().numpy(), st)
+    if fixed:
+        low = fine.count < 4
+        ref = np.where(low[:, None], coarse.mean_fixed, fine.mean_fixed)
+        assert np.array_equal(_rgb(out), ref)
+    else:
+        _check(_rgb(out), val, cnt)
+    tab.close()
+
+
+def test_multilevel_without_status_or_count_arrays():
+    """The choice needs the fine status: the library keeps its own when the
+    caller passes no status (and no count) array."""
+    _, spec, cfg = _setup("coarse", width=96, height=80)
+    v = _gen(spec)
+    n = v["px"].numel()
+    tab = pps.Table(cfg)
+    out = tab.filter(_dev(v), spec.view.eye, 1, out=pps.empty_output(n, "cuda", count=False,
+                                                                     status=False))
+    p = O.KeyParams(**cfg.oracle_kwargs())
+    fine = O.filter_frame(p, spec.view.eye, 1, _np(v))
+    coarse = O.filter_frame(O.coarse_params(p), spec.view.eye, 1, _np(v))
+    val, cnt, _ = O.multilevel_select(fine.mean64, fine.count, coarse.mean64, coarse.count, 4)
+    _check(_rgb(out), val, cnt)
+    tab.close()
+
+
+@pytest.mark.parametrize("fused", [True, False])
+@pytest.mark.parametrize("fixed", [False, True])
+def test_neighborhood_matches_oracle(fused, fixed):
+    _, spec, cfg = _setup("neighbors", accum_fixed=fixed)
+    v = _gen(spec)
+    tab = pps.Table(cfg)
+    out = _run(tab, _dev(v), spec.view.eye, 4, fused)
+    fr = O.filter_frame(O.KeyParams(**cfg.oracle_kwargs()), spec.view.eye, 4, _np(v))
+    val64, valfx, cnt, st = O.neighborhood(fr, 4)
+    assert (st == O.STATUS_NEIGHBORS).sum() > 1000
+    assert np.array_equal(out["count"].cpu().numpy().astype(np.int64), cnt)
+    assert np.array_equal(out["status"].cpu().numpy(), st)
+    if fixed:
+        assert np.array_equal(_rgb(out), valfx)
+    else:
+        _check(_rgb(out), val64, cnt, extra=27 * U)
+    tab.close()
+
+
+@pytest.mark.parametrize("fallback", ["coarse", "neighbors"])
+@pytest.mark.parametrize("fused", [True, False])
+def test_fallbacks_after_temporal_blend(fallback, fused):
+    w, _, cfg = _setup(fallback, hist_mode=1, log2_hist_slots=19)
+    alpha = 0.2
+    tab = pps.Table(cfg)
+    p = O.KeyParams(**cfg.oracle_kwargs())
+    hist = O.History.empty()
+    hist_c = O.History.empty()
+    for f in range(3):
+        spec = configs.frame_spec(w, 0, f)
+        spec.view = scene.View(128, 96, eye=(0.05 * f, 3.0, -12.0), target=(0.05 * f, 0.5, 0.0))
+        spec.bounces = 2
+        v = _gen(spec, f)
+        out = _run(tab, _dev(v), spec.view.eye, f, fused, blend=True, alpha=alpha)
+        fr = O.filter_frame(p, spec.view.eye, f, _np(v))
+        hist, val, cnt = O.blend(hist, fr, alpha)
+        if fallback == "coarse":
+            frc = O.filter_frame(O.coarse_params(p), spec.view.eye, f, _np(v))
+            hist_c, val_c, cnt_c = O.blend(hist_c, frc, alpha)
+            ref, rcnt, st = O.multilevel_select(val, cnt, val_c, cnt_c, 4)
+        else:
+            cv = np.zeros((fr.tuples.shape[0], 3))
+            cw = np.zeros(fr.tuples.shape[0], dtype=np.int64)
+            cv[fr.cell] = val
+            cw[fr.cell] = cnt
+            ref, _, rcnt, st = O.neighborhood(fr, 4, cell_value=cv, cell_weight=cw)
+        assert np.array_equal(out["count"].cpu().numpy().astype(np.int64), rcnt)
+        assert np.array_equal(out["status"].cpu().numpy(), st)
+        _check(_rgb(out), ref, rcnt, extra=8 * U * (f + 1) + 30 * U)
+    assert tab.stats()["hist_overflow"] == 0
+    tab.close()
+
+
+def test_batch_rejects_fallback_tables():
+    _, spec, cfg = _setup("neighbors", width=64, height=64, bounces=1)
+    v = _dev(_gen(spec))
+    tab = pps.Table(cfg)
+    out = pps.empty_output(v["px"].numel(), "cuda")
+    with pytest.raises(pps.PPSError) as e:
+        pps.Batch([(tab, v, out)])
+    assert e.value.code == pps.PPS_EINVAL
+    tab.close()
