@@ -55,9 +55,13 @@ def _peaks():
         return 6800.0, "fallback"
 
 
+# the sources that define k_fused; its DRAM counters stay valid while they do
+KERNEL_SOURCES = ("pps_device.cuh", "pps_internal.h", "pps_kernels.cu")
+
+
 def _source_hash() -> str:
     h = hashlib.sha256()
-    for f in sorted(os.listdir(CSRC)):
+    for f in KERNEL_SOURCES:
         with open(os.path.join(CSRC, f), "rb") as fh:
             h.update(f.encode())
             h.update(fh.read())
@@ -239,36 +243,44 @@ def run_ours(args):
     peak, peak_kind = _peaks()
     traffic = _traffic_per_launch()
 
-    # end to end through the host-buffer entry point: H2D of the inputs, the
-    # filter, D2H of r, g, b and status, inside the timed region
+    # end to end through the host-buffer entry point: the uploads of each
+    # frame's inputs from pinned host memory, the filter, and the downloads of
+    # r, g, b and status, all inside the timed region; pps_filter_host_async
+    # overlaps one frame's uploads with the previous frame's filter and
+    # downloads, and pps_host_wait ends the timed region
     e2e = None
     if not args.no_e2e:
         hv = [{k: t.cpu().pin_memory() for k, t in fr[0].items()} for fr in frames[:4]]
-        ho = pps.empty_output(n_max, "cpu", count=False, status=True)
-        ho = {k: t.pin_memory() for k, t in ho.items()}
+        ho = []
+        for _ in range(2):
+            o = pps.empty_output(n_max, "cpu", count=False, status=True)
+            ho.append({k: t.pin_memory() for k, t in o.items()})
         tab_h = pps.Table(cfg)
 
         def hstep(i):
             v = hv[i % len(hv)]
             n = v["px"].numel()
-            o = {k: t[:n] for k, t in ho.items()}
-            pps.pps_filter_host(tab_h.handle, pps.camera(frames[i % len(hv)][1]), i,
-                                pps.make_vertices(v, n, device=False), n, True, cfg.alpha,
-                                pps.make_output(o, n, device=False), stream)
+            o = {k: t[:n] for k, t in ho[i % 2].items()}
+            pps.pps_filter_host_async(tab_h.handle, pps.camera(frames[i % len(hv)][1]), i,
+                                      pps.make_vertices(v, n, device=False), n, True, cfg.alpha,
+                                      pps.make_output(o, n, device=False), stream)
             return n
 
         for i in range(args.warmup):
             hstep(i)
+        pps.pps_host_wait(tab_h.handle)
         torch.cuda.synchronize()
         if ws > 1:
             dist.barrier()
         t0 = time.perf_counter()
         hn = sum(hstep(args.warmup + i) for i in range(args.steps))
+        pps.pps_host_wait(tab_h.handle)
         dt = time.perf_counter() - t0
         dt, hn = reduce_ranks(dt, float(hn), dev)
         e2e = {"value": hn / dt, "unit": UNIT,
                "h2d_bytes_per_step": int(36 * mean_n), "d2h_bytes_per_step": int(13 * mean_n),
-               "ms_per_step": 1e3 * dt / args.steps}
+               "ms_per_step": 1e3 * dt / args.steps,
+               "api": "pps_filter_host_async + pps_host_wait (pinned host buffers)"}
         tab_h.close()
 
     if rank == 0:
@@ -593,8 +605,11 @@ def run_reference(args):
 
 
 def run_ncu_case(args):
-    """A small fixed case for profilers: one HD frame through the fused launch,
-    three times (history on, batch width from --batch), no timing."""
+    """A small fixed case for profilers, no timing.  `--case hd`: one HD frame
+    through the fused launch, three times (history from --hist, batch width
+    from --batch, fallback from --fallback).  `--case mlp`: that frame
+    filtered with history, then the learned fallback: one training call (4
+    Adam steps of 16,384 samples) and one inference call."""
     import torch
     from paper_1902_05942_gb300 import build, configs, pps, scene
     build.build()
@@ -604,14 +619,26 @@ def run_ncu_case(args):
     spec = configs.frame_spec(w, 0, 0)
     v = scene.trace_stream(spec, 0, "cuda")
     d = {k: v[k] for k in scene.STREAMS}
+    if args.case == "mlp":
+        out = pps.empty_output(d["px"].numel(), "cuda")
+        tab = pps.Table(cfg)
+        net = pps.MLP(pps.mlp_params())
+        tab.filter(d, spec.view.eye, 0, blend=True, alpha=cfg.alpha, out=out)
+        net.train(d, out, 0)
+        net.infer(d, out)
+        torch.cuda.synchronize()
+        print(json.dumps({"ncu_case": "mlp",
+                          "lowcount": int((out["status"] == pps.STATUS_MLP).sum().item())}))
+        return
     out = pps.empty_output(d["px"].numel(), "cuda", count=False)
-    tab = pps.Table(cfg, hist_mode=args.hist)
+    tab = pps.Table(cfg, hist_mode=args.hist, fallback=args.fallback)
     if args.batch:
         tab.tune(args.batch)
     for i in range(3):
         tab.filter(d, spec.view.eye, i, blend=args.hist != 0, alpha=cfg.alpha, out=out)
     torch.cuda.synchronize()
-    print(json.dumps({"ncu_case": "hd", "hist": args.hist, "stats": tab.stats()}))
+    print(json.dumps({"ncu_case": "hd", "hist": args.hist, "fallback": args.fallback,
+                      "stats": tab.stats()}))
 
 
 def run_rates(args):
@@ -647,6 +674,9 @@ def main():
     ap.add_argument("--rates", action="store_true", help="random memory-operation rates")
     ap.add_argument("--hist", type=int, default=1, help="--ncu-case: history mode")
     ap.add_argument("--batch", type=int, default=0, help="--ncu-case: batch width")
+    ap.add_argument("--case", default="hd", choices=("hd", "mlp"), help="--ncu-case: workload")
+    ap.add_argument("--fallback", default="none", choices=("none", "coarse", "neighbors"),
+                    help="--ncu-case hd: low-count fallback")
     args = ap.parse_args()
     if args.ncu_case:
         return run_ncu_case(args)

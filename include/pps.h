@@ -285,6 +285,28 @@ int pps_filter_host(pps_table *t, const pps_camera *cam, uint32_t frame,
                     const pps_vertices *v_host, size_t n, int blend, float alpha,
                     const pps_output *out_host, void *stream);
 
+/*
+ * pps_filter_host_async: pps_filter_host without the final synchronization,
+ * for frame loops.  Each call takes one of two library-owned staging slots
+ * (alternating) and enqueues: the uploads of the nine input arrays on the
+ * table's upload stream, once that slot's previous outputs are home; the
+ * filter on `stream`, once the uploads are done; the downloads of the results
+ * on the table's download stream, once the filter is done.  So the uploads of
+ * one call overlap the filtering of the previous one and the downloads of the
+ * one before.  The host arrays must stay untouched (inputs) and unread
+ * (outputs) until pps_host_wait returns; pinned host memory is needed for
+ * the copies to run asynchronously (pageable memory works, without overlap).
+ * Calls on one table must come from one host thread, in frame order.
+ * Errors: as pps_filter_host.
+ */
+int pps_filter_host_async(pps_table *t, const pps_camera *cam, uint32_t frame,
+                          const pps_vertices *v_host, size_t n, int blend, float alpha,
+                          const pps_output *out_host, void *stream);
+
+/* pps_host_wait: block until the results of every earlier
+ * pps_filter_host_async call on t are in host memory.  Errors: PPS_ECUDA. */
+int pps_host_wait(pps_table *t);
+
 /* pps_set_tuning / pps_get_tuning: set or read the launch shape (pps_tuning).
  * Results do not depend on it.  Errors: PPS_EINVAL. */
 int pps_set_tuning(pps_table *t, const pps_tuning *tune);

@@ -58,6 +58,16 @@ struct pps_table {
   void* stage = nullptr;  // pps_filter_host device staging
   size_t stage_cap = 0;
   unsigned long long* scratch_u64 = nullptr;  // 1 word for occupancy counting
+  // pps_filter_host_async: two staging slots, an upload and a download stream
+  struct HostSlot {
+    void* dev = nullptr;
+    size_t cap = 0;
+    cudaEvent_t in_ready = nullptr, computed = nullptr, done = nullptr;
+    bool used = false;
+  };
+  HostSlot hslot[2];
+  cudaStream_t up = nullptr, down = nullptr;
+  uint64_t host_calls = 0;
   pps_table* coarse = nullptr;  // multi-level accumulation: the next coarser resolution
   void* fb = nullptr;           // multi-level scratch: coarse results and fine status
   size_t fb_cap = 0;            // vertices the scratch holds
@@ -223,6 +233,14 @@ void free_all(pps_table* t) {
   cudaFree(t->stage);
   cudaFree(t->scratch_u64);
   cudaFree(t->fb);
+  for (auto& h : t->hslot) {
+    cudaFree(h.dev);
+    if (h.in_ready) cudaEventDestroy(h.in_ready);
+    if (h.computed) cudaEventDestroy(h.computed);
+    if (h.done) cudaEventDestroy(h.done);
+  }
+  if (t->up) cudaStreamDestroy(t->up);
+  if (t->down) cudaStreamDestroy(t->down);
 }
 
 // Multi-level scratch for n vertices: the coarse pass's r, g, b, count and
@@ -471,16 +489,75 @@ int pps_filter(pps_table* t, const pps_camera* cam, uint32_t frame, const pps_ve
 
 
 
-int pps_filter_host(pps_table* t, const pps_camera* cam, uint32_t frame, const pps_vertices* vh,
-                    size_t n, int blend, float alpha, const pps_output* oh, void* stream) {
+}  // extern "C"
+
+namespace {
+
+// Device staging of one host call: the nine inputs, r, g, b, count, status.
+size_t host_stage_bytes(size_t n) {
+  const size_t nn = (n + 3) & ~static_cast<size_t>(3);
+  return nn * (9 + 3 + 1) * sizeof(float) + nn;
+}
+
+// Upload the host inputs to `base` on stream `st`; fill the device views.
+int host_upload(const pps_vertices* vh, size_t n, const pps_output* oh, void* stage,
+                cudaStream_t st, pps_vertices* vd, pps_output* od) {
+  const size_t nn = (n + 3) & ~static_cast<size_t>(3);
+  float* base = static_cast<float*>(stage);
+  const float* src[9] = {vh->px, vh->py, vh->pz, vh->nx, vh->ny, vh->nz, vh->r, vh->g, vh->b};
+  float* dst[9];
+  for (int i = 0; i < 9; ++i) {
+    dst[i] = base + static_cast<size_t>(i) * nn;
+    PPS_CUDA(cudaMemcpyAsync(dst[i], src[i], n * sizeof(float), cudaMemcpyHostToDevice, st));
+  }
+  *vd = pps_vertices{};
+  vd->px = dst[0];
+  vd->py = dst[1];
+  vd->pz = dst[2];
+  vd->nx = dst[3];
+  vd->ny = dst[4];
+  vd->nz = dst[5];
+  vd->r = dst[6];
+  vd->g = dst[7];
+  vd->b = dst[8];
+  vd->id_base = vh->id_base;
+  vd->stream_id = vh->stream_id;
+  *od = pps_output{};
+  od->r = base + 9 * nn;
+  od->g = base + 10 * nn;
+  od->b = base + 11 * nn;
+  od->count = oh->count ? reinterpret_cast<uint32_t*>(base + 12 * nn) : nullptr;
+  od->status = oh->status ? reinterpret_cast<uint8_t*>(base + 13 * nn) : nullptr;
+  return PPS_OK;
+}
+
+int host_download(const pps_output* od, size_t n, const pps_output* oh, cudaStream_t st) {
+  PPS_CUDA(cudaMemcpyAsync(oh->r, od->r, n * sizeof(float), cudaMemcpyDeviceToHost, st));
+  PPS_CUDA(cudaMemcpyAsync(oh->g, od->g, n * sizeof(float), cudaMemcpyDeviceToHost, st));
+  PPS_CUDA(cudaMemcpyAsync(oh->b, od->b, n * sizeof(float), cudaMemcpyDeviceToHost, st));
+  if (oh->count)
+    PPS_CUDA(cudaMemcpyAsync(oh->count, od->count, n * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+  if (oh->status) PPS_CUDA(cudaMemcpyAsync(oh->status, od->status, n, cudaMemcpyDeviceToHost, st));
+  return PPS_OK;
+}
+
+int check_host_call(pps_table* t, const pps_vertices* vh, size_t n, const pps_output* oh) {
   if (int rc = check_table(t)) return rc;
   if (int rc = check_vertices(vh, n)) return rc;
   if (int rc = check_output(oh, n)) return rc;
-  if (vh->id) return fail(PPS_EINVAL, "pps_filter_host takes no id array");
+  if (vh->id) return fail(PPS_EINVAL, "host-buffer filtering takes no id array");
+  return PPS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pps_filter_host(pps_table* t, const pps_camera* cam, uint32_t frame, const pps_vertices* vh,
+                    size_t n, int blend, float alpha, const pps_output* oh, void* stream) {
+  if (int rc = check_host_call(t, vh, n, oh)) return rc;
   const cudaStream_t st = static_cast<cudaStream_t>(stream);
-  // staging: 9 input floats, 3 output floats, 1 count word, status bytes (rounded)
-  const size_t nn = (n + 3) & ~static_cast<size_t>(3);
-  const size_t need = nn * (9 + 3 + 1) * sizeof(float) + nn;
+  const size_t need = host_stage_bytes(n);
   if (t->stage_cap < need) {
     cudaFree(t->stage);
     t->stage = nullptr;
@@ -492,40 +569,66 @@ int pps_filter_host(pps_table* t, const pps_camera* cam, uint32_t frame, const p
     }
     t->stage_cap = need;
   }
-  float* base = static_cast<float*>(t->stage);
-  const float* src[9] = {vh->px, vh->py, vh->pz, vh->nx, vh->ny, vh->nz, vh->r, vh->g, vh->b};
-  float* dst[9];
-  for (int i = 0; i < 9; ++i) {
-    dst[i] = base + static_cast<size_t>(i) * nn;
-    PPS_CUDA(cudaMemcpyAsync(dst[i], src[i], n * sizeof(float), cudaMemcpyHostToDevice, st));
-  }
-  pps_vertices vd{};
-  vd.px = dst[0];
-  vd.py = dst[1];
-  vd.pz = dst[2];
-  vd.nx = dst[3];
-  vd.ny = dst[4];
-  vd.nz = dst[5];
-  vd.r = dst[6];
-  vd.g = dst[7];
-  vd.b = dst[8];
-  vd.id_base = vh->id_base;
-  vd.stream_id = vh->stream_id;
-  pps_output od{};
-  od.r = base + 9 * nn;
-  od.g = base + 10 * nn;
-  od.b = base + 11 * nn;
-  od.count = oh->count ? reinterpret_cast<uint32_t*>(base + 12 * nn) : nullptr;
-  od.status = oh->status ? reinterpret_cast<uint8_t*>(base + 13 * nn) : nullptr;
+  pps_vertices vd;
+  pps_output od;
+  if (int rc = host_upload(vh, n, oh, t->stage, st, &vd, &od)) return rc;
   if (int rc = pps_filter(t, cam, frame, &vd, n, blend, alpha, &od, stream)) return rc;
-  PPS_CUDA(cudaMemcpyAsync(oh->r, od.r, n * sizeof(float), cudaMemcpyDeviceToHost, st));
-  PPS_CUDA(cudaMemcpyAsync(oh->g, od.g, n * sizeof(float), cudaMemcpyDeviceToHost, st));
-  PPS_CUDA(cudaMemcpyAsync(oh->b, od.b, n * sizeof(float), cudaMemcpyDeviceToHost, st));
-  if (oh->count)
-    PPS_CUDA(cudaMemcpyAsync(oh->count, od.count, n * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
-  if (oh->status)
-    PPS_CUDA(cudaMemcpyAsync(oh->status, od.status, n, cudaMemcpyDeviceToHost, st));
+  if (int rc = host_download(&od, n, oh, st)) return rc;
   PPS_CUDA(cudaStreamSynchronize(st));
+  return PPS_OK;
+}
+
+int pps_filter_host_async(pps_table* t, const pps_camera* cam, uint32_t frame,
+                          const pps_vertices* vh, size_t n, int blend, float alpha,
+                          const pps_output* oh, void* stream) {
+  if (int rc = check_host_call(t, vh, n, oh)) return rc;
+  const cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (!t->up) {
+    PPS_CUDA(cudaStreamCreateWithFlags(&t->up, cudaStreamNonBlocking));
+    PPS_CUDA(cudaStreamCreateWithFlags(&t->down, cudaStreamNonBlocking));
+    for (auto& h : t->hslot) {
+      PPS_CUDA(cudaEventCreateWithFlags(&h.in_ready, cudaEventDisableTiming));
+      PPS_CUDA(cudaEventCreateWithFlags(&h.computed, cudaEventDisableTiming));
+      PPS_CUDA(cudaEventCreateWithFlags(&h.done, cudaEventDisableTiming));
+    }
+  }
+  pps_table::HostSlot& h = t->hslot[t->host_calls & 1];
+  const size_t need = host_stage_bytes(n);
+  if (h.cap < need) {
+    if (h.used) PPS_CUDA(cudaEventSynchronize(h.done));
+    cudaFree(h.dev);
+    h.dev = nullptr;
+    h.cap = 0;
+    cudaError_t e = cudaMalloc(&h.dev, need);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(PPS_ENOMEM, "pps_filter_host_async: staging allocation failed");
+    }
+    h.cap = need;
+  }
+  // uploads once this slot's previous results are home
+  if (h.used) PPS_CUDA(cudaStreamWaitEvent(t->up, h.done, 0));
+  pps_vertices vd;
+  pps_output od;
+  if (int rc = host_upload(vh, n, oh, h.dev, t->up, &vd, &od)) return rc;
+  PPS_CUDA(cudaEventRecord(h.in_ready, t->up));
+  // the filter on the caller's stream once the inputs are there
+  PPS_CUDA(cudaStreamWaitEvent(st, h.in_ready, 0));
+  if (int rc = pps_filter(t, cam, frame, &vd, n, blend, alpha, &od, stream)) return rc;
+  PPS_CUDA(cudaEventRecord(h.computed, st));
+  // downloads once the filter is done
+  PPS_CUDA(cudaStreamWaitEvent(t->down, h.computed, 0));
+  if (int rc = host_download(&od, n, oh, t->down)) return rc;
+  PPS_CUDA(cudaEventRecord(h.done, t->down));
+  h.used = true;
+  ++t->host_calls;
+  return PPS_OK;
+}
+
+int pps_host_wait(pps_table* t) {
+  if (int rc = check_table(t)) return rc;
+  for (auto& h : t->hslot)
+    if (h.used) PPS_CUDA(cudaEventSynchronize(h.done));
   return PPS_OK;
 }
 

@@ -96,6 +96,10 @@ SIGNATURES = {
     "pps_filter_host": ([_vp, ctypes.POINTER(pps_camera), _u32, ctypes.POINTER(pps_vertices),
                          ctypes.c_size_t, ctypes.c_int, _f32, ctypes.POINTER(pps_output), _vp],
                         ctypes.c_int),
+    "pps_filter_host_async": ([_vp, ctypes.POINTER(pps_camera), _u32,
+                               ctypes.POINTER(pps_vertices), ctypes.c_size_t, ctypes.c_int, _f32,
+                               ctypes.POINTER(pps_output), _vp], ctypes.c_int),
+    "pps_host_wait": ([_vp], ctypes.c_int),
     "pps_keys": ([_vp, ctypes.POINTER(pps_vertices), ctypes.c_size_t, _vp, _vp, _vp],
                  ctypes.c_int),
     "pps_stats": ([_vp, ctypes.POINTER(pps_stats_t), _vp], ctypes.c_int),
@@ -264,6 +268,17 @@ def pps_filter_host(handle, cam: pps_camera, frame: int, v: pps_vertices, n: int
     _check(lib().pps_filter_host(handle, ctypes.byref(cam), frame & 0xFFFFFFFF, ctypes.byref(v),
                                  n, 1 if blend else 0, float(alpha), ctypes.byref(out),
                                  _stream(stream)))
+
+
+def pps_filter_host_async(handle, cam: pps_camera, frame: int, v: pps_vertices, n: int,
+                          blend: bool, alpha: float, out: pps_output, stream=None):
+    _check(lib().pps_filter_host_async(handle, ctypes.byref(cam), frame & 0xFFFFFFFF,
+                                       ctypes.byref(v), n, 1 if blend else 0, float(alpha),
+                                       ctypes.byref(out), _stream(stream)))
+
+
+def pps_host_wait(handle):
+    _check(lib().pps_host_wait(handle))
 
 
 def pps_filter_noalloc(params: pps_params, cam: pps_camera, frame: int, v: pps_vertices, n: int,

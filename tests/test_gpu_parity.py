@@ -338,6 +338,39 @@ def test_filter_host_matches_device_path():
     tab.close()
 
 
+def test_filter_host_async_matches_device_path():
+    """Four temporal frames through the pipelined host-buffer call (uploads of
+    one frame overlapping the filter of the previous), each into its own host
+    outputs, equal the same frames through the device path (fixed point, so
+    bit for bit), including the blend's frame-to-frame history."""
+    w = configs.small()
+    _, cfg = _small(width=100, height=80, bounces=2, accum_fixed=True, hist_mode=1,
+                    log2_hist_slots=18)
+    tab_d, tab_h = pps.Table(cfg), pps.Table(cfg)
+    outs_h, refs, keep = [], [], []
+    for f in range(4):
+        spec = configs.frame_spec(w, 0, f)
+        spec.view = scene.View(100, 80, eye=(0.05 * f, 3.0, -12.0), target=(0.05 * f, 0.5, 0.0))
+        spec.bounces = 2
+        v = _gen(spec, f)
+        n = v["px"].numel()
+        refs.append({k: t.cpu() for k, t in tab_d.filter(_dev(v), spec.view.eye, f, blend=True,
+                                                          alpha=0.3).items()})
+        host = {k: v[k].contiguous().pin_memory() for k in scene.STREAMS}
+        oh = {k: t.pin_memory() for k, t in pps.empty_output(n, "cpu").items()}
+        keep.append(host)
+        outs_h.append(oh)
+        pps.pps_filter_host_async(tab_h.handle, pps.camera(spec.view.eye), f,
+                                  pps.make_vertices(host, n, device=False), n, True, 0.3,
+                                  pps.make_output(oh, n, device=False))
+    pps.pps_host_wait(tab_h.handle)
+    for oh, ref in zip(outs_h, refs):
+        for c in ("r", "g", "b", "count", "status"):
+            assert torch.equal(oh[c], ref[c]), c
+    tab_d.close()
+    tab_h.close()
+
+
 def test_call_order_and_argument_errors():
     spec, cfg = _small()
     v = _dev(_gen(spec))
