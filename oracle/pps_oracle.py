@@ -26,6 +26,10 @@ What it computes, and from which passage
   integrating weight alpha = N_old / (N_old + N_new).
 * Overflow audit (Sec. 3.2: the probe limit, after which a vertex keeps its
   own unfiltered contribution): a helper that checks a table dump.
+* History eviction (Sec. 3.4.3): a sequential model of a history table whose
+  fingerprint words carry a priority (the frame of last use) in their top
+  bits, so that a cell without room replaces the least recently used entry
+  of its probe window.
 * Fallbacks for cells with few vertices (Sec. 3.3.2 neighborhood search,
   Sec. 3.3.3 multi-level accumulation): the pooled average of the 3x3x3
   block of cells around a vertex's cell, and the average of the next coarser
@@ -609,3 +613,70 @@ def neighborhood(fr: FrameResult, threshold: int, cell_value=None, cell_weight=N
         s64 = np.where(ok[:, :, None], cv[nbc] * wn[:, :, None], 0.0).sum(axis=1)
         value64[idx] = s64 / tot[:, None]
     return value64, value_fx, count, status
+
+
+# ----------------------------------------------------------------------------
+# History eviction, Sec. 3.4.3: the most significant bits of a history
+# fingerprint word hold a priority -- here the blend epoch (frame) of the
+# entry's last use, 1..255 -- and the low 24 bits the fingerprint, so that one
+# word compare orders entries by recency.  0 is an empty cell.
+# ----------------------------------------------------------------------------
+EVICT_FP_BITS = 24
+EVICT_FP_MASK = (1 << EVICT_FP_BITS) - 1
+
+
+def evict_word(rank: int, f) -> np.ndarray:
+    """Priority `rank` (1..255) over the low 24 fingerprint bits."""
+    return ((np.uint32(rank) << np.uint32(EVICT_FP_BITS)) |
+            (np.asarray(f, dtype=U32) & U32(EVICT_FP_MASK))).astype(U32)
+
+
+def history_evict_step(table: np.ndarray, home: np.ndarray, fp: np.ndarray, rank: int,
+                       max_probes: int):
+    """One frame of an evicting history table, cells in the given order.
+
+    For each cell (home h, fingerprint f): scan h .. h+P-1; the first empty
+    word is claimed (fresh entry); a word whose low 24 bits equal f's is the
+    cell's entry (kept, its priority set to `rank`); if the window is full,
+    the entry with the smallest word (oldest priority, then smallest
+    fingerprint) is replaced when its priority is older than `rank` (fresh
+    entry), otherwise the cell has no history this frame.
+
+    Updates `table` (uint32 words) in place and returns, per cell, the slot
+    (-1: none) and whether the entry is fresh (no usable history)."""
+    T = table.shape[0]
+    slot = np.full(home.shape[0], -1, dtype=np.int64)
+    fresh = np.zeros(home.shape[0], dtype=bool)
+    f24 = (np.asarray(fp, dtype=np.uint64) & EVICT_FP_MASK).astype(np.int64)
+    nw = evict_word(rank, fp).astype(np.int64)
+    for j in range(home.shape[0]):
+        victim, vword = -1, None
+        for p in range(max_probes):
+            q = (int(home[j]) + p) % T
+            w = int(table[q])
+            if w == 0:
+                table[q] = nw[j]
+                slot[j], fresh[j] = q, True
+                break
+            if (w & EVICT_FP_MASK) == f24[j]:
+                table[q] = nw[j]
+                slot[j] = q
+                break
+            if vword is None or w < vword:
+                victim, vword = q, w
+        else:
+            if (vword >> EVICT_FP_BITS) < rank:
+                table[victim] = nw[j]
+                slot[j], fresh[j] = victim, True
+    return slot, fresh
+
+
+def history_age(table: np.ndarray, by: int = 128) -> None:
+    """Rebase the priorities when the epoch counter runs out: every non-empty
+    word's priority drops by `by` (at least 1 stays), keeping the order of
+    entries used within the last 255 - by epochs."""
+    nz = table != 0
+    r = (table >> U32(EVICT_FP_BITS)).astype(np.int64)
+    r = np.maximum(r - by, 1)
+    table[nz] = ((r[nz].astype(np.uint64) << EVICT_FP_BITS) |
+                 (table[nz].astype(np.uint64) & EVICT_FP_MASK)).astype(U32)
