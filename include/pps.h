@@ -118,6 +118,17 @@ extern "C" {
  *                     pps_batch_create and pps_filter_noalloc reject them, and
  *                     pps_stats / pps_table_dump / pps_keys describe the
  *                     table's own (finest) resolution.
+ *  hist_evict         1: the history table evicts (Sec. 3.4.3).  Its 32-bit
+ *                     fingerprint words hold a priority in the top 8 bits --
+ *                     the blend epoch of the entry's last use (1..255, counted
+ *                     per table; when it runs out every priority drops by 128)
+ *                     -- over the fingerprint's low 24 bits.  A cell that finds
+ *                     neither its entry nor an empty cell in its P-cell window
+ *                     replaces the entry with the smallest word (least recently
+ *                     used) if that entry is older than this frame, and starts
+ *                     afresh there (no history).  Entries found are refreshed
+ *                     to this epoch.  Needs hist_mode != NONE.  0: no eviction
+ *                     (history entries live as long as the table).
  *  reserved           must be zero.
  */
 typedef struct pps_params {
@@ -137,7 +148,8 @@ typedef struct pps_params {
   uint32_t lowcount_threshold;
   uint32_t log2_hist_slots;
   uint32_t fallback;
-  uint32_t reserved[2];
+  uint32_t hist_evict;
+  uint32_t reserved[1];
 } pps_params;
 
 /* Camera position p_cam of Algorithm 1 (world space). */

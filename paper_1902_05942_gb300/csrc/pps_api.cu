@@ -58,16 +58,19 @@ struct pps_table {
   void* stage = nullptr;  // pps_filter_host device staging
   size_t stage_cap = 0;
   unsigned long long* scratch_u64 = nullptr;  // 1 word for occupancy counting
-  // pps_filter_host_async: two staging slots, an upload and a download stream
+  // pps_filter_host_async: two staging slots; the uploads may spread over
+  // kUpStreams streams (three measured no faster than one), one download stream
+  static constexpr int kUpStreams = 1;
   struct HostSlot {
     void* dev = nullptr;
     size_t cap = 0;
-    cudaEvent_t in_ready = nullptr, computed = nullptr, done = nullptr;
+    cudaEvent_t in_ready[kUpStreams] = {}, computed = nullptr, done = nullptr;
     bool used = false;
   };
   HostSlot hslot[2];
-  cudaStream_t up = nullptr, down = nullptr;
+  cudaStream_t up[kUpStreams] = {}, down = nullptr;
   uint64_t host_calls = 0;
+  uint32_t epoch = 0;           // evicting history: blends so far (priority of this frame)
   pps_table* coarse = nullptr;  // multi-level accumulation: the next coarser resolution
   void* fb = nullptr;           // multi-level scratch: coarse results and fine status
   size_t fb_cap = 0;            // vertices the scratch holds
@@ -95,6 +98,9 @@ int check_params(const pps_params* p) {
   if (p->log2_hist_slots != 0 && p->max_probes > (1ull << p->log2_hist_slots))
     return fail(PPS_EINVAL, "max_probes exceeds the history table size");
   if (p->fallback > PPS_FALLBACK_NEIGHBORS) return fail(PPS_EINVAL, "bad fallback");
+  if (p->hist_evict > 1) return fail(PPS_EINVAL, "hist_evict must be 0 or 1");
+  if (p->hist_evict && p->hist_mode == PPS_HIST_NONE)
+    return fail(PPS_EINVAL, "hist_evict needs a history (hist_mode != NONE)");
   if (p->fallback == PPS_FALLBACK_COARSE && !std::isfinite(2.0f * p->voxel_scale))
     return fail(PPS_EINVAL, "voxel_scale too large for a coarser level");
   for (uint32_t r : p->reserved)
@@ -235,12 +241,27 @@ void free_all(pps_table* t) {
   cudaFree(t->fb);
   for (auto& h : t->hslot) {
     cudaFree(h.dev);
-    if (h.in_ready) cudaEventDestroy(h.in_ready);
+    for (cudaEvent_t e : h.in_ready)
+      if (e) cudaEventDestroy(e);
     if (h.computed) cudaEventDestroy(h.computed);
     if (h.done) cudaEventDestroy(h.done);
   }
-  if (t->up) cudaStreamDestroy(t->up);
+  for (cudaStream_t s : t->up)
+    if (s) cudaStreamDestroy(s);
   if (t->down) cudaStreamDestroy(t->down);
+}
+
+// Evicting history: the priority of the coming blend.  Priorities are 8-bit
+// epochs 1..255; when they run out, every entry drops by 128 (the order of
+// the last 127 epochs survives) and counting resumes at 128.
+int next_epoch(pps_table* t, cudaStream_t st) {
+  if (!t->dev.hist_evict) return PPS_OK;
+  if (t->epoch >= 255) {
+    PPS_CUDA(pps::launch_hist_age(t->dev, 128u, st));
+    t->epoch -= 128;
+  }
+  t->dev.hist_rank = ++t->epoch;
+  return PPS_OK;
 }
 
 // Multi-level scratch for n vertices: the coarse pass's r, g, b, count and
@@ -334,6 +355,7 @@ int pps_create(pps_table** out, const pps_params* p) {
   t->kc.jitter = p->jitter;
   t->kc.nih = p->normal_in_home_hash;
   t->dev.neighbors = p->fallback == PPS_FALLBACK_NEIGHBORS ? 1 : 0;
+  t->dev.hist_evict = p->hist_evict ? 1 : 0;
   if (p->fallback == PPS_FALLBACK_COARSE) {
     // the next coarser resolution: s doubled, so every level grows by one
     pps_params pc = *p;
@@ -393,6 +415,7 @@ int pps_blend(pps_table* t, float alpha, void* stream) {
   if (!temporal(t)) return fail(PPS_EINVAL, "pps_blend needs a table with hist_mode != NONE");
   if (!std::isfinite(alpha) || alpha > 1.0f) return fail(PPS_EINVAL, "alpha must be finite and <= 1");
   if (t->state != kOpen) return fail(PPS_ESTATE, "pps_blend needs an open frame (pps_build, pps_insert)");
+  if (int rc = next_epoch(t, static_cast<cudaStream_t>(stream))) return rc;
   PPS_CUDA(pps::launch_blend(t->dev, t->frame_tiles, alpha, static_cast<cudaStream_t>(stream)));
   t->state = kBlended;
   if (t->coarse) return pps_blend(t->coarse, alpha, stream);
@@ -438,7 +461,7 @@ int filter_one(pps_table* t, const pps_camera* cam, uint32_t frame, const pps_ve
   set_camera(t, cam, frame);
   if (n == 0) return PPS_OK;
   pps::FusedPlan plan;
-  PPS_CUDA(pps::plan_fused(n, temporal(t), batch_of(t), &plan));
+  PPS_CUDA(pps::plan_fused(n, temporal(t), batch_of(t), &plan, t->dev.hist_evict != 0));
   // cell ids and (off-chip) stash words cover whole tiles: [0, ntiles * tile)
   const size_t ftile = static_cast<size_t>(pps::fused_tile_size());
   const size_t stash_need = (n + ftile - 1) / ftile * ftile;
@@ -454,6 +477,8 @@ int filter_one(pps_table* t, const pps_camera* cam, uint32_t frame, const pps_ve
     }
     t->gstash_cap = stash_need;
   }
+  if (blend)
+    if (int rc = next_epoch(t, st)) return rc;
   PPS_CUDA(pps::launch_fused(t->kc, t->dev, to_dev(v), n, out, temporal(t), blend != 0, alpha,
                              plan, t->gstash, st));
   t->state = kClean;
@@ -499,16 +524,18 @@ size_t host_stage_bytes(size_t n) {
   return nn * (9 + 3 + 1) * sizeof(float) + nn;
 }
 
-// Upload the host inputs to `base` on stream `st`; fill the device views.
+// Upload the host inputs to `stage`, array i on stream st[i % nst]; fill the
+// device views.
 int host_upload(const pps_vertices* vh, size_t n, const pps_output* oh, void* stage,
-                cudaStream_t st, pps_vertices* vd, pps_output* od) {
+                const cudaStream_t* st, int nst, pps_vertices* vd, pps_output* od) {
   const size_t nn = (n + 3) & ~static_cast<size_t>(3);
   float* base = static_cast<float*>(stage);
   const float* src[9] = {vh->px, vh->py, vh->pz, vh->nx, vh->ny, vh->nz, vh->r, vh->g, vh->b};
   float* dst[9];
   for (int i = 0; i < 9; ++i) {
     dst[i] = base + static_cast<size_t>(i) * nn;
-    PPS_CUDA(cudaMemcpyAsync(dst[i], src[i], n * sizeof(float), cudaMemcpyHostToDevice, st));
+    PPS_CUDA(cudaMemcpyAsync(dst[i], src[i], n * sizeof(float), cudaMemcpyHostToDevice,
+                             st[i % nst]));
   }
   *vd = pps_vertices{};
   vd->px = dst[0];
@@ -571,7 +598,7 @@ int pps_filter_host(pps_table* t, const pps_camera* cam, uint32_t frame, const p
   }
   pps_vertices vd;
   pps_output od;
-  if (int rc = host_upload(vh, n, oh, t->stage, st, &vd, &od)) return rc;
+  if (int rc = host_upload(vh, n, oh, t->stage, &st, 1, &vd, &od)) return rc;
   if (int rc = pps_filter(t, cam, frame, &vd, n, blend, alpha, &od, stream)) return rc;
   if (int rc = host_download(&od, n, oh, st)) return rc;
   PPS_CUDA(cudaStreamSynchronize(st));
@@ -583,11 +610,13 @@ int pps_filter_host_async(pps_table* t, const pps_camera* cam, uint32_t frame,
                           const pps_output* oh, void* stream) {
   if (int rc = check_host_call(t, vh, n, oh)) return rc;
   const cudaStream_t st = static_cast<cudaStream_t>(stream);
-  if (!t->up) {
-    PPS_CUDA(cudaStreamCreateWithFlags(&t->up, cudaStreamNonBlocking));
+  constexpr int K = pps_table::kUpStreams;
+  if (!t->down) {
+    for (cudaStream_t& s : t->up) PPS_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
     PPS_CUDA(cudaStreamCreateWithFlags(&t->down, cudaStreamNonBlocking));
     for (auto& h : t->hslot) {
-      PPS_CUDA(cudaEventCreateWithFlags(&h.in_ready, cudaEventDisableTiming));
+      for (cudaEvent_t& e : h.in_ready)
+        PPS_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
       PPS_CUDA(cudaEventCreateWithFlags(&h.computed, cudaEventDisableTiming));
       PPS_CUDA(cudaEventCreateWithFlags(&h.done, cudaEventDisableTiming));
     }
@@ -607,13 +636,16 @@ int pps_filter_host_async(pps_table* t, const pps_camera* cam, uint32_t frame,
     h.cap = need;
   }
   // uploads once this slot's previous results are home
-  if (h.used) PPS_CUDA(cudaStreamWaitEvent(t->up, h.done, 0));
+  if (h.used)
+    for (cudaStream_t s : t->up) PPS_CUDA(cudaStreamWaitEvent(s, h.done, 0));
   pps_vertices vd;
   pps_output od;
-  if (int rc = host_upload(vh, n, oh, h.dev, t->up, &vd, &od)) return rc;
-  PPS_CUDA(cudaEventRecord(h.in_ready, t->up));
+  if (int rc = host_upload(vh, n, oh, h.dev, t->up, K, &vd, &od)) return rc;
   // the filter on the caller's stream once the inputs are there
-  PPS_CUDA(cudaStreamWaitEvent(st, h.in_ready, 0));
+  for (int k = 0; k < K; ++k) {
+    PPS_CUDA(cudaEventRecord(h.in_ready[k], t->up[k]));
+    PPS_CUDA(cudaStreamWaitEvent(st, h.in_ready[k], 0));
+  }
   if (int rc = pps_filter(t, cam, frame, &vd, n, blend, alpha, &od, stream)) return rc;
   PPS_CUDA(cudaEventRecord(h.computed, st));
   // downloads once the filter is done
@@ -642,8 +674,8 @@ int table_for_batch(pps_table* t, size_t n, ViewDesc* vd, int* batch, bool* temp
                     cudaStream_t st) {
   if (int rc = check_table(t)) return rc;
   if (t->state != kClean) return fail(PPS_ESTATE, "a table of a batch is in the middle of a frame");
-  if (t->p.fallback != PPS_FALLBACK_NONE)
-    return fail(PPS_EINVAL, "batched views take tables without a low-count fallback");
+  if (t->p.fallback != PPS_FALLBACK_NONE || t->p.hist_evict)
+    return fail(PPS_EINVAL, "batched views take tables without a low-count fallback or eviction");
   const size_t ftile = static_cast<size_t>(fused_tile_size());
   if (int rc = ensure_dense(t, (n + ftile - 1) / ftile * ftile, 0, st)) return rc;
   vd->kc = t->kc;

@@ -89,6 +89,8 @@ struct TableDev {
   int fixed;                  // accumulation mode
   int hist_mode;              // 0 none, 1 FP32, 2 FP16
   int neighbors;              // low-count vertices take the 3x3x3 pooled average
+  int hist_evict;             // history fingerprints carry a priority (evicting table)
+  uint32_t hist_rank;         // evicting table: this frame's priority (blend epoch)
 };
 
 constexpr uint32_t kNoSlot = 0xFFFFFFFFu;  // info.x of an id reserved but not used
@@ -372,6 +374,57 @@ __device__ __forceinline__ uint32_t hist_probe_rest(const TableDev& t, uint32_t 
     const uint32_t h = (home + p) & t.hmask;
     const uint32_t old = atomicCAS(hist_fp(t, h), 0u, f);
     if (old == 0u || old == f) return h;
+  }
+  return kOverflowSlot;
+}
+
+// Evicting history table (Sec. 3.4.3): fingerprint word = priority << 24 |
+// low 24 bits of the fingerprint, 0 = empty.  Find the cell's entry in its
+// window (refreshing its priority to this frame's), or claim the first empty
+// cell, or -- with the window full -- replace the smallest word if its
+// priority is older than this frame's.  `fresh`: the entry holds no history
+// of this cell.  Compare-and-swaps on the whole word keep a concurrent
+// claim, refresh or replacement from being lost; a few retries, then none.
+static __device__ __noinline__ uint32_t hist_claim_evict(const TableDev& t, uint32_t home,
+                                                         uint32_t f, bool* fresh) {
+  const uint32_t f24 = f & 0xFFFFFFu;
+  const uint32_t nw = (t.hist_rank << 24) | f24;
+  for (int attempt = 0; attempt < 4; ++attempt) {
+    uint32_t victim = kOverflowSlot, vword = 0xFFFFFFFFu;
+    bool retry = false;
+    for (uint32_t p = 0; p < t.max_probes; ++p) {
+      const uint32_t h = (home + p) & t.hmask;
+      uint32_t* fp = hist_fp(t, h);
+      uint32_t w = __ldcg(fp);
+      if (w == 0u) {
+        w = atomicCAS(fp, 0u, nw);
+        if (w == 0u) {
+          *fresh = true;
+          return h;
+        }
+      }
+      if ((w & 0xFFFFFFu) == f24) {
+        if (w != nw) {
+          const uint32_t o = atomicCAS(fp, w, nw);
+          if (o != w && (o & 0xFFFFFFu) != f24) {
+            retry = true;  // replaced under us: scan again
+            break;
+          }
+        }
+        *fresh = false;
+        return h;
+      }
+      if (w < vword) {
+        vword = w;
+        victim = h;
+      }
+    }
+    if (retry) continue;
+    if ((vword >> 24) >= t.hist_rank) return kOverflowSlot;  // all entries are this frame's
+    if (atomicCAS(hist_fp(t, victim), vword, nw) == vword) {
+      *fresh = true;
+      return victim;
+    }
   }
   return kOverflowSlot;
 }

@@ -17,6 +17,7 @@ struct FusedPlan {
   uint32_t cap_tiles = 0;  // tiles one CTA may take (stash capacity)
   size_t smem = 0;         // dynamic shared memory per CTA (stash of cap_tiles tiles)
   bool global_stash = false;
+  bool evict = false;      // the kernel variant for an evicting history
 };
 
 // One view of a batched launch: its table, key constants, vertices and
@@ -62,6 +63,8 @@ cudaError_t launch_keys(const KeyConst& kc, const VertexPtrs& v, size_t n, uint3
                         uint32_t* f_out, cudaStream_t st);
 cudaError_t launch_blend(const TableDev& t, uint32_t ntiles, float alpha, cudaStream_t st);
 cudaError_t launch_clear(const TableDev& t, uint32_t ntiles, cudaStream_t st);
+// Evicting history: lower every entry's priority by `by` (epoch rebase).
+cudaError_t launch_hist_age(const TableDev& t, uint32_t by, cudaStream_t st);
 // Multi-level accumulation: vertices with fine status LOWCOUNT take the
 // coarse resolution's value, count and status COARSE (unless the coarse
 // insert overflowed).  `fine_status` may alias o.status.
@@ -69,7 +72,7 @@ cudaError_t launch_combine_coarse(size_t n, const uint8_t* fine_status, const Ou
                                   const OutPtrs& o, cudaStream_t st);
 cudaError_t launch_count_nonzero(const void* base, uint32_t stride, uint32_t off, uint32_t width,
                                  uint64_t n, unsigned long long* out, cudaStream_t st);
-cudaError_t plan_fused(size_t n, bool temporal, int batch, FusedPlan* plan);
+cudaError_t plan_fused(size_t n, bool temporal, int batch, FusedPlan* plan, bool evict = false);
 cudaError_t launch_fused(const KeyConst& kc, const TableDev& t, const VertexPtrs& v, size_t n,
                          const OutPtrs& o, bool temporal, bool blend, float alpha,
                          const FusedPlan& plan, uint32_t* gstash, cudaStream_t st);

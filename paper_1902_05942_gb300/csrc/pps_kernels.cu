@@ -457,10 +457,23 @@ __device__ __forceinline__ void blend_cells(const TableDev& t, const uint32_t (&
     if (use[q]) blend_store(t, d[q], h[q], mean_of(t, a[q]), hv[q], alpha);
 }
 
+// The same for an evicting history (Sec. 3.4.3), one cell at a time, kept
+// out of line so that the common path above keeps its registers.
+__device__ __noinline__ unsigned long long blend_cell_evict(const TableDev& t, uint32_t d,
+                                                            uint32_t home, uint32_t f,
+                                                            float alpha) {
+  const AccRaw a = load_acc(t, d);
+  bool fresh = true;
+  const uint32_t h = hist_claim_evict(t, home, f, &fresh);
+  const HistRaw hv = h != kOverflowSlot && !fresh ? load_hist(t, h) : HistRaw{0.f, 0.f, 0.f, 0u};
+  blend_store(t, d, h, mean_of(t, a), hv, alpha);
+  return h == kOverflowSlot ? 1ull : 0ull;
+}
+
 // Blend the cells [base, base + count): each thread takes BW cells, one from
 // each of BW consecutive runs of `stride` ids (coalesced loads), and issues
 // their history probes together.  `first` is this thread's offset.
-template <int BW>
+template <int BW, bool EVICT>
 __device__ __forceinline__ void blend_range(const TableDev& t, uint32_t base, uint32_t count,
                                             uint32_t first, uint32_t stride, float alpha,
                                             unsigned long long& n_hovf) {
@@ -480,10 +493,16 @@ __device__ __forceinline__ void blend_range(const TableDev& t, uint32_t base, ui
         use[q] = in.x != kNoSlot;
         home[q] = in.y & t.hmask;
         f[q] = in.z;
-        if (use[q]) a[q] = load_acc(t, d[q]);
+        if (use[q] && !EVICT) a[q] = load_acc(t, d[q]);
       }
     }
-    blend_cells<BW>(t, d, home, f, use, a, alpha, n_hovf);
+    if constexpr (EVICT) {
+#pragma unroll
+      for (int q = 0; q < BW; ++q)
+        if (use[q]) n_hovf += blend_cell_evict(t, d[q], home[q], f[q], alpha);
+    } else {
+      blend_cells<BW>(t, d, home, f, use, a, alpha, n_hovf);
+    }
   }
 }
 
@@ -589,7 +608,10 @@ __global__ void __launch_bounds__(kBlock) k_query(KeyConst kc, TableDev t, Verte
 __global__ void __launch_bounds__(kBlock) k_blend_sweep(TableDev t, uint32_t ntiles, float alpha) {
   unsigned long long n_hovf = 0;
   for (uint32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x)
-    blend_range<4>(t, tile * kTile, t.bcount[tile], threadIdx.x, blockDim.x, alpha, n_hovf);
+    if (t.hist_evict)
+      blend_range<4, true>(t, tile * kTile, t.bcount[tile], threadIdx.x, blockDim.x, alpha, n_hovf);
+    else
+      blend_range<4, false>(t, tile * kTile, t.bcount[tile], threadIdx.x, blockDim.x, alpha, n_hovf);
   const unsigned long long h = block_sum(n_hovf);
   if (threadIdx.x == 0 && h) atomicAdd(&t.ctrl->hist_overflow, h);
 }
@@ -654,7 +676,7 @@ struct FusedArgs {
 // cell id in its shared-memory stash, and later blends, looks up and clears
 // exactly those tiles.  A tile's new cells take ids from the tile's own range
 // [tile * kFusedTile, tile * kFusedTile + claims).
-template <bool TEMPORAL, int W>
+template <bool TEMPORAL, int W, bool EVICT = false>
 __global__ void __launch_bounds__(kFusedBlock, W == 4 ? 1 : 2) k_fused(FusedArgs a) {
   extern __shared__ __align__(16) uint32_t s_stash[];
   __shared__ uint32_t s_tile[kMaxTilesPerCta];
@@ -722,8 +744,8 @@ __global__ void __launch_bounds__(kFusedBlock, W == 4 ? 1 : 2) k_fused(FusedArgs
   if (blended) {
     unsigned long long n_hovf = 0;
     for (uint32_t k = 0; k < taken; ++k)
-      blend_range<W>(t, s_tile[k] * static_cast<uint32_t>(kFusedTile), s_claims[k], threadIdx.x,
-                     blockDim.x, a.alpha, n_hovf);
+      blend_range<W, EVICT>(t, s_tile[k] * static_cast<uint32_t>(kFusedTile), s_claims[k],
+                            threadIdx.x, blockDim.x, a.alpha, n_hovf);
     const unsigned long long h = block_sum(n_hovf);
     if (threadIdx.x == 0 && h) atomicAdd(&t.ctrl->hist_overflow, h);
     if (!grid_barrier(t.ctrl, gridDim.x)) return;
@@ -868,7 +890,7 @@ __global__ void __launch_bounds__(kFusedBlock, W == 4 ? 1 : 2) k_fused_multi(Mul
       __syncthreads();
       if (!s_vd.blended) continue;
       unsigned long long n_hovf = 0;
-      blend_range<W>(s_vd.t, s_tile[k] * static_cast<uint32_t>(kFusedTile), s_claims[k],
+      blend_range<W, false>(s_vd.t, s_tile[k] * static_cast<uint32_t>(kFusedTile), s_claims[k],
                      threadIdx.x, blockDim.x, a.alpha, n_hovf);
       if (n_hovf) atomicAdd(&s_vd.t.ctrl->hist_overflow, n_hovf);
     }
@@ -1006,6 +1028,26 @@ cudaError_t launch_clear(const TableDev& t, uint32_t ntiles, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+// Evicting history: when the per-table epoch runs out, every entry's
+// priority drops by `by` (at least 1 remains), keeping the order of recent
+// entries.
+__global__ void __launch_bounds__(kBlock) k_hist_age(TableDev t, uint32_t by) {
+  const size_t Th = static_cast<size_t>(t.hmask) + 1;
+  for (size_t h = blockIdx.x * (size_t)blockDim.x + threadIdx.x; h < Th;
+       h += (size_t)gridDim.x * blockDim.x) {
+    uint32_t* fp = hist_fp(t, static_cast<uint32_t>(h));
+    const uint32_t w = *fp;
+    if (w == 0u) continue;
+    const uint32_t r = w >> 24;
+    *fp = ((r > by ? r - by : 1u) << 24) | (w & 0xFFFFFFu);
+  }
+}
+
+cudaError_t launch_hist_age(const TableDev& t, uint32_t by, cudaStream_t st) {
+  k_hist_age<<<sm_count() * 8, kBlock, 0, st>>>(t, by);
+  return cudaGetLastError();
+}
+
 __global__ void __launch_bounds__(kBlock) k_combine_coarse(size_t n, const uint8_t* fine_status,
                                                            OutPtrs c, OutPtrs o) {
   for (size_t j = blockIdx.x * (size_t)blockDim.x + threadIdx.x; j < n;
@@ -1034,12 +1076,15 @@ cudaError_t launch_count_nonzero(const void* base, uint32_t stride, uint32_t off
   return cudaGetLastError();
 }
 
-template <bool TEMPORAL, int W>
+template <bool TEMPORAL, int W, bool EVICT = false>
 static const void* fused_fn() {
-  return reinterpret_cast<const void*>(k_fused<TEMPORAL, W>);
+  return reinterpret_cast<const void*>(k_fused<TEMPORAL, W, EVICT>);
 }
 
-static const void* fused_kernel(bool temporal, int batch) {
+// The kernel for a frame: with or without a history, an evicting one or not.
+static const void* fused_kernel(bool temporal, int batch, bool evict) {
+  if (temporal && evict)
+    return batch == 2 ? fused_fn<true, 2, true>() : fused_fn<true, 4, true>();
   if (temporal) return batch == 2 ? fused_fn<true, 2>() : fused_fn<true, 4>();
   return batch == 2 ? fused_fn<false, 2>() : fused_fn<false, 4>();
 }
@@ -1073,8 +1118,9 @@ static cudaError_t fused_dyn_smem_limit(const void* fn, size_t* limit) {
   return cudaSuccess;
 }
 
-cudaError_t plan_fused(size_t n, bool temporal, int batch, FusedPlan* plan) {
-  const void* fn = fused_kernel(temporal, batch);
+cudaError_t plan_fused(size_t n, bool temporal, int batch, FusedPlan* plan, bool evict) {
+  const void* fn = fused_kernel(temporal, batch, evict);
+  plan->evict = temporal && evict;
   const int sms = sm_count();
   size_t maxdyn = 0;
   cudaError_t e = fused_dyn_smem_limit(fn, &maxdyn);
@@ -1133,8 +1179,8 @@ cudaError_t launch_fused(const KeyConst& kc, const TableDev& t, const VertexPtrs
   a.blend = blend ? 1 : 0;
   a.sweep = sweep_pays(t, n) ? 1 : 0;
   void* args[] = {&a};
-  return cudaLaunchCooperativeKernel(fused_kernel(temporal, plan.batch), dim3(plan.grid),
-                                     dim3(plan.block), args, plan.smem, st);
+  return cudaLaunchCooperativeKernel(fused_kernel(temporal, plan.batch, plan.evict),
+                                     dim3(plan.grid), dim3(plan.block), args, plan.smem, st);
 }
 
 bool vec_inputs_host(const VertexPtrs& v) { return vec_inputs(v); }

@@ -40,7 +40,8 @@ class pps_params(ctypes.Structure):
                 ("hash_seed_home", _u32), ("hash_seed_fp", _u32),
                 ("normal_in_home_hash", _u32), ("lod_min", _i32), ("lod_max", _i32),
                 ("accum_mode", _u32), ("hist_mode", _u32), ("lowcount_threshold", _u32),
-                ("log2_hist_slots", _u32), ("fallback", _u32), ("reserved", _u32 * 2)]
+                ("log2_hist_slots", _u32), ("fallback", _u32), ("hist_evict", _u32),
+                ("reserved", _u32 * 1)]
 
 
 class pps_camera(ctypes.Structure):
@@ -205,17 +206,19 @@ def make_output(out: Dict[str, torch.Tensor], n: int, device=True) -> pps_output
 
 
 def make_params(cfg, hist_mode: Optional[int] = None, accum_fixed: Optional[bool] = None,
-                log2_hist_slots: Optional[int] = None, fallback: Optional[str] = None) -> pps_params:
+                log2_hist_slots: Optional[int] = None, fallback: Optional[str] = None,
+                hist_evict: Optional[bool] = None) -> pps_params:
     """pps_params from a FilterConfig-like object (attribute names as in configs.py)."""
     hm = cfg.hist_mode if hist_mode is None else hist_mode
     fx = cfg.accum_fixed if accum_fixed is None else accum_fixed
     lh = cfg.log2_hist_slots if log2_hist_slots is None else log2_hist_slots
     fb = getattr(cfg, "fallback", "none") if fallback is None else fallback
+    ev = getattr(cfg, "hist_evict", False) if hist_evict is None else hist_evict
     return pps_params(cfg.log2_slots, cfg.max_probes, cfg.voxel_scale, cfg.pixel_angle,
                       int(cfg.jitter), cfg.seed & 0xFFFFFFFF, cfg.hash_seed_home & 0xFFFFFFFF,
                       cfg.hash_seed_fp & 0xFFFFFFFF, int(cfg.normal_in_home_hash), cfg.lod_min,
                       cfg.lod_max, ACCUM_FIXED if fx else ACCUM_FP32, hm,
-                      cfg.lowcount_threshold, lh, FALLBACKS[fb], (_u32 * 2)(0, 0))
+                      cfg.lowcount_threshold, lh, FALLBACKS[fb], int(bool(ev)), (_u32 * 1)(0))
 
 
 def camera(pos: Sequence[float]) -> pps_camera:
@@ -451,8 +454,10 @@ class Table:
     """One filter table (frame table plus optional history) on the current device."""
 
     def __init__(self, cfg, hist_mode: Optional[int] = None, accum_fixed: Optional[bool] = None,
-                 log2_hist_slots: Optional[int] = None, fallback: Optional[str] = None):
-        self.params = make_params(cfg, hist_mode, accum_fixed, log2_hist_slots, fallback)
+                 log2_hist_slots: Optional[int] = None, fallback: Optional[str] = None,
+                 hist_evict: Optional[bool] = None):
+        self.params = make_params(cfg, hist_mode, accum_fixed, log2_hist_slots, fallback,
+                                  hist_evict)
         self.handle = pps_create(self.params)
         self.T = 1 << self.params.log2_slots
         self.fixed = self.params.accum_mode == ACCUM_FIXED

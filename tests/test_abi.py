@@ -92,7 +92,7 @@ def test_create_rejects_bad_parameters_without_touching_the_gpu(field, value):
 def test_reserved_fields_must_be_zero():
     pps, L = _lib()
     p = _params(pps)
-    p.reserved[1] = 7
+    p.reserved[0] = 7
     h = ctypes.c_void_p()
     assert L.pps_create(ctypes.byref(h), ctypes.byref(p)) == pps.PPS_EINVAL
     assert "reserved" in pps.last_error()
@@ -116,3 +116,13 @@ def test_bad_fallback_is_rejected():
     h = ctypes.c_void_p()
     assert L.pps_create(ctypes.byref(h), ctypes.byref(p)) == pps.PPS_EINVAL
     assert "fallback" in pps.last_error()
+
+
+def test_eviction_needs_a_history():
+    pps, L = _lib()
+    p = _params(pps)
+    p.hist_evict = 1
+    p.hist_mode = 0
+    h = ctypes.c_void_p()
+    assert L.pps_create(ctypes.byref(h), ctypes.byref(p)) == pps.PPS_EINVAL
+    assert "hist_evict" in pps.last_error()
