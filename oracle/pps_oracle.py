@@ -233,22 +233,52 @@ class Keys:
                                 self.nq.astype(np.int64)])
 
 
+def camera_distance(cx, cy, cz, x, y, z) -> np.ndarray:
+    """|p_cam - x| in FP32: sqrt(((dx*dx) + (dy*dy)) + (dz*dz)), each op rounded."""
+    dx = F32(cx) - x
+    dy = F32(cy) - y
+    dz = F32(cz) - z
+    return np.sqrt((dx * dx + dy * dy) + dz * dz)
+
+
+def level_of_detail_at(d, k, lod_min, lod_max) -> np.ndarray:
+    """floor(log2(k * d)) for a given FP32 distance d (exponent bits), clamped."""
+    F = F32(k) * np.asarray(d, dtype=F32)
+    e = ((F.view(U32) >> U32(23)) & U32(0xFF)).astype(np.int32) - 127
+    return np.clip(e, lod_min, lod_max).astype(np.int32)
+
+
 def vertex_keys(p: KeyParams, cam, frame: int, px, py, pz, nx, ny, nz,
-                ids=None, stream: int = 0) -> Keys:
+                ids=None, stream: int = 0, dist=None, extra=None) -> Keys:
     """Algorithm 1 for every vertex.
 
     l  <- level_of_detail(|p_cam - x|)
     x' <- x + jitter(n) * 2^l          (tangent plane of n; skipped if no jitter)
     l' <- level_of_detail(|p_cam - x'|)
     x~ <- floor(x' * 2^-l')            (exact scaling by a power of two)
-    i  <- hash(x~, l') mod T,   f <- hash2(x~, l', q(n)), 0 replaced by 1."""
+    i  <- hash(x~, l') mod T,   f <- hash2(x~, l', q(n)), 0 replaced by 1.
+
+    Key variants (Sec. 3.1.2, 3.1.1 and the caption of Algorithm 1, which
+    lets the hashed arguments be extended):
+    * `dist`: a per-vertex distance d (e.g. the length of the path to the
+      vertex) replaces the camera distance in the first level of detail; the
+      second uses d' = (d - |p_cam - x|) + |p_cam - x'|, the same distance
+      moved by the jitter's change of camera distance (with d = |p_cam - x|,
+      d' = |p_cam - x'| exactly, and the keys are those of Algorithm 1).
+    * `extra`: a per-vertex 32-bit word (e.g. a material or layer id, a
+      quantized incident direction) hashed after the other words into both
+      hashes."""
     px, py, pz, nx, ny, nz = (np.asarray(a, dtype=F32) for a in (px, py, pz, nx, ny, nz))
     n = px.shape[0]
     if ids is None:
         ids = np.arange(n, dtype=np.uint64).astype(U32)
     cx, cy, cz = (F32(c) for c in cam)
     k = footprint_scale(p)
-    l0 = level_of_detail(cx, cy, cz, px, py, pz, k, p.lod_min, p.lod_max)
+    if dist is None:
+        l0 = level_of_detail(cx, cy, cz, px, py, pz, k, p.lod_min, p.lod_max)
+    else:
+        dist = np.asarray(dist, dtype=F32)
+        l0 = level_of_detail_at(dist, k, p.lod_min, p.lod_max)
     if p.jitter:
         u, w = jitter_uw(ids, stream, p.seed, frame)
         (tx, ty, tz), (bx, by, bz) = orthonormal_basis(nx, ny, nz)
@@ -259,7 +289,12 @@ def vertex_keys(p: KeyParams, cam, frame: int, px, py, pz, nx, ny, nz,
         xj = px + jx * E
         yj = py + jy * E
         zj = pz + jz * E
-        l1 = level_of_detail(cx, cy, cz, xj, yj, zj, k, p.lod_min, p.lod_max)
+        if dist is None:
+            l1 = level_of_detail(cx, cy, cz, xj, yj, zj, k, p.lod_min, p.lod_max)
+        else:
+            d1 = (dist - camera_distance(cx, cy, cz, px, py, pz)) + \
+                camera_distance(cx, cy, cz, xj, yj, zj)
+            l1 = level_of_detail_at(d1, k, p.lod_min, p.lod_max)
     else:
         xj, yj, zj = px, py, pz
         l1 = l0
@@ -271,10 +306,11 @@ def vertex_keys(p: KeyParams, cam, frame: int, px, py, pz, nx, ny, nz,
     X, Y, Z = (c.view(U32) for c in q)
     L = l1.astype(np.int32).view(U32)
     NQ = (nq[:, 0] | (nq[:, 1] << 8) | (nq[:, 2] << 16)).astype(U32)
-    home_words = [X, Y, Z, L] + ([NQ] if p.normal_in_home_hash else [])
+    EX = [] if extra is None else [np.asarray(extra, dtype=U32)]
+    home_words = [X, Y, Z, L] + ([NQ] if p.normal_in_home_hash else []) + EX
     h1 = murmur3_32(home_words, p.hash_seed_home)
     home = h1 & U32((1 << p.log2_slots) - 1)
-    f = murmur3_32([X, Y, Z, L, NQ], p.hash_seed_fp)
+    f = murmur3_32([X, Y, Z, L, NQ] + EX, p.hash_seed_fp)
     f = np.where(f == 0, U32(1), f).astype(U32)
     return Keys(xq, l1, l0, nq, home.astype(U32), f, np.column_stack([xj, yj, zj]))
 
@@ -356,10 +392,14 @@ def fixed_mean_f32(sum_fixed: np.ndarray, count: np.ndarray) -> np.ndarray:
 
 def filter_frame(p: KeyParams, cam, frame: int, v: Dict[str, np.ndarray],
                  ids=None, stream: int = 0) -> FrameResult:
-    """One frame of hashed path space filtering over the vertex arrays `v`."""
+    """One frame of hashed path space filtering over the vertex arrays `v`
+    (optional entries "dist" and "extra": the key variants of vertex_keys;
+    the extra word then joins the grouping tuple)."""
     keys = vertex_keys(p, cam, frame, v["px"], v["py"], v["pz"], v["nx"], v["ny"], v["nz"],
-                       ids=ids, stream=stream)
+                       ids=ids, stream=stream, dist=v.get("dist"), extra=v.get("extra"))
     tuples = keys.tuples()
+    if v.get("extra") is not None:
+        tuples = np.column_stack([tuples, np.asarray(v["extra"], dtype=np.uint32).astype(np.int64)])
     uniq, inv, cnt = group_cells(tuples)
     C = uniq.shape[0]
     rgb = np.column_stack([np.asarray(v[c], dtype=F32) for c in ("r", "g", "b")])
