@@ -162,6 +162,20 @@ typedef struct pps_camera {
  *  px,py,pz   position x;  nx,ny,nz unit normal n;  r,g,b contribution.
  *  id         optional per-vertex jitter counter (NULL: id_base + index).
  *  stream_id  second jitter counter word (e.g. a view index).
+ *  dist       optional per-vertex distance for the level of detail (e.g. the
+ *             length of the path to the vertex, Sec. 3.1.1) in place of the
+ *             camera distance: l = level(dist); after the jitter,
+ *             l' = level((dist - |p_cam - x|) + |p_cam - x'|), FP32 with one
+ *             rounding per operation (so dist = |p_cam - x| gives Algorithm 1
+ *             exactly).  NULL: Algorithm 1.
+ *  extra      optional per-vertex 32-bit key word (a material or layer id, a
+ *             quantized incident direction, ...; Sec. 3.1.2 and the caption of
+ *             Algorithm 1) hashed last into both hashes: vertices share a cell
+ *             only if their extra words are equal.  NULL: none.  Use the same
+ *             choice for every call on a table in a frame.
+ * pps_filter runs frames with dist or extra through the split kernels (the
+ * persistent launch is built without them); pps_batch_create,
+ * pps_filter_noalloc and the host-buffer calls reject them.
  * All nine float arrays are required.  16-byte-aligned arrays are read with
  * 128-bit loads; other alignments take a scalar path.
  */
@@ -172,6 +186,8 @@ typedef struct pps_vertices {
   const uint32_t *id;
   uint32_t id_base;
   uint32_t stream_id;
+  const float *dist;
+  const uint32_t *extra;
 } pps_vertices;
 
 /*
@@ -291,7 +307,7 @@ int pps_filter(pps_table *t, const pps_camera *cam, uint32_t frame, const pps_ve
  * pps_filter_host: pps_filter on HOST arrays (pinned or pageable): copies the
  * nine input arrays to library-owned device buffers, filters, copies r, g, b
  * (and count / status when non-NULL) back, and synchronizes `stream`.
- * `v->id` must be NULL.  Errors: as pps_filter.
+ * `v->id`, `v->dist` and `v->extra` must be NULL.  Errors: as pps_filter.
  */
 int pps_filter_host(pps_table *t, const pps_camera *cam, uint32_t frame,
                     const pps_vertices *v_host, size_t n, int blend, float alpha,

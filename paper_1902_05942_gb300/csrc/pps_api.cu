@@ -145,6 +145,8 @@ pps::VertexPtrs to_dev(const pps_vertices* v) {
   d.id = v->id;
   d.id_base = v->id_base;
   d.stream_id = v->stream_id;
+  d.dist = v->dist;
+  d.extra = v->extra;
   return d;
 }
 
@@ -461,7 +463,8 @@ int filter_one(pps_table* t, const pps_camera* cam, uint32_t frame, const pps_ve
   set_camera(t, cam, frame);
   if (n == 0) return PPS_OK;
   pps::FusedPlan plan;
-  PPS_CUDA(pps::plan_fused(n, temporal(t), batch_of(t), &plan, t->dev.hist_evict != 0));
+  PPS_CUDA(pps::plan_fused(n, temporal(t), batch_of(t), &plan, t->dev.hist_evict != 0,
+                           t->dev.neighbors != 0));
   // cell ids and (off-chip) stash words cover whole tiles: [0, ntiles * tile)
   const size_t ftile = static_cast<size_t>(pps::fused_tile_size());
   const size_t stash_need = (n + ftile - 1) / ftile * ftile;
@@ -499,6 +502,14 @@ int pps_filter(pps_table* t, const pps_camera* cam, uint32_t frame, const pps_ve
   if (blend && (!std::isfinite(alpha) || alpha > 1.0f))
     return fail(PPS_EINVAL, "alpha must be finite and <= 1");
   const cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (v->dist || v->extra) {
+    // key variants: the split kernels (the persistent ones are built without them)
+    if (int rc = pps_build(t, cam, frame, stream)) return rc;
+    if (int rc = pps_insert(t, v, n, nullptr, stream)) return rc;
+    if (blend)
+      if (int rc = pps_blend(t, alpha, stream)) return rc;
+    return pps_query(t, v, n, nullptr, out, stream);
+  }
   if (!t->coarse) return filter_one(t, cam, frame, v, n, blend, alpha, to_dev(out), st);
   // multi-level: both resolutions, then the choice per vertex
   pps::OutPtrs c{}, o = to_dev(out);
@@ -572,7 +583,8 @@ int check_host_call(pps_table* t, const pps_vertices* vh, size_t n, const pps_ou
   if (int rc = check_table(t)) return rc;
   if (int rc = check_vertices(vh, n)) return rc;
   if (int rc = check_output(oh, n)) return rc;
-  if (vh->id) return fail(PPS_EINVAL, "host-buffer filtering takes no id array");
+  if (vh->id || vh->dist || vh->extra)
+    return fail(PPS_EINVAL, "host-buffer filtering takes no id, dist or extra array");
   return PPS_OK;
 }
 

@@ -66,6 +66,10 @@ int pps_batch_create(pps_batch** out, const pps_view* views, uint32_t nviews, in
       delete b;
       return bfail(PPS_EINVAL, "view " + std::to_string(i) + ": table, vertices and r, g, b required");
     }
+    if (v.v.dist || v.v.extra) {
+      delete b;
+      return bfail(PPS_EINVAL, "view " + std::to_string(i) + ": batched views take no dist or extra arrays");
+    }
     pps::ViewDesc vd{};
     bool tmp = false;
     int bw = 2;
@@ -75,7 +79,7 @@ int pps_batch_create(pps_batch** out, const pps_view* views, uint32_t nviews, in
     }
     if (i == 0) batch = bw;
     vd.v = pps::VertexPtrs{v.v.px, v.v.py, v.v.pz, v.v.nx, v.v.ny, v.v.nz, v.v.r, v.v.g, v.v.b,
-                           v.v.id, v.v.id_base, v.v.stream_id};
+                           v.v.id, v.v.id_base, v.v.stream_id, v.v.dist, v.v.extra};
     vd.o = pps::OutPtrs{v.out.r, v.out.g, v.out.b, v.out.count, v.out.status};
     vd.n = v.n;
     vd.tile_base = b->total_tiles;

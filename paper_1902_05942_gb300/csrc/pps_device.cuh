@@ -100,6 +100,8 @@ struct VertexPtrs {
   const uint32_t* id;
   uint32_t id_base;
   uint32_t stream_id;
+  const float* dist;       // optional distance for the level of detail
+  const uint32_t* extra;   // optional extra key word
 };
 
 struct OutPtrs {
@@ -156,15 +158,24 @@ __device__ __forceinline__ float pow2_int(int l) {
   return __uint_as_float(static_cast<uint32_t>(l + 127) << 23);
 }
 
-// floor(log2(k * |p_cam - x|)) from the exponent bits of the FP32 product.
-__device__ __forceinline__ int level_of_detail(const KeyConst& kc, float x, float y, float z) {
+// |p_cam - x| in FP32, one rounding per operation.
+__device__ __forceinline__ float camera_distance(const KeyConst& kc, float x, float y, float z) {
   const float dx = __fsub_rn(kc.cam[0], x);
   const float dy = __fsub_rn(kc.cam[1], y);
   const float dz = __fsub_rn(kc.cam[2], z);
-  const float d2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
-  const float F = __fmul_rn(kc.k, __fsqrt_rn(d2));
+  return __fsqrt_rn(__fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz)));
+}
+
+// floor(log2(k * d)) from the exponent bits of the FP32 product.
+__device__ __forceinline__ int level_at(const KeyConst& kc, float d) {
+  const float F = __fmul_rn(kc.k, d);
   const int e = static_cast<int>((__float_as_uint(F) >> 23) & 0xFFu) - 127;
   return min(max(e, kc.lod_min), kc.lod_max);
+}
+
+// Algorithm 1's level_of_detail(|p_cam - x|).
+__device__ __forceinline__ int level_of_detail(const KeyConst& kc, float x, float y, float z) {
+  return level_at(kc, camera_distance(kc, x, y, z));
 }
 
 __device__ __forceinline__ int32_t quantize_coord(float v, float inv) {
@@ -185,15 +196,34 @@ struct Key {
 };
 
 // The words a key is hashed from: the quantized position x~ (three int32 as
-// bits), the level l' and the packed quantized normal.
+// bits), the level l', the packed quantized normal and, if given, an extra
+// word.
 struct KeyWords {
-  uint32_t X, Y, Z, L, NQ;
+  uint32_t X, Y, Z, L, NQ, EX;
+  bool has_ex;
 };
+
+// Where the optional per-vertex inputs of the key variants are: a distance
+// for the level of detail and an extra key word of vertex j (read where they
+// are used, so that a frame without them carries nothing extra).
+struct KeyExtra {
+  const float* dist = nullptr;
+  const uint32_t* extra = nullptr;
+  size_t j = 0;
+};
+
+__device__ __forceinline__ KeyExtra key_extra(const VertexPtrs& v, size_t j) {
+  KeyExtra e;
+  e.dist = v.dist;
+  e.extra = v.extra;
+  e.j = j;
+  return e;
+}
 
 __device__ __forceinline__ KeyWords key_words(const KeyConst& kc, float px, float py, float pz,
                                               float nx, float ny, float nz, uint32_t id,
-                                              uint32_t stream_id) {
-  const int l0 = level_of_detail(kc, px, py, pz);
+                                              uint32_t stream_id, const KeyExtra& ke = KeyExtra{}) {
+  const int l0 = ke.dist ? level_at(kc, __ldg(ke.dist + ke.j)) : level_of_detail(kc, px, py, pz);
   float xj = px, yj = py, zj = pz;
   int l1 = l0;
   if (kc.jitter) {
@@ -215,7 +245,10 @@ __device__ __forceinline__ KeyWords key_words(const KeyConst& kc, float px, floa
     xj = __fadd_rn(px, __fmul_rn(__fadd_rn(__fmul_rn(u, tx), __fmul_rn(w, bx)), E));
     yj = __fadd_rn(py, __fmul_rn(__fadd_rn(__fmul_rn(u, ty), __fmul_rn(w, by)), E));
     zj = __fadd_rn(pz, __fmul_rn(__fadd_rn(__fmul_rn(u, tz), __fmul_rn(w, bz)), E));
-    l1 = level_of_detail(kc, xj, yj, zj);
+    l1 = ke.dist ? level_at(kc, __fadd_rn(__fsub_rn(__ldg(ke.dist + ke.j),
+                                                    camera_distance(kc, px, py, pz)),
+                                          camera_distance(kc, xj, yj, zj)))
+                 : level_of_detail(kc, xj, yj, zj);
   }
   const float inv = pow2_int(-l1);
   KeyWords kw;
@@ -224,6 +257,8 @@ __device__ __forceinline__ KeyWords key_words(const KeyConst& kc, float px, floa
   kw.Z = static_cast<uint32_t>(quantize_coord(zj, inv));
   kw.L = static_cast<uint32_t>(l1);
   kw.NQ = quantize_normal(nx) | (quantize_normal(ny) << 8) | (quantize_normal(nz) << 16);
+  kw.has_ex = ke.extra != nullptr;
+  kw.EX = kw.has_ex ? __ldg(ke.extra + ke.j) : 0u;
   return kw;
 }
 
@@ -234,11 +269,10 @@ __device__ __forceinline__ Key key_hash(const KeyConst& kc, const KeyWords& kw) 
   h = mm_body(h, kw.Y);
   h = mm_body(h, kw.Z);
   h = mm_body(h, kw.L);
+  uint32_t hbytes = 16u;
   if (kc.nih) {
     h = mm_body(h, kw.NQ);
-    h = mm_final(h, 20u);
-  } else {
-    h = mm_final(h, 16u);
+    hbytes = 20u;
   }
   uint32_t f = kc.hseed_fp;
   f = mm_body(f, kw.X);
@@ -246,14 +280,22 @@ __device__ __forceinline__ Key key_hash(const KeyConst& kc, const KeyWords& kw) 
   f = mm_body(f, kw.Z);
   f = mm_body(f, kw.L);
   f = mm_body(f, kw.NQ);
-  f = mm_final(f, 20u);
+  uint32_t fbytes = 20u;
+  if (kw.has_ex) {
+    h = mm_body(h, kw.EX);
+    f = mm_body(f, kw.EX);
+    hbytes += 4u;
+    fbytes += 4u;
+  }
+  h = mm_final(h, hbytes);
+  f = mm_final(f, fbytes);
   return Key{h, f ? f : 1u};
 }
 
 __device__ __forceinline__ Key vertex_key(const KeyConst& kc, float px, float py, float pz,
                                           float nx, float ny, float nz, uint32_t id,
-                                          uint32_t stream_id) {
-  return key_hash(kc, key_words(kc, px, py, pz, nx, ny, nz, id, stream_id));
+                                          uint32_t stream_id, const KeyExtra& ke = KeyExtra{}) {
+  return key_hash(kc, key_words(kc, px, py, pz, nx, ny, nz, id, stream_id, ke));
 }
 
 // ---------------------------------------------------------------- memory helpers

@@ -18,6 +18,7 @@ struct FusedPlan {
   size_t smem = 0;         // dynamic shared memory per CTA (stash of cap_tiles tiles)
   bool global_stash = false;
   bool evict = false;      // the kernel variant for an evicting history
+  bool neigh = false;      // the kernel variant with the neighborhood search
 };
 
 // One view of a batched launch: its table, key constants, vertices and
@@ -72,7 +73,8 @@ cudaError_t launch_combine_coarse(size_t n, const uint8_t* fine_status, const Ou
                                   const OutPtrs& o, cudaStream_t st);
 cudaError_t launch_count_nonzero(const void* base, uint32_t stride, uint32_t off, uint32_t width,
                                  uint64_t n, unsigned long long* out, cudaStream_t st);
-cudaError_t plan_fused(size_t n, bool temporal, int batch, FusedPlan* plan, bool evict = false);
+cudaError_t plan_fused(size_t n, bool temporal, int batch, FusedPlan* plan, bool evict = false,
+                       bool neigh = false);
 cudaError_t launch_fused(const KeyConst& kc, const TableDev& t, const VertexPtrs& v, size_t n,
                          const OutPtrs& o, bool temporal, bool blend, float alpha,
                          const FusedPlan& plan, uint32_t* gstash, cudaStream_t st);

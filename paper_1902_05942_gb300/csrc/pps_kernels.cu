@@ -139,7 +139,9 @@ struct Batch {
 //
 // `rec`: write each new cell's record (t.info) for the later blend and clear;
 // a frame that neither blends nor clears slot by slot never reads it.
-template <int W>
+// KV: the vertices may carry the key variants (distance, extra word); the
+// persistent kernels are built without them.
+template <int W, bool KV = false>
 __device__ __forceinline__ Batch<W> insert_batch(const KeyConst& kc, const TableDev& t,
                                                  const VertexPtrs& v, size_t j, size_t end,
                                                  bool vec, uint32_t id_base, uint32_t* claims,
@@ -160,7 +162,7 @@ __device__ __forceinline__ Batch<W> insert_batch(const KeyConst& kc, const Table
     Key k{0u, 0u};
     if (valid)
       k = vertex_key(kc, PX[q], PY[q], PZ[q], NX[q], NY[q], NZ[q], vertex_id(v, j + q),
-                     v.stream_id);
+                     v.stream_id, KV ? key_extra(v, j + q) : KeyExtra{});
     h1[q] = k.h1;
     f[q] = k.fp;  // 0 marks an absent vertex (fingerprints are never 0)
     lead[q] = valid;
@@ -292,7 +294,7 @@ __device__ __noinline__ Result neighbor_pool(const KeyConst& kc, const TableDev&
                                              Result own) {
   const KeyWords w0 =
       key_words(kc, __ldg(v.px + j), __ldg(v.py + j), __ldg(v.pz + j), __ldg(v.nx + j),
-                __ldg(v.ny + j), __ldg(v.nz + j), vertex_id(v, j), v.stream_id);
+                __ldg(v.ny + j), __ldg(v.nz + j), vertex_id(v, j), v.stream_id, key_extra(v, j));
   float sr = 0.f, sg = 0.f, sb = 0.f;
   long long fr = 0, fg = 0, fb = 0;
   unsigned long long n = 0;
@@ -541,7 +543,7 @@ __global__ void __launch_bounds__(kBlock) k_insert(KeyConst kc, TableDev t, Vert
     for (int sub = 0; sub < 4; sub += W) {
       const size_t j = tile * kTile + threadIdx.x * 4 + sub;
       if (j < n) {
-        const Batch<W> b = insert_batch<W>(kc, t, v, j, n, vec != 0, tix * kTile, &s_claims, c);
+        const Batch<W> b = insert_batch<W, true>(kc, t, v, j, n, vec != 0, tix * kTile, &s_claims, c);
         if (id_out) {
 #pragma unroll
           for (int q = 0; q < W; ++q)
@@ -582,7 +584,8 @@ __global__ void __launch_bounds__(kBlock) k_query(KeyConst kc, TableDev t, Verte
         id[q] = kOverflowSlot;
         if (j + q < n) {
           const Key k = vertex_key(kc, comp(PX, q), comp(PY, q), comp(PZ, q), comp(NX, q),
-                                   comp(NY, q), comp(NZ, q), vertex_id(v, j + q), v.stream_id);
+                                   comp(NY, q), comp(NZ, q), vertex_id(v, j + q), v.stream_id,
+                                   key_extra(v, j + q));
           id[q] = probe_find(t, k.h1 & t.mask, k.fp);
         }
       }
@@ -630,7 +633,7 @@ __global__ void __launch_bounds__(kBlock) k_keys(KeyConst kc, VertexPtrs v, size
        j += (size_t)gridDim.x * blockDim.x) {
     const Key k = vertex_key(kc, __ldcs(v.px + j), __ldcs(v.py + j), __ldcs(v.pz + j),
                              __ldcs(v.nx + j), __ldcs(v.ny + j), __ldcs(v.nz + j),
-                             vertex_id(v, j), v.stream_id);
+                             vertex_id(v, j), v.stream_id, key_extra(v, j));
     h_out[j] = k.h1;
     f_out[j] = k.fp;
   }
@@ -676,7 +679,7 @@ struct FusedArgs {
 // cell id in its shared-memory stash, and later blends, looks up and clears
 // exactly those tiles.  A tile's new cells take ids from the tile's own range
 // [tile * kFusedTile, tile * kFusedTile + claims).
-template <bool TEMPORAL, int W, bool EVICT = false>
+template <bool TEMPORAL, int W, bool EVICT = false, bool NEIGH = false>
 __global__ void __launch_bounds__(kFusedBlock, W == 4 ? 1 : 2) k_fused(FusedArgs a) {
   extern __shared__ __align__(16) uint32_t s_stash[];
   __shared__ uint32_t s_tile[kMaxTilesPerCta];
@@ -771,8 +774,9 @@ __global__ void __launch_bounds__(kFusedBlock, W == 4 ? 1 : 2) k_fused(FusedArgs
     }
   }
   // Neighborhood search for this CTA's low-count vertices (the table is only
-  // read from phase C on, so no barrier is needed before it).
-  if (t.neighbors) {
+  // read from phase C on, so no barrier is needed before it).  A separate
+  // kernel variant, so that the plain one carries no call.
+  if constexpr (NEIGH) {
     for (uint32_t k = 0; k < taken; ++k) {
       const size_t t0 = static_cast<size_t>(s_tile[k]) * kFusedTile;
       const size_t end = min(a.n, t0 + kFusedTile);
@@ -1076,25 +1080,27 @@ cudaError_t launch_count_nonzero(const void* base, uint32_t stride, uint32_t off
   return cudaGetLastError();
 }
 
-template <bool TEMPORAL, int W, bool EVICT = false>
-static const void* fused_fn() {
-  return reinterpret_cast<const void*>(k_fused<TEMPORAL, W, EVICT>);
+template <bool TEMPORAL, bool EVICT, bool NEIGH>
+static const void* fused_fn(int batch) {
+  return batch == 2 ? reinterpret_cast<const void*>(k_fused<TEMPORAL, 2, EVICT, NEIGH>)
+                    : reinterpret_cast<const void*>(k_fused<TEMPORAL, 4, EVICT, NEIGH>);
 }
 
-// The kernel for a frame: with or without a history, an evicting one or not.
-static const void* fused_kernel(bool temporal, int batch, bool evict) {
+// The kernel for a frame: with or without a history, an evicting one or not,
+// with or without the neighborhood search.
+static const void* fused_kernel(bool temporal, int batch, bool evict, bool neigh) {
   if (temporal && evict)
-    return batch == 2 ? fused_fn<true, 2, true>() : fused_fn<true, 4, true>();
-  if (temporal) return batch == 2 ? fused_fn<true, 2>() : fused_fn<true, 4>();
-  return batch == 2 ? fused_fn<false, 2>() : fused_fn<false, 4>();
+    return neigh ? fused_fn<true, true, true>(batch) : fused_fn<true, true, false>(batch);
+  if (temporal) return neigh ? fused_fn<true, false, true>(batch) : fused_fn<true, false, false>(batch);
+  return neigh ? fused_fn<false, false, true>(batch) : fused_fn<false, false, false>(batch);
 }
 
 // Largest dynamic shared memory a k_fused CTA may request: the opt-in limit
 // per block minus the kernel's static shared memory (set once per kernel).
 static cudaError_t fused_dyn_smem_limit(const void* fn, size_t* limit) {
-  static const void* done[8] = {nullptr};
-  static size_t lims[8] = {0};
-  for (int i = 0; i < 8; ++i)
+  static const void* done[16] = {nullptr};
+  static size_t lims[16] = {0};
+  for (int i = 0; i < 16; ++i)
     if (done[i] == fn) {
       *limit = lims[i];
       return cudaSuccess;
@@ -1108,7 +1114,7 @@ static cudaError_t fused_dyn_smem_limit(const void* fn, size_t* limit) {
   const size_t lim = static_cast<size_t>(maxopt) - fa.sharedSizeBytes;
   e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(lim));
   if (e != cudaSuccess) return e;
-  for (int i = 0; i < 8; ++i)
+  for (int i = 0; i < 16; ++i)
     if (!done[i]) {
       done[i] = fn;
       lims[i] = lim;
@@ -1118,9 +1124,11 @@ static cudaError_t fused_dyn_smem_limit(const void* fn, size_t* limit) {
   return cudaSuccess;
 }
 
-cudaError_t plan_fused(size_t n, bool temporal, int batch, FusedPlan* plan, bool evict) {
-  const void* fn = fused_kernel(temporal, batch, evict);
+cudaError_t plan_fused(size_t n, bool temporal, int batch, FusedPlan* plan, bool evict,
+                       bool neigh) {
+  const void* fn = fused_kernel(temporal, batch, evict, neigh);
   plan->evict = temporal && evict;
+  plan->neigh = neigh;
   const int sms = sm_count();
   size_t maxdyn = 0;
   cudaError_t e = fused_dyn_smem_limit(fn, &maxdyn);
@@ -1179,7 +1187,7 @@ cudaError_t launch_fused(const KeyConst& kc, const TableDev& t, const VertexPtrs
   a.blend = blend ? 1 : 0;
   a.sweep = sweep_pays(t, n) ? 1 : 0;
   void* args[] = {&a};
-  return cudaLaunchCooperativeKernel(fused_kernel(temporal, plan.batch, plan.evict),
+  return cudaLaunchCooperativeKernel(fused_kernel(temporal, plan.batch, plan.evict, plan.neigh),
                                      dim3(plan.grid), dim3(plan.block), args, plan.smem, st);
 }
 

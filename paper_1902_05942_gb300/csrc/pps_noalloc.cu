@@ -90,6 +90,8 @@ extern "C" int pps_filter_noalloc(const pps_params* p, const pps_camera* cam, ui
       !(p->voxel_scale > 0.0f) || !(p->pixel_angle > 0.0f) || p->lod_min <= -126 ||
       p->lod_max >= 127 || p->lod_min > p->lod_max || p->jitter > 1 || p->normal_in_home_hash > 1)
     return noalloc_fail(PPS_EINVAL, "pps_filter_noalloc: bad parameters");
+  if (v->dist || v->extra)
+    return noalloc_fail(PPS_EINVAL, "pps_filter_noalloc: no dist or extra arrays");
   if (n && (!v->px || !v->py || !v->pz || !v->nx || !v->ny || !v->nz || !v->r || !v->g ||
             !v->b || !out->r || !out->g || !out->b))
     return noalloc_fail(PPS_EINVAL, "pps_filter_noalloc: vertex and output arrays are required");
@@ -149,6 +151,8 @@ extern "C" int pps_filter_noalloc(const pps_params* p, const pps_camera* cam, ui
   dv.id = v->id;
   dv.id_base = v->id_base;
   dv.stream_id = v->stream_id;
+  dv.dist = v->dist;
+  dv.extra = v->extra;
   pps::OutPtrs dout;
   dout.r = out->r;
   dout.g = out->g;

@@ -51,7 +51,7 @@ class pps_camera(ctypes.Structure):
 class pps_vertices(ctypes.Structure):
     _fields_ = [("px", _vp), ("py", _vp), ("pz", _vp), ("nx", _vp), ("ny", _vp), ("nz", _vp),
                 ("r", _vp), ("g", _vp), ("b", _vp), ("id", _vp), ("id_base", _u32),
-                ("stream_id", _u32)]
+                ("stream_id", _u32), ("dist", _vp), ("extra", _vp)]
 
 
 class pps_output(ctypes.Structure):
@@ -194,7 +194,9 @@ def make_vertices(v: Dict[str, torch.Tensor], n: Optional[int] = None, ids=None,
     n = v["px"].numel() if n is None else n
     ptrs = [_ptr(v[k], n, torch.float32, k, device) for k in STREAM_NAMES]
     return pps_vertices(*ptrs, _ptr(ids, n, torch.int32, "id", device) if ids is not None
-                        else None, id_base & 0xFFFFFFFF, stream_id & 0xFFFFFFFF)
+                        else None, id_base & 0xFFFFFFFF, stream_id & 0xFFFFFFFF,
+                        _ptr(v.get("dist"), n, torch.float32, "dist", device),
+                        _ptr(v.get("extra"), n, torch.int32, "extra", device))
 
 
 def make_output(out: Dict[str, torch.Tensor], n: int, device=True) -> pps_output:
