@@ -51,6 +51,7 @@ struct Dev {
   float* grad;    // [kP] gradient accumulator
   __nv_bfloat16* wb;  // [kWb] BF16 weights
   int32_t* idx;   // [batch] training sample vertex indices
+  unsigned int* err;  // device error word (a tensor-core wait that gave up)
   float lo[3], inv[3];
 };
 
@@ -92,18 +93,12 @@ __device__ __forceinline__ float lo_f(uint32_t w) { return __uint_as_float(w << 
 __device__ __forceinline__ float hi_f(uint32_t w) { return __uint_as_float(w & 0xFFFF0000u); }
 
 // ---------------------------------------------------------------- encoding
-// Encoded columns c and c + 1 (c even) of one vertex: a (sin, cos) pair of
-// one axis and frequency, two normal components, or padding.
-__device__ __forceinline__ float2 enc_pair(int c, const float (&pn)[3], const float (&nr)[3]) {
-  if (c < 72) {
-    const int a = c / 24, k = (c % 24) / 2;
-    float s, co;
-    sincospif(pn[a] * static_cast<float>(1 << k), &s, &co);
-    return make_float2(s, co);
-  }
-  if (c == 72) return make_float2(nr[0], nr[1]);
-  if (c == 74) return make_float2(nr[2], 0.f);
-  return make_float2(0.f, 0.f);
+// In the A-fragment layout of mma.m16n8k16 a lane with t = lane & 3 holds the
+// input columns c = 8 i + 2 t (i = 0..9) of its two rows.  For i < 9 that is
+// the (sin, cos) pair of axis i / 3 at frequency k = 4 (i % 3) + t; column
+// 72 + 2t is (n_x, n_y), (n_z, 0) or padding.
+__device__ __forceinline__ float2 enc_normal(int t, const float (&nr)[3]) {
+  return t == 0 ? make_float2(nr[0], nr[1]) : t == 1 ? make_float2(nr[2], 0.f) : make_float2(0.f, 0.f);
 }
 
 struct VertexIn {
@@ -131,13 +126,21 @@ __device__ __forceinline__ void encode_frag(uint32_t (&a)[5][4], const VertexIn&
                                             const VertexIn& vb, int t) {
 #pragma unroll
   for (int kk = 0; kk < 5; ++kk) {
-    const int c0 = 16 * kk + 2 * t, c1 = c0 + 8;
-    const float2 p00 = enc_pair(c0, va.pn, va.nr), p01 = enc_pair(c0, vb.pn, vb.nr);
-    const float2 p10 = enc_pair(c1, va.pn, va.nr), p11 = enc_pair(c1, vb.pn, vb.nr);
-    a[kk][0] = pack2(p00.x, p00.y);
-    a[kk][1] = pack2(p01.x, p01.y);
-    a[kk][2] = pack2(p10.x, p10.y);
-    a[kk][3] = pack2(p11.x, p11.y);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int i = 2 * kk + h;  // columns 8 i + 2 t, 8 i + 2 t + 1
+      float2 pa, pb;
+      if (i < 9) {
+        const float f = static_cast<float>(1 << (4 * (i % 3) + t));
+        sincospif(va.pn[i / 3] * f, &pa.x, &pa.y);
+        sincospif(vb.pn[i / 3] * f, &pb.x, &pb.y);
+      } else {
+        pa = enc_normal(t, va.nr);
+        pb = enc_normal(t, vb.nr);
+      }
+      a[kk][2 * h] = pack2(pa.x, pa.y);
+      a[kk][2 * h + 1] = pack2(pb.x, pb.y);
+    }
   }
 }
 
@@ -231,75 +234,312 @@ __device__ __forceinline__ void forward16(float (&y)[1][4], Hidden& h, const uin
 
 // ---------------------------------------------------------------- inference
 // For every vertex whose cell count is below `max_count` (and that did not
-// overflow), or every vertex when `all`: evaluate the network and write its RGB
-// (and status PPS_STATUS_MLP unless `all`).  Vertices are compacted per warp
-// into groups of 16 with ballots.
-__global__ void __launch_bounds__(256) k_mlp_infer(Dev d, VertexPtrs v, size_t n, OutPtrs o,
-                                                   uint32_t max_count, int all) {
-  __shared__ SmemW s;
-  __shared__ int32_t queue[8][48];
-  load_weights(s, d.wb);
-  __syncthreads();
+// overflow), or every vertex when `all`, the network's RGB (and status
+// PPS_STATUS_MLP unless `all`).  Two kernels: k_mlp_compact lists the
+// vertices to evaluate; k_mlp_infer_tc evaluates them 128 at a time on the
+// fifth-generation tensor cores.
+// One pass: each thread looks at 4 consecutive vertices, a CTA-wide scan
+// places its CTA's candidates, and one atomic per CTA (1,024 vertices)
+// reserves their places in the list.
+constexpr int kCompactPer = 4;
+__global__ void __launch_bounds__(256) k_mlp_compact(size_t n, const uint8_t* status,
+                                                     const uint32_t* count, uint32_t max_count,
+                                                     int all, int32_t* list, uint32_t* counter) {
+  __shared__ uint32_t s_warp[8];
+  __shared__ uint32_t s_base;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int g = lane >> 2, t = lane & 3;
-  const size_t nwarps = static_cast<size_t>(gridDim.x) * (blockDim.x >> 5);
-  const size_t gw = static_cast<size_t>(blockIdx.x) * (blockDim.x >> 5) + warp;
-  const size_t per = ((n + nwarps - 1) / nwarps + 31) / 32 * 32;
-  const size_t beg = gw * per, end = min(n, beg + per);
-  int qn = 0;
-  for (size_t base = beg;; base += 32) {
-    if (base < end) {
-      const size_t j = base + lane;
-      bool cand = false;
-      if (j < end) {
-        if (all) {
-          cand = true;
-        } else {
-          const uint8_t st = o.status[j];
-          cand = st != PPS_STATUS_OVERFLOW && o.count[j] < max_count;
-        }
-      }
-      const unsigned mask = __ballot_sync(0xFFFFFFFFu, cand);
-      if (cand) queue[warp][qn + __popc(mask & ((1u << lane) - 1u))] = static_cast<int32_t>(j);
-      qn += __popc(mask);
-      __syncwarp();
-    }
-    const bool last = base >= end;
-    while (qn >= 16 || (last && qn > 0)) {
-      const int rows = min(qn, 16);
-      const int64_t ja = g < rows ? queue[warp][g] : -1;
-      const int64_t jb = g + 8 < rows ? queue[warp][g + 8] : -1;
-      uint32_t x0[5][4];
-      encode_frag(x0, load_vertex(d, v, ja), load_vertex(d, v, jb), t);
-      float y[1][4];
-      Hidden h;
-      forward16(y, h, x0, s, d.master, lane);
-      if (t == 0) {
-        if (ja >= 0) {
-          o.r[ja] = y[0][0];
-          o.g[ja] = y[0][1];
-          if (!all) o.status[ja] = PPS_STATUS_MLP;
-        }
-        if (jb >= 0) {
-          o.r[jb] = y[0][2];
-          o.g[jb] = y[0][3];
-          if (!all) o.status[jb] = PPS_STATUS_MLP;
-        }
-      } else if (t == 1) {
-        if (ja >= 0) o.b[ja] = y[0][0];
-        if (jb >= 0) o.b[jb] = y[0][2];
-      }
-      __syncwarp();
-      // drop the 16 evaluated entries from the queue
-      const int rest = qn - rows;
-      const int32_t moved = lane < rest ? queue[warp][rows + lane] : 0;
-      __syncwarp();
-      if (lane < rest) queue[warp][lane] = moved;
-      __syncwarp();
-      qn = rest;
-    }
-    if (last) break;
+  const size_t j0 = (static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x) * kCompactPer;
+  bool f[kCompactPer];
+  uint32_t mine = 0;
+#pragma unroll
+  for (int q = 0; q < kCompactPer; ++q) {
+    const size_t j = j0 + q;
+    f[q] = j < n && (all || (status[j] != PPS_STATUS_OVERFLOW && count[j] < max_count));
+    mine += f[q] ? 1u : 0u;
   }
+  // inclusive scan of `mine` over the warp, then over the warps
+  uint32_t incl = mine;
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) s_warp[warp] = incl;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t tot = 0;
+    for (int w = 0; w < 8; ++w) {
+      const uint32_t c = s_warp[w];
+      s_warp[w] = tot;  // exclusive prefix of the warps
+      tot += c;
+    }
+    s_base = tot ? atomicAdd(counter, tot) : 0u;
+  }
+  __syncthreads();
+  uint32_t pos = s_base + s_warp[warp] + incl - mine;
+#pragma unroll
+  for (int q = 0; q < kCompactPer; ++q)
+    if (f[q]) list[pos++] = static_cast<int32_t>(j0 + q);
+}
+
+// One CTA of 128 threads takes tiles of 128 listed vertices (the MMA's M).
+// Each thread encodes its vertex into a shared-memory tile in the canonical
+// K-major layout without swizzle (core matrices of 8 rows x 16 bytes: byte of
+// (r, k) = (r / 8 * K / 8 + k / 8) * 128 + r % 8 * 16 + k % 8 * 2); one thread
+// issues tcgen05.mma for each layer (A = activations, B = W as [out][in], both
+// K-major, BF16; D = FP32 in tensor memory, 64 columns) and commits it to an
+// mbarrier; the four warps read their 32 rows back with tcgen05.ld, add the
+// bias, apply ReLU, round to BF16 and store the next layer's A tile.  The
+// output layer is N = 16 (rows 3..15 of W4 are zero).
+namespace tc {
+constexpr int kRows = 128;
+constexpr uint32_t kTmemCols = 64;
+
+__device__ __forceinline__ uint32_t cm(int r, int k, int K) {
+  return static_cast<uint32_t>(((r >> 3) * (K >> 3) + (k >> 3)) * 128 + (r & 7) * 16 + (k & 7) * 2);
+}
+
+// The activation tile holds the encoded input (K = 80) and, once layer 1's
+// product is complete, each hidden layer's output (K = 64) in turn.
+struct Smem {
+  alignas(128) unsigned char act[kRows * 80 * 2];
+  alignas(128) unsigned char w1[64 * 80 * 2];
+  alignas(128) unsigned char w2[64 * 64 * 2];
+  alignas(128) unsigned char w3[64 * 64 * 2];
+  alignas(128) unsigned char w4[16 * 64 * 2];
+  float bias[3 * 64 + 16];
+  alignas(8) unsigned long long mbar;
+  uint32_t tmem;
+};
+constexpr size_t kSmemBytes = sizeof(Smem) + 128;  // + alignment of the dynamic base
+
+// Shared-memory matrix descriptor: start address, leading byte offset 128
+// (the next core matrix along K), stride byte offset `sbo` (the next 8 rows),
+// bits 46..48 = 0b001, no swizzle.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t sbo) {
+  return static_cast<uint64_t>((saddr >> 4) & 0x3FFFu) | (static_cast<uint64_t>(128u >> 4) << 16) |
+         (static_cast<uint64_t>((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// Instruction descriptor of kind::f16: D FP32, A and B BF16, both K-major,
+// N / 8 in bits 17..22, M / 16 in bits 24..28.
+__host__ __device__ constexpr uint32_t idesc(uint32_t M, uint32_t N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((N >> 3) << 17) | ((M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t a, uint64_t b, uint32_t id,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d),
+      "l"(a), "l"(b), "r"(id), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void commit(uint32_t mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+               : "memory");
+}
+
+__device__ __forceinline__ void fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+// shared-memory stores of the threads, made visible to the tensor cores
+__device__ __forceinline__ void fence_smem_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// Wait for the mbarrier phase `parity`; gives up after about two seconds.
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
+  const unsigned long long t0 = globaltimer_ns();
+  for (;;) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(mbar), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (globaltimer_ns() - t0 > 2000000000ull) return false;
+  }
+}
+
+__device__ __forceinline__ void tmem_ld_x64(uint32_t taddr, uint32_t (&v)[64]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x64.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32, %33, %34, %35, %36, %37, %38, %39, %40, %41, %42, %43, %44, %45, %46, %47, %48, %49, %50, %51, %52, %53, %54, %55, %56, %57, %58, %59, %60, %61, %62, %63}, [%64];"
+               : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31]), "=r"(v[32]), "=r"(v[33]), "=r"(v[34]), "=r"(v[35]), "=r"(v[36]), "=r"(v[37]), "=r"(v[38]), "=r"(v[39]), "=r"(v[40]), "=r"(v[41]), "=r"(v[42]), "=r"(v[43]), "=r"(v[44]), "=r"(v[45]), "=r"(v[46]), "=r"(v[47]), "=r"(v[48]), "=r"(v[49]), "=r"(v[50]), "=r"(v[51]), "=r"(v[52]), "=r"(v[53]), "=r"(v[54]), "=r"(v[55]), "=r"(v[56]), "=r"(v[57]), "=r"(v[58]), "=r"(v[59]), "=r"(v[60]), "=r"(v[61]), "=r"(v[62]), "=r"(v[63])
+               : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_ld_x16(uint32_t taddr, uint32_t (&v)[16]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+               : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+               : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+__device__ __forceinline__ void st16(unsigned char* base, uint32_t off, uint4 v) {
+  *reinterpret_cast<uint4*>(base + off) = v;
+}
+
+// Encoded row of one vertex, 8 columns (16 bytes) at a time: column block
+// kb < 9 holds (sin, cos)(pi 2^k p_a) for axis a = kb / 3 and k = 4 (kb % 3)
+// .. + 3 -- one sincospif, then three double-angle steps (error at most 8x
+// the FP32 rounding, far below BF16's); block 9 holds n_x, n_y, n_z, 0...
+__device__ __forceinline__ void encode_row(unsigned char* x, int r, const VertexIn& vi, bool valid) {
+#pragma unroll
+  for (int kb = 0; kb < 9; ++kb) {
+    float sn, cs;
+    sincospif(vi.pn[kb / 3] * static_cast<float>(1 << (4 * (kb % 3))), &sn, &cs);
+    uint32_t w[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      w[q] = valid ? pack2(sn, cs) : 0u;
+      const float s2 = 2.f * sn * cs;
+      cs = (cs - sn) * (cs + sn);
+      sn = s2;
+    }
+    st16(x, cm(r, 8 * kb, 80), make_uint4(w[0], w[1], w[2], w[3]));
+  }
+  const uint4 nv = valid ? make_uint4(pack2(vi.nr[0], vi.nr[1]), pack2(vi.nr[2], 0.f), 0u, 0u)
+                         : make_uint4(0u, 0u, 0u, 0u);
+  st16(x, cm(r, 72, 80), nv);
+}
+
+// bias + ReLU + BF16 of 64 accumulator columns of row r, into the A tile h
+__device__ __forceinline__ void hidden_row(unsigned char* h, int r, const uint32_t (&acc)[64],
+                                           const float* bias) {
+#pragma unroll
+  for (int kb = 0; kb < 8; ++kb) {
+    uint32_t w[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int c = 8 * kb + 2 * q;
+      w[q] = pack2(fmaxf(__uint_as_float(acc[c]) + bias[c], 0.f),
+                   fmaxf(__uint_as_float(acc[c + 1]) + bias[c + 1], 0.f));
+    }
+    st16(h, cm(r, 8 * kb, 64), make_uint4(w[0], w[1], w[2], w[3]));
+  }
+}
+
+}  // namespace tc
+
+__global__ void __launch_bounds__(128) k_mlp_infer_tc(Dev d, VertexPtrs v, const int32_t* list,
+                                                      const uint32_t* counter, OutPtrs o, int all) {
+  extern __shared__ unsigned char smem_raw[];
+  tc::Smem& s = *reinterpret_cast<tc::Smem*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~static_cast<uintptr_t>(127));
+  const int tid = threadIdx.x, warp = tid >> 5;
+  // weights in the canonical layout, biases
+  for (int i = tid; i < 64 * kIn; i += blockDim.x)
+    *reinterpret_cast<__nv_bfloat16*>(s.w1 + tc::cm(i / kIn, i % kIn, kIn)) = d.wb[bW1 + i];
+  for (int i = tid; i < 64 * kHid; i += blockDim.x) {
+    *reinterpret_cast<__nv_bfloat16*>(s.w2 + tc::cm(i / kHid, i % kHid, kHid)) = d.wb[bW2 + i];
+    *reinterpret_cast<__nv_bfloat16*>(s.w3 + tc::cm(i / kHid, i % kHid, kHid)) = d.wb[bW3 + i];
+  }
+  for (int i = tid; i < 16 * kHid; i += blockDim.x)
+    *reinterpret_cast<__nv_bfloat16*>(s.w4 + tc::cm(i / kHid, i % kHid, kHid)) = d.wb[bW4 + i];
+  for (int i = tid; i < 3 * 64 + 16; i += blockDim.x) {
+    float b = 0.f;
+    if (i < 64) b = d.master[oB1 + i];
+    else if (i < 128) b = d.master[oB2 + i - 64];
+    else if (i < 192) b = d.master[oB3 + i - 128];
+    else if (i < 192 + kOut) b = d.master[oB4 + i - 192];
+    s.bias[i] = b;
+  }
+  const uint32_t mbar = smem_u32(&s.mbar);
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncwarp();
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&s.tmem)),
+                 "r"(tc::kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc::fence_smem_async();
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tmem = s.tmem;
+  const uint32_t trow = tmem + (static_cast<uint32_t>(warp * 32) << 16);  // this warp's lanes
+  const uint32_t aa = smem_u32(s.act);
+  const uint32_t count = *counter;
+  const uint32_t ntiles = (count + tc::kRows - 1) / tc::kRows;
+  uint32_t parity = 0;
+  bool ok = true;
+  auto row_of = [&](uint32_t tile) -> int64_t {
+    const uint32_t i = tile * tc::kRows + tid;
+    return tile < ntiles && i < count ? list[i] : -1;
+  };
+  int64_t j = row_of(blockIdx.x);
+  VertexIn vi = load_vertex(d, v, j);
+  for (uint32_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+    tc::encode_row(s.act, tid, vi, j >= 0);
+    // the next tile's vertex, loaded while this tile goes through the layers
+    const int64_t jn = row_of(tile + gridDim.x);
+    const VertexIn vn = load_vertex(d, v, jn);
+    tc::fence_smem_async();
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    uint32_t acc[64];
+#pragma unroll 1
+    for (int layer = 0; layer < 4; ++layer) {
+      if (tid == 0) {
+        const uint32_t a = aa;
+        const uint32_t sboa = layer == 0 ? 1280u : 1024u;
+        const uint32_t b = smem_u32(layer == 0 ? s.w1 : layer == 1 ? s.w2 : layer == 2 ? s.w3 : s.w4);
+        const int ksteps = layer == 0 ? 5 : 4;
+        const uint32_t id = layer == 3 ? tc::idesc(128, 16) : tc::idesc(128, 64);
+        for (int k = 0; k < ksteps; ++k)
+          tc::mma_bf16(tmem, tc::sdesc(a + 256u * k, sboa), tc::sdesc(b + 256u * k, sboa), id,
+                       k > 0 ? 1u : 0u);
+        tc::commit(mbar);
+      }
+      ok = __syncthreads_and(tc::mbar_wait(mbar, parity)) != 0;  // the same verdict in every thread
+      parity ^= 1u;
+      if (!ok) break;
+      tc::fence_after();
+      if (layer < 3) {
+        tc::tmem_ld_x64(trow, acc);
+        tc::tmem_wait_ld();
+        tc::hidden_row(s.act, tid, acc, s.bias + 64 * layer);
+        tc::fence_smem_async();
+        tc::fence_before();
+        __syncthreads();
+        tc::fence_after();
+      } else {
+        uint32_t y[16];
+        tc::tmem_ld_x16(trow, y);
+        tc::tmem_wait_ld();
+        if (j >= 0) {
+          o.r[j] = __uint_as_float(y[0]) + s.bias[192];
+          o.g[j] = __uint_as_float(y[1]) + s.bias[193];
+          o.b[j] = __uint_as_float(y[2]) + s.bias[194];
+          if (!all) o.status[j] = PPS_STATUS_MLP;
+        }
+        tc::fence_before();
+        __syncthreads();  // the next tile's MMA overwrites the accumulator
+        tc::fence_after();
+      }
+    }
+    j = jn;
+    vi = vn;
+  }
+  if (!ok && tid == 0) atomicOr(d.err, 1u);
+  tc::fence_before();
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(tc::kTmemCols)
+                 : "memory");
 }
 
 // ---------------------------------------------------------------- training
@@ -550,6 +790,10 @@ struct pps_mlp {
   pps::mlp::Dev dev{};
   size_t idx_cap = 0;
   uint32_t step = 0;  // Adam steps taken
+  int sms = 0;                  // multiprocessors of the device
+  int32_t* list = nullptr;      // inference: indices of the vertices to evaluate
+  uint32_t* counter = nullptr;  // inference: their number
+  size_t list_cap = 0;
 };
 
 namespace {
@@ -576,6 +820,8 @@ pps::VertexPtrs vptrs(const pps_vertices* v) {
   d.id = v->id;
   d.id_base = v->id_base;
   d.stream_id = v->stream_id;
+  d.dist = v->dist;
+  d.extra = v->extra;
   return d;
 }
 
@@ -616,6 +862,7 @@ int pps_mlp_create(pps_mlp** out, const pps_mlp_params* p, const float* init_hos
   if (!m) return mfail(PPS_ENOMEM, "host allocation failed");
   m->p = *p;
   cudaGetDevice(&m->device);
+  cudaDeviceGetAttribute(&m->sms, cudaDevAttrMultiProcessorCount, m->device);
   for (int a = 0; a < 3; ++a) {
     m->dev.lo[a] = p->box_min[a];
     m->dev.inv[a] = 1.0f / (p->box_max[a] - p->box_min[a]);
@@ -627,6 +874,9 @@ int pps_mlp_create(pps_mlp** out, const pps_mlp_params* p, const float* init_hos
   if (e == cudaSuccess) e = cudaMalloc(&m->dev.grad, P * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc(&m->dev.wb, pps::mlp::kWb * sizeof(__nv_bfloat16));
   if (e == cudaSuccess) e = cudaMalloc(&m->dev.idx, p->batch * sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaMalloc(&m->dev.err, sizeof(unsigned int));
+  if (e == cudaSuccess) e = cudaMalloc(&m->counter, sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMemset(m->dev.err, 0, sizeof(unsigned int));
   if (e == cudaSuccess) e = cudaMemset(m->dev.m, 0, P * sizeof(float));
   if (e == cudaSuccess) e = cudaMemset(m->dev.v, 0, P * sizeof(float));
   if (e == cudaSuccess) e = cudaMemset(m->dev.grad, 0, P * sizeof(float));
@@ -648,7 +898,9 @@ int pps_mlp_create(pps_mlp** out, const pps_mlp_params* p, const float* init_hos
   if (e == cudaSuccess) e = cudaMemcpy(m->dev.master, w.data(), P * sizeof(float), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) {
     if (cudaFuncSetAttribute(pps::mlp::k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             static_cast<int>(grad_smem())) != cudaSuccess)
+                             static_cast<int>(grad_smem())) != cudaSuccess ||
+        cudaFuncSetAttribute(pps::mlp::k_mlp_infer_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(pps::mlp::tc::kSmemBytes)) != cudaSuccess)
       e = cudaGetLastError();
   }
   if (e == cudaSuccess && refresh_bf16(m, nullptr) != PPS_OK) e = cudaErrorUnknown;
@@ -660,6 +912,8 @@ int pps_mlp_create(pps_mlp** out, const pps_mlp_params* p, const float* init_hos
     cudaFree(m->dev.grad);
     cudaFree(m->dev.wb);
     cudaFree(m->dev.idx);
+    cudaFree(m->dev.err);
+    cudaFree(m->counter);
     delete m;
     cudaGetLastError();
     return mfail(e == cudaErrorMemoryAllocation ? PPS_ENOMEM : PPS_ECUDA,
@@ -679,6 +933,9 @@ int pps_mlp_destroy(pps_mlp* m) {
   cudaFree(m->dev.grad);
   cudaFree(m->dev.wb);
   cudaFree(m->dev.idx);
+  cudaFree(m->dev.err);
+  cudaFree(m->counter);
+  cudaFree(m->list);
   delete m;
   return PPS_OK;
 }
@@ -704,6 +961,9 @@ int pps_mlp_get_weights(pps_mlp* m, float* host, size_t count) {
     return mfail(PPS_EINVAL, "weights: need exactly 13699 floats");
   MLP_CUDA(cudaDeviceSynchronize());
   MLP_CUDA(cudaMemcpy(host, m->dev.master, count * sizeof(float), cudaMemcpyDeviceToHost));
+  unsigned int err = 0;
+  MLP_CUDA(cudaMemcpy(&err, m->dev.err, sizeof(err), cudaMemcpyDeviceToHost));
+  if (err) return mfail(PPS_EDEVICE, "an inference launch gave up waiting for the tensor cores");
   return PPS_OK;
 }
 
@@ -753,13 +1013,26 @@ int pps_mlp_train(pps_mlp* m, const pps_vertices* v, size_t n, const pps_output*
 static int launch_infer(pps_mlp* m, const pps_vertices* v, size_t n, const pps::OutPtrs& o, int all,
                         cudaStream_t st) {
   if (n == 0) return PPS_OK;
-  int sms = 0, dev = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const size_t warps_needed = (n + 511) / 512;
-  const int grid = static_cast<int>(std::min<size_t>(static_cast<size_t>(sms) * 4,
-                                                     std::max<size_t>(1, (warps_needed + 7) / 8)));
-  pps::mlp::k_mlp_infer<<<grid, 256, 0, st>>>(m->dev, vptrs(v), n, o, m->p.infer_max_count, all);
+  if (n >= (1ull << 31)) return mfail(PPS_EINVAL, "n too large");
+  if (m->list_cap < n) {
+    cudaFree(m->list);
+    m->list = nullptr;
+    m->list_cap = 0;
+    if (cudaMalloc(&m->list, n * sizeof(int32_t)) != cudaSuccess) {
+      cudaGetLastError();
+      return mfail(PPS_ENOMEM, "inference list allocation failed");
+    }
+    m->list_cap = n;
+  }
+  const int sms = m->sms;
+  MLP_CUDA(cudaMemsetAsync(m->counter, 0, sizeof(uint32_t), st));
+  const int cgrid = static_cast<int>((n + 256 * pps::mlp::kCompactPer - 1) / (256 * pps::mlp::kCompactPer));
+  pps::mlp::k_mlp_compact<<<cgrid, 256, 0, st>>>(n, o.status, o.count, m->p.infer_max_count, all,
+                                                 m->list, m->counter);
+  MLP_CUDA(cudaGetLastError());
+  const int grid = static_cast<int>(std::min<size_t>(static_cast<size_t>(sms) * 4, (n + 127) / 128));
+  pps::mlp::k_mlp_infer_tc<<<grid, 128, pps::mlp::tc::kSmemBytes, st>>>(m->dev, vptrs(v), m->list,
+                                                                        m->counter, o, all);
   MLP_CUDA(cudaGetLastError());
   return PPS_OK;
 }
