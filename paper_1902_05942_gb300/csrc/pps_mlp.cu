@@ -433,15 +433,19 @@ __global__ void __launch_bounds__(128) k_mlp_infer_tc(Dev d, VertexPtrs v, const
   tc::Smem& s = *reinterpret_cast<tc::Smem*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~static_cast<uintptr_t>(127));
   const int tid = threadIdx.x, warp = tid >> 5;
-  // weights in the canonical layout, biases
-  for (int i = tid; i < 64 * kIn; i += blockDim.x)
-    *reinterpret_cast<__nv_bfloat16*>(s.w1 + tc::cm(i / kIn, i % kIn, kIn)) = d.wb[bW1 + i];
-  for (int i = tid; i < 64 * kHid; i += blockDim.x) {
-    *reinterpret_cast<__nv_bfloat16*>(s.w2 + tc::cm(i / kHid, i % kHid, kHid)) = d.wb[bW2 + i];
-    *reinterpret_cast<__nv_bfloat16*>(s.w3 + tc::cm(i / kHid, i % kHid, kHid)) = d.wb[bW3 + i];
+  // weights in the canonical layout, 8 elements (one 16-byte chunk of a core
+  // matrix row) per load, biases
+  const uint4* wb4 = reinterpret_cast<const uint4*>(d.wb);
+#pragma unroll 5
+  for (int c = tid; c < 64 * kIn / 8; c += blockDim.x)
+    tc::st16(s.w1, tc::cm(c / 10, 8 * (c % 10), kIn), __ldg(wb4 + bW1 / 8 + c));
+#pragma unroll 4
+  for (int c = tid; c < 64 * kHid / 8; c += blockDim.x) {
+    tc::st16(s.w2, tc::cm(c / 8, 8 * (c % 8), kHid), __ldg(wb4 + bW2 / 8 + c));
+    tc::st16(s.w3, tc::cm(c / 8, 8 * (c % 8), kHid), __ldg(wb4 + bW3 / 8 + c));
   }
-  for (int i = tid; i < 16 * kHid; i += blockDim.x)
-    *reinterpret_cast<__nv_bfloat16*>(s.w4 + tc::cm(i / kHid, i % kHid, kHid)) = d.wb[bW4 + i];
+  for (int c = tid; c < 16 * kHid / 8; c += blockDim.x)
+    tc::st16(s.w4, tc::cm(c / 8, 8 * (c % 8), kHid), __ldg(wb4 + bW4 / 8 + c));
   for (int i = tid; i < 3 * 64 + 16; i += blockDim.x) {
     float b = 0.f;
     if (i < 64) b = d.master[oB1 + i];

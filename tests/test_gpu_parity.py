@@ -163,6 +163,33 @@ def test_fused_filter_matches_oracle(fixed, batch):
     tab.close()
 
 
+def test_results_do_not_depend_on_placement():
+    """Fixed point, so bit for bit: the table size, the probe limit, the hash
+    seeds and the order of the vertices (ids kept) change where cells live in
+    the table, not what any vertex receives."""
+    spec, cfg = _small(width=128, height=96, bounces=2, accum_fixed=True)
+    v = _gen(spec, 4)
+    n = v["px"].numel()
+    ref = pps.Table(cfg).filter(_dev(v), spec.view.eye, 4)
+    perm = torch.from_numpy(np.random.default_rng(8).permutation(n))
+    ids = perm.to(torch.int32).cuda()
+    for change in ({"log2_slots": 17}, {"log2_slots": 20, "max_probes": 64},
+                   {"hash_seed_home": 12345, "hash_seed_fp": 777}, {"permute": True}):
+        _, c2 = _small(width=128, height=96, bounces=2, accum_fixed=True,
+                       **{k: x for k, x in change.items() if k != "permute"})
+        tab = pps.Table(c2)
+        if "permute" in change:
+            vp = {k: t[perm] for k, t in v.items()}
+            out = tab.filter(_dev(vp), spec.view.eye, 4, ids=ids)
+            inv = torch.argsort(perm)
+            out = {k: t.cpu()[inv] for k, t in out.items()}
+        else:
+            out = {k: t.cpu() for k, t in tab.filter(_dev(v), spec.view.eye, 4).items()}
+        for c in ("r", "g", "b", "count", "status"):
+            assert torch.equal(out[c], ref[c].cpu()), (change, c)
+        tab.close()
+
+
 @pytest.mark.parametrize("fixed", [False, True])
 def test_split_path_matches_oracle_and_audit(fixed):
     spec, cfg = _small(width=160, height=120, bounces=2, accum_fixed=fixed)

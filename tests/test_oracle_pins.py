@@ -381,3 +381,19 @@ def test_linear_probing_mean_probes_match_knuth():
         want = 0.5 * (1 + 1 / (1 - a))
         assert abs(probes.mean() - want) < 0.05 * want
         assert np.all(slot >= 0) and (table != 0).sum() == m
+
+
+def test_fingerprint_collisions_follow_the_birthday_bound():
+    """hash2 behaves like a random 32-bit function on distinct key tuples:
+    among m distinct keys the number of colliding pairs has mean
+    m (m - 1) / 2 / 2^32 (Poisson), here 116.4 for m = 10^6."""
+    rng = np.random.default_rng(23)
+    m = 1_000_000
+    words = rng.integers(0, 2 ** 32, size=(4, 3 * m // 2), dtype=np.uint64).astype(np.uint32)
+    t = np.unique(words.T, axis=0)[:m].T  # distinct 4-word keys
+    assert t.shape[1] == m
+    f = O.murmur3_32([t[0], t[1], t[2], t[3]], 0x2F0F1D3B)
+    _, c = np.unique(f, return_counts=True)
+    pairs = int((c * (c - 1) // 2).sum())
+    mean = m * (m - 1) / 2 / 2 ** 32
+    assert abs(pairs - mean) < 5 * np.sqrt(mean), (pairs, mean)
