@@ -315,6 +315,8 @@ def run_ours(args):
         if not args.no_batched:
             del frames
             line["batched"] = batched_leg()
+        if not args.no_stress:
+            line["stress"] = stress_leg()
         print(json.dumps(line), flush=True)
     tab.close()
     if ws > 1:
@@ -541,6 +543,60 @@ def batched_leg(steps_timed=8, tune=True):
             "batch_width": width, "batch_width_trials_ms": wt, "views": tuned}
 
 
+def stress_leg(steps_timed=6):
+    """The stress workload: 3840x2160 at 2 paths per pixel, 6 bounces (~61 M
+    vertices per frame, 80 % of them squeezed into 5 % of the scene box),
+    table 2^26 slots at load ~0.7, FP16 history of 2^28 cells with a temporal
+    blend, and the learned fallback (training + inference) every frame.  Two
+    frames are generated on the GPU and alternate; times per frame with CUDA
+    events: the filter alone and the whole frame."""
+    import torch
+    from paper_1902_05942_gb300 import configs, pps, scene
+    w = configs.stress()
+    cfg = w.filters[0]
+    frames = []
+    for f in range(2):
+        spec = configs.frame_spec(w, 0, f)
+        v = scene.trace_stream(spec, f, "cuda")
+        frames.append(({k: v[k] for k in scene.STREAMS}, tuple(spec.view.eye)))
+        del v
+    torch.cuda.synchronize()
+    n = frames[0][0]["px"].numel()
+    tab = pps.Table(cfg)
+    net = pps.MLP(pps.mlp_params())
+    out = pps.empty_output(max(fr[0]["px"].numel() for fr in frames), "cuda")
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    t_f = t_all = 0.0
+    nv = 0
+    for i in range(2 + steps_timed):
+        v, eye = frames[i % 2]
+        m = v["px"].numel()
+        o = {k: t[:m] for k, t in out.items()}
+        ev[0].record()
+        tab.filter(v, eye, i, blend=True, alpha=cfg.alpha, out=o)
+        ev[1].record()
+        net.train(v, o, i)
+        net.infer(v, o)
+        ev[2].record()
+        torch.cuda.synchronize()
+        if i >= 2:
+            t_f += ev[0].elapsed_time(ev[1])
+            t_all += ev[0].elapsed_time(ev[2])
+            nv += m
+    st = tab.stats()
+    tab.close()
+    net.close()
+    del frames, out
+    torch.cuda.empty_cache()
+    k = steps_timed
+    return {"workload": "3840x2160 x2 paths x6 bounces, 80% of vertices in 5% of the box, "
+                        "T=2^26, P=16, FP16 history 2^28, alpha=0.2, learned fallback",
+            "vertices_per_frame": nv / k, "ms_filter": t_f / k, "ms_frame_with_mlp": t_all / k,
+            "filter_vertices_per_s": nv / (t_f * 1e-3),
+            "overflow_vertices_last_frame": st["overflow_vertices"],
+            "frame_cells_last_frame": st["frame_cells"]}
+
+
 def _oracle_step(v_np, w, frame, eye, hist):
     from oracle import pps_oracle as O
     cfg = w.filters[0]
@@ -670,6 +726,7 @@ def main():
     ap.add_argument("--no-mlp", action="store_true", help="skip the learned-fallback leg")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-views leg")
     ap.add_argument("--no-fallbacks", action="store_true", help="skip the low-count fallback legs")
+    ap.add_argument("--no-stress", action="store_true", help="skip the stress-workload leg")
     ap.add_argument("--ncu-case", action="store_true", help="small fixed case for profilers")
     ap.add_argument("--rates", action="store_true", help="random memory-operation rates")
     ap.add_argument("--hist", type=int, default=1, help="--ncu-case: history mode")

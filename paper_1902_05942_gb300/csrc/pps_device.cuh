@@ -395,14 +395,20 @@ __device__ __forceinline__ uint32_t probe_rest(const TableDev& t, uint32_t home,
   return kOverflowSlot;
 }
 
-// Read-only lookup of a key's cell id (query without a stored id).
-__device__ __forceinline__ uint32_t probe_find(const TableDev& t, uint32_t home, uint32_t f) {
-  for (uint32_t p = 0; p < t.max_probes; ++p) {
+// Read-only lookup of a key's cell id (query without a stored id), from
+// probe step p0 on.
+__device__ __forceinline__ uint32_t probe_find_from(const TableDev& t, uint32_t home, uint32_t f,
+                                                    uint32_t p0) {
+  for (uint32_t p = p0; p < t.max_probes; ++p) {
     const unsigned long long w = __ldcg(t.slots + ((home + p) & t.mask));
     if (w == 0ull) return kOverflowSlot;
     if (slot_fp(w) == f) return slot_id(w);
   }
   return kOverflowSlot;
+}
+
+__device__ __forceinline__ uint32_t probe_find(const TableDev& t, uint32_t home, uint32_t f) {
+  return probe_find_from(t, home, f, 0u);
 }
 
 // History table probing: 32-bit compare-and-swap on the history fingerprint.

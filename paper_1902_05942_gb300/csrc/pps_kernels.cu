@@ -298,34 +298,59 @@ __device__ __noinline__ Result neighbor_pool(const KeyConst& kc, const TableDev&
   float sr = 0.f, sg = 0.f, sb = 0.f;
   long long fr = 0, fg = 0, fb = 0;
   unsigned long long n = 0;
-  for (int o = 0; o < 27; ++o) {
-    KeyWords w = w0;
-    w.X += static_cast<uint32_t>(o / 9 - 1);
-    w.Y += static_cast<uint32_t>(o / 3 % 3 - 1);
-    w.Z += static_cast<uint32_t>(o % 3 - 1);
-    const Key k = key_hash(kc, w);
-    const uint32_t id = probe_find(t, k.h1 & t.mask, k.fp);
-    if (id == kOverflowSlot) continue;
-    if (blended) {
-      const float4 c = __ldcg(value_ptr(t, id));
-      const uint32_t N = __float_as_uint(c.w);
-      const float fN = __uint2float_rn(N);
-      sr = __fadd_rn(sr, __fmul_rn(fN, c.x));
-      sg = __fadd_rn(sg, __fmul_rn(fN, c.y));
-      sb = __fadd_rn(sb, __fmul_rn(fN, c.z));
-      n += N;
-    } else if (!t.fixed) {
-      const float4 a = __ldcg(t.acc + id);
-      sr = __fadd_rn(sr, a.x);
-      sg = __fadd_rn(sg, a.y);
-      sb = __fadd_rn(sb, a.z);
-      n += static_cast<unsigned long long>(a.w);
-    } else {
-      const unsigned long long* a = t.acc64 + 4 * static_cast<size_t>(id);
-      fr += static_cast<long long>(__ldcg(a + 0));
-      fg += static_cast<long long>(__ldcg(a + 1));
-      fb += static_cast<long long>(__ldcg(a + 2));
-      n += __ldcg(a + 3);
+  // three cells (dz = -1, 0, +1) at a time: their first probes, then their
+  // values, each as loads in flight together
+#pragma unroll 1
+  for (int o3 = 0; o3 < 9; ++o3) {
+    uint32_t home[3], fp[3], id[3];
+    unsigned long long w[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      KeyWords kw = w0;
+      kw.X += static_cast<uint32_t>(o3 / 3 - 1);
+      kw.Y += static_cast<uint32_t>(o3 % 3 - 1);
+      kw.Z += static_cast<uint32_t>(q - 1);
+      const Key k = key_hash(kc, kw);
+      home[q] = k.h1 & t.mask;
+      fp[q] = k.fp;
+    }
+#pragma unroll
+    for (int q = 0; q < 3; ++q) w[q] = __ldcg(t.slots + home[q]);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      if (w[q] == 0ull)
+        id[q] = kOverflowSlot;
+      else if (slot_fp(w[q]) == fp[q])
+        id[q] = slot_id(w[q]);
+      else  // the home slot holds another key: the rest of the probe sequence
+        id[q] = probe_find_from(t, home[q], fp[q], 1u);
+    }
+    float4 c[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q)
+      if (id[q] != kOverflowSlot && !(t.fixed && !blended)) c[q] = __ldcg(value_ptr(t, id[q]));
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      if (id[q] == kOverflowSlot) continue;
+      if (blended) {
+        const uint32_t N = __float_as_uint(c[q].w);
+        const float fN = __uint2float_rn(N);
+        sr = __fadd_rn(sr, __fmul_rn(fN, c[q].x));
+        sg = __fadd_rn(sg, __fmul_rn(fN, c[q].y));
+        sb = __fadd_rn(sb, __fmul_rn(fN, c[q].z));
+        n += N;
+      } else if (!t.fixed) {
+        sr = __fadd_rn(sr, c[q].x);
+        sg = __fadd_rn(sg, c[q].y);
+        sb = __fadd_rn(sb, c[q].z);
+        n += static_cast<unsigned long long>(c[q].w);
+      } else {
+        const unsigned long long* a = t.acc64 + 4 * static_cast<size_t>(id[q]);
+        fr += static_cast<long long>(__ldcg(a + 0));
+        fg += static_cast<long long>(__ldcg(a + 1));
+        fb += static_cast<long long>(__ldcg(a + 2));
+        n += __ldcg(a + 3);
+      }
     }
   }
   if (n == 0) return own;  // the own cell is always found; kept as a guard
@@ -354,6 +379,20 @@ __device__ __forceinline__ void neighbors_of_vertex(const KeyConst& kc, const Ta
   const CellMean m = value_of(t, load_value(t, id, blended), blended);
   if (m.n >= t.lowcount) return;
   const Result r = neighbor_pool(kc, t, v, j, blended, Result{m.r, m.g, m.b, m.n, 1});
+  o.r[j] = r.r;
+  o.g[j] = r.g;
+  o.b[j] = r.b;
+  if (o.count) o.count[j] = r.n;
+  if (o.status) o.status[j] = r.status;
+}
+
+// A queued low-count vertex j: its neighborhood-search result into the
+// outputs.  The vertex's own cell is among the 27, so the pooled count is at
+// least its own.
+__device__ __forceinline__ void neighbors_of_queued(const KeyConst& kc, const TableDev& t,
+                                                    const VertexPtrs& v, const OutPtrs& o,
+                                                    uint32_t j, bool blended) {
+  const Result r = neighbor_pool(kc, t, v, j, blended, Result{o.r[j], o.g[j], o.b[j], 0u, 1});
   o.r[j] = r.r;
   o.g[j] = r.g;
   o.b[j] = r.b;
@@ -776,14 +815,40 @@ __global__ void __launch_bounds__(kFusedBlock, W == 4 ? 1 : 2) k_fused(FusedArgs
   // Neighborhood search for this CTA's low-count vertices (the table is only
   // read from phase C on, so no barrier is needed before it).  A separate
   // kernel variant, so that the plain one carries no call.
+  // Low-count vertices are rare and scattered, so each warp first collects
+  // them in a queue of its own and runs the search 32 at a time, one per lane.
   if constexpr (NEIGH) {
+    __shared__ uint32_t s_nq[kFusedBlock / 32][64];
+    const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
+    uint32_t qn = 0;
     for (uint32_t k = 0; k < taken; ++k) {
       const size_t t0 = static_cast<size_t>(s_tile[k]) * kFusedTile;
       const size_t end = min(a.n, t0 + kFusedTile);
       const uint32_t* stash = a.gstash ? a.gstash + t0 : s_stash + static_cast<size_t>(k) * kFusedTile;
-      for (size_t j = t0 + threadIdx.x; j < end; j += blockDim.x)
-        neighbors_of_vertex(a.kc, t, a.v, a.o, j, stash[j - t0], blended);
+      for (size_t base = t0 + (threadIdx.x & ~31u); base < end; base += blockDim.x) {
+        const size_t j = base + lane;
+        bool low = false;
+        if (j < end) {
+          const uint32_t id = stash[j - t0];
+          low = id != kOverflowSlot &&
+                value_of(t, load_value(t, id, blended), blended).n < t.lowcount;
+        }
+        const unsigned mask = __ballot_sync(0xFFFFFFFFu, low);
+        if (low) s_nq[wq][qn + __popc(mask & ((1u << lane) - 1u))] = static_cast<uint32_t>(j);
+        qn += __popc(mask);
+        __syncwarp();
+        if (qn >= 32) {
+          neighbors_of_queued(a.kc, t, a.v, a.o, s_nq[wq][lane], blended);
+          __syncwarp();
+          const uint32_t moved = lane + 32 < qn ? s_nq[wq][lane + 32] : 0u;
+          __syncwarp();
+          if (lane + 32 < qn) s_nq[wq][lane] = moved;
+          qn -= 32;
+          __syncwarp();
+        }
+      }
     }
+    if (lane < qn) neighbors_of_queued(a.kc, t, a.v, a.o, s_nq[wq][lane], blended);
   }
   if (!grid_barrier(t.ctrl, gridDim.x)) return;
 
@@ -1147,12 +1212,15 @@ cudaError_t plan_fused(size_t n, bool temporal, int batch, FusedPlan* plan, bool
   for (int b = b0; b >= 1; --b) {
     // shared memory per CTA when b CTAs share an SM (static part and a reserve deducted)
     const size_t per = std::min(maxdyn, static_cast<size_t>(smem_sm) / b - 12 * 1024);
-    const size_t cap = std::min<size_t>(per / tile_bytes, kMaxTilesPerCta);
-    if (cap == 0 || cap * static_cast<size_t>(sms) * b < ntiles) continue;
-    // keep some headroom so that fast CTAs can take extra tiles
+    size_t cap = std::min<size_t>(per / tile_bytes, kMaxTilesPerCta);
+    // the largest stash with which b CTAs still fit on an SM
     int nb = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, kFusedBlock, cap * tile_bytes);
-    if (e != cudaSuccess) return e;
+    for (; cap > 0; --cap) {
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, kFusedBlock, cap * tile_bytes);
+      if (e != cudaSuccess) return e;
+      if (nb >= b) break;
+    }
+    if (cap == 0 || cap * static_cast<size_t>(sms) * b < ntiles) continue;
     if (nb >= b) {
       plan->grid = sms * b;
       plan->cap_tiles = static_cast<uint32_t>(cap);
