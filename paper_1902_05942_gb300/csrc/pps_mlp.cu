@@ -5,14 +5,15 @@
 // Network: input 80 = per axis sin/cos(pi 2^k p), k = 0..11, of the position
 // normalized to a box (72), the normal (3), 5 zeros; three hidden layers of
 // 64 with ReLU; linear RGB output.  BF16 weights and activations, FP32
-// accumulation, on the tensor cores with mma.sync.m16n8k16 (operands staged in
-// shared memory and loaded with ldmatrix).  A warp handles 16 samples: the
-// FP32 result fragment of one layer, after bias, ReLU and BF16 packing, is
-// directly the A fragment of the next layer, so activations never leave
-// registers in inference.  Training: a CTA of 8 warps takes 128 samples;
-// forward and delta chains run per warp, the weight gradients X^T dZ are
-// CTA-level products over the 128 samples, reduced into an FP32 gradient with
-// atomics; Adam updates FP32 master weights and refreshes the BF16 copies.
+// accumulation, on the fifth-generation tensor cores: tcgen05.mma from
+// shared-memory tiles in the canonical K-major layout into tensor memory,
+// tcgen05.ld back to registers for the bias / ReLU / rounding epilogues.
+// Inference: a CTA of 128 threads evaluates 128 vertices per tile.
+// Training: a CTA of 128 threads takes 128 samples through the forward pass,
+// the delta chain and the weight gradients X^T dZ (products over the samples,
+// from transposed tiles the epilogues write), reduced into an FP32 gradient
+// with atomics; Adam updates FP32 master weights and refreshes the BF16
+// copies.
 //
 // Parameter vector (FP32, this order): W1 [64][80], b1 [64], W2 [64][64], b2,
 // W3 [64][64], b3, W4 [3][64], b4 [3]  (W as [out][in]).
@@ -39,10 +40,7 @@ constexpr int oW1 = 0, oB1 = 5120, oW2 = 5184, oB2 = 9280, oW3 = 9344, oB3 = 134
 // (rows 3..15 of W4 zero, so the output layer is one 8-wide and the first
 // backward product one 16-deep tile).
 constexpr int bW1 = 0, bW2 = 5120, bW3 = 9216, bW4 = 13312, kWb = 14336;
-// shared-memory row strides (BF16 elements), padded so ldmatrix rows fall in
-// different banks
-constexpr int sIn = 88, sHid = 72, sDy = 24;
-constexpr int kWarps = 8, kThreads = kWarps * 32, kSamples = kWarps * 16;  // training CTA
+constexpr int kSamples = 128;  // training samples per CTA (the MMA's M)
 
 struct Dev {
   float* master;  // [kP]
@@ -60,46 +58,12 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
-__device__ __forceinline__ void ldsm_x2(uint32_t& r0, uint32_t& r1, const void* p) {
-  asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0, %1}, [%2];"
-               : "=r"(r0), "=r"(r1)
-               : "r"(smem_u32(p)));
-}
-__device__ __forceinline__ void ldsm_x2_t(uint32_t& r0, uint32_t& r1, const void* p) {
-  asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0, %1}, [%2];"
-               : "=r"(r0), "=r"(r1)
-               : "r"(smem_u32(p)));
-}
-__device__ __forceinline__ void ldsm_x4_t(uint32_t (&r)[4], const void* p) {
-  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0, %1, %2, %3}, [%4];"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-               : "r"(smem_u32(p)));
-}
-
-// D = A (16x16 bf16, row) * B (16x8 bf16, col) + D, FP32 accumulate.
-__device__ __forceinline__ void mma(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, "
-      "{%8, %9}, {%0, %1, %2, %3};"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-
 __device__ __forceinline__ uint32_t pack2(float x, float y) {
   const __nv_bfloat162 h = __floats2bfloat162_rn(x, y);  // x in the low half
   return *reinterpret_cast<const uint32_t*>(&h);
 }
 __device__ __forceinline__ float lo_f(uint32_t w) { return __uint_as_float(w << 16); }
 __device__ __forceinline__ float hi_f(uint32_t w) { return __uint_as_float(w & 0xFFFF0000u); }
-
-// ---------------------------------------------------------------- encoding
-// In the A-fragment layout of mma.m16n8k16 a lane with t = lane & 3 holds the
-// input columns c = 8 i + 2 t (i = 0..9) of its two rows.  For i < 9 that is
-// the (sin, cos) pair of axis i / 3 at frequency k = 4 (i % 3) + t; column
-// 72 + 2t is (n_x, n_y), (n_z, 0) or padding.
-__device__ __forceinline__ float2 enc_normal(int t, const float (&nr)[3]) {
-  return t == 0 ? make_float2(nr[0], nr[1]) : t == 1 ? make_float2(nr[2], 0.f) : make_float2(0.f, 0.f);
-}
 
 struct VertexIn {
   float pn[3], nr[3];
@@ -119,117 +83,6 @@ __device__ __forceinline__ VertexIn load_vertex(const Dev& d, const VertexPtrs& 
   o.nr[1] = __ldg(v.ny + j);
   o.nr[2] = __ldg(v.nz + j);
   return o;
-}
-
-// A fragments of the encoded input for this lane's rows g (va) and g + 8 (vb).
-__device__ __forceinline__ void encode_frag(uint32_t (&a)[5][4], const VertexIn& va,
-                                            const VertexIn& vb, int t) {
-#pragma unroll
-  for (int kk = 0; kk < 5; ++kk) {
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int i = 2 * kk + h;  // columns 8 i + 2 t, 8 i + 2 t + 1
-      float2 pa, pb;
-      if (i < 9) {
-        const float f = static_cast<float>(1 << (4 * (i % 3) + t));
-        sincospif(va.pn[i / 3] * f, &pa.x, &pa.y);
-        sincospif(vb.pn[i / 3] * f, &pb.x, &pb.y);
-      } else {
-        pa = enc_normal(t, va.nr);
-        pb = enc_normal(t, vb.nr);
-      }
-      a[kk][2 * h] = pack2(pa.x, pa.y);
-      a[kk][2 * h + 1] = pack2(pb.x, pb.y);
-    }
-  }
-}
-
-// ---------------------------------------------------------------- layers
-// C[nt] (16 x 8 tiles) = A (16 x 16 KT) * W^T + bias, W in shared memory as
-// [out][in] rows of `stride` elements (B operand, column-major K x N).
-template <int KT, int NT>
-__device__ __forceinline__ void layer_fwd(float (&c)[NT][4], const uint32_t (&a)[KT][4],
-                                          const __nv_bfloat16* W, int stride, const float* bias,
-                                          int lane) {
-  const int g = lane >> 2, t = lane & 3;
-#pragma unroll
-  for (int nt = 0; nt < NT; ++nt) {
-    const float b0 = bias ? __ldg(bias + nt * 8 + 2 * t) : 0.f;
-    const float b1 = bias ? __ldg(bias + nt * 8 + 2 * t + 1) : 0.f;
-    c[nt][0] = b0;
-    c[nt][1] = b1;
-    c[nt][2] = b0;
-    c[nt][3] = b1;
-    (void)g;
-#pragma unroll
-    for (int kt = 0; kt < KT; ++kt) {
-      uint32_t w0, w1;
-      ldsm_x2(w0, w1, W + (nt * 8 + (lane & 7)) * stride + kt * 16 + ((lane >> 3) & 1) * 8);
-      mma(c[nt], a[kt], w0, w1);
-    }
-  }
-}
-
-// ReLU and BF16 packing: the result tiles become the next layer's A fragments.
-template <int NT>
-__device__ __forceinline__ void relu_pack(uint32_t (&a)[NT / 2][4], const float (&c)[NT][4]) {
-#pragma unroll
-  for (int k = 0; k < NT / 2; ++k) {
-    a[k][0] = pack2(fmaxf(c[2 * k][0], 0.f), fmaxf(c[2 * k][1], 0.f));
-    a[k][1] = pack2(fmaxf(c[2 * k][2], 0.f), fmaxf(c[2 * k][3], 0.f));
-    a[k][2] = pack2(fmaxf(c[2 * k + 1][0], 0.f), fmaxf(c[2 * k + 1][1], 0.f));
-    a[k][3] = pack2(fmaxf(c[2 * k + 1][2], 0.f), fmaxf(c[2 * k + 1][3], 0.f));
-  }
-}
-
-// Shared-memory copy of the BF16 weights with padded rows.
-struct SmemW {
-  __nv_bfloat16 w1[64 * sIn];
-  __nv_bfloat16 w2[64 * sHid];
-  __nv_bfloat16 w3[64 * sHid];
-  __nv_bfloat16 w4[16 * sHid];
-};
-
-__device__ __forceinline__ void load_weights(SmemW& s, const __nv_bfloat16* wb) {
-  for (int i = threadIdx.x; i < 64 * kIn; i += blockDim.x) s.w1[(i / kIn) * sIn + i % kIn] = wb[bW1 + i];
-  for (int i = threadIdx.x; i < 64 * kHid; i += blockDim.x) {
-    s.w2[(i / kHid) * sHid + i % kHid] = wb[bW2 + i];
-    s.w3[(i / kHid) * sHid + i % kHid] = wb[bW3 + i];
-  }
-  for (int i = threadIdx.x; i < 16 * kHid; i += blockDim.x) s.w4[(i / kHid) * sHid + i % kHid] = wb[bW4 + i];
-}
-
-// Forward of 16 vertices held by one warp; returns the output tile (cols 0..7,
-// 0..2 meaningful) and optionally keeps the hidden activations as A fragments.
-struct Hidden {
-  uint32_t h1[4][4], h2[4][4], h3[4][4];
-};
-
-__device__ __forceinline__ void forward16(float (&y)[1][4], Hidden& h, const uint32_t (&x0)[5][4],
-                                          const SmemW& s, const float* master, int lane) {
-  float c[8][4];
-  layer_fwd<5, 8>(c, x0, s.w1, sIn, master + oB1, lane);
-  relu_pack<8>(h.h1, c);
-  layer_fwd<4, 8>(c, h.h1, s.w2, sHid, master + oB2, lane);
-  relu_pack<8>(h.h2, c);
-  layer_fwd<4, 8>(c, h.h2, s.w3, sHid, master + oB3, lane);
-  relu_pack<8>(h.h3, c);
-  // output layer: W4 rows 0..7 (3..7 zero); bias only on columns 0..2
-  const int t = lane & 3;
-#pragma unroll
-  for (int i = 0; i < 4; ++i) y[0][i] = 0.f;
-#pragma unroll
-  for (int kt = 0; kt < 4; ++kt) {
-    uint32_t w0, w1;
-    ldsm_x2(w0, w1, s.w4 + (lane & 7) * sHid + kt * 16 + ((lane >> 3) & 1) * 8);
-    mma(y[0], h.h3[kt], w0, w1);
-  }
-  const float b0 = 2 * t < kOut ? __ldg(master + oB4 + 2 * t) : 0.f;
-  const float b1 = 2 * t + 1 < kOut ? __ldg(master + oB4 + 2 * t + 1) : 0.f;
-  y[0][0] += b0;
-  y[0][1] += b1;
-  y[0][2] += b0;
-  y[0][3] += b1;
 }
 
 // ---------------------------------------------------------------- inference
@@ -577,189 +430,283 @@ __global__ void k_mlp_select(const uint32_t* count, size_t n, uint32_t seed, uin
   idx[i] = pick;
 }
 
-struct SmemTrain {
-  SmemW w;
-  __nv_bfloat16 x0[kSamples * sIn];
-  __nv_bfloat16 h1[kSamples * sHid], h2[kSamples * sHid], h3[kSamples * sHid];
-  __nv_bfloat16 z1[kSamples * sHid], z2[kSamples * sHid], z3[kSamples * sHid];
-  __nv_bfloat16 dy[kSamples * sDy];
+// ---------------------------------------------------------------- training on tcgen05
+// One CTA of 128 threads takes 128 samples (the MMA's M).  Every operand is a
+// K-major BF16 tile in the canonical no-swizzle layout, so the products that
+// run over the samples read transposed copies that the epilogues write beside
+// the row-per-sample tiles:
+//   forward   Z_l = X_l W_l^T        A = X_l   [sample][in],  B = W_l   [out][in]
+//   backward  dH_l = dZ_{l+1} W_{l+1} A = dZ    [sample][out], B = W^T   [in][out]
+//   gradient  gW_l^T = X_l^T dZ_l    A = X_l^T [in][sample],  B = dZ^T  [out][sample]
+// (M = 128 rows for the gradients: rows past the layer's inputs read the next
+// tile and are ignored).  Deltas are rounded to BF16 where the oracle rounds
+// them; weight and bias gradients are summed over the CTA's samples in FP32
+// and added to the gradient with atomics.
+namespace tct {
+constexpr uint32_t kTmemCols = 512;  // [0, 64): layer products, then the four gradients
+
+struct Smem {
+  alignas(128) unsigned char act[128 * 80 * 2];  // X0, then H1..H3 [sample][feature]
+  alignas(128) unsigned char xt0[80 * 128 * 2];  // X0^T [feature][sample]
+  alignas(128) unsigned char ht[3][64 * 128 * 2];  // H1^T..H3^T
+  alignas(128) unsigned char dz[128 * 64 * 2];   // dY (K = 16), then dZ3, dZ2 [sample][out]
+  alignas(128) unsigned char dzt[3][64 * 128 * 2];  // dZ1^T..dZ3^T [out][sample]
+  alignas(128) unsigned char dyt[16 * 128 * 2];  // dY^T [out][sample]
+  alignas(128) unsigned char w1[64 * 80 * 2];    // W_l [out][in]
+  alignas(128) unsigned char w2[64 * 64 * 2];
+  alignas(128) unsigned char w3[64 * 64 * 2];
+  alignas(128) unsigned char w4[16 * 64 * 2];
+  alignas(128) unsigned char wt2[64 * 64 * 2];   // W_l^T [in][out]
+  alignas(128) unsigned char wt3[64 * 64 * 2];
+  alignas(128) unsigned char wt4[64 * 16 * 2];
+  float bias[3 * 64 + 16];
+  alignas(8) unsigned long long mbar;
+  uint32_t tmem;
 };
+constexpr size_t kSmemBytes = sizeof(Smem) + 128;
 
-__device__ __forceinline__ void put2(__nv_bfloat16* base, int row, int col, int stride, uint32_t w) {
-  *reinterpret_cast<uint32_t*>(base + row * stride + col) = w;
+__device__ __forceinline__ void st_b16(unsigned char* base, uint32_t off, float x) {
+  *reinterpret_cast<__nv_bfloat16*>(base + off) = __float2bfloat16_rn(x);
+}
+__device__ __forceinline__ float ld_b16(const unsigned char* base, uint32_t off) {
+  return __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(base + off));
 }
 
-// Store result-layout tiles (as packed A fragments of 16 x 16 k-tiles) to
-// shared memory rows [r0, r0 + 16).
-template <int KT>
-__device__ __forceinline__ void store_frag(__nv_bfloat16* base, int stride, int r0,
-                                           const uint32_t (&a)[KT][4], int lane) {
-  const int g = lane >> 2, t = lane & 3;
-#pragma unroll
-  for (int k = 0; k < KT; ++k) {
-    put2(base, r0 + g, 16 * k + 2 * t, stride, a[k][0]);
-    put2(base, r0 + g + 8, 16 * k + 2 * t, stride, a[k][1]);
-    put2(base, r0 + g, 16 * k + 8 + 2 * t, stride, a[k][2]);
-    put2(base, r0 + g + 8, 16 * k + 8 + 2 * t, stride, a[k][3]);
-  }
+// Issue `ksteps` MMAs of K = 16 (A and B advance two core matrices, 256 bytes,
+// per step) into tensor-memory column `dcol`; product() also commits them to
+// the mbarrier.
+__device__ __forceinline__ void issue(uint32_t tmem, uint32_t dcol, uint32_t a, uint32_t sboa,
+                                      uint32_t b, uint32_t sbob, uint32_t n, int ksteps) {
+  const uint32_t id = tc::idesc(128, n);
+  for (int k = 0; k < ksteps; ++k)
+    tc::mma_bf16(tmem + dcol, tc::sdesc(a + 256u * k, sboa), tc::sdesc(b + 256u * k, sbob), id,
+                 k > 0 ? 1u : 0u);
 }
 
-// dH (16 x 64) = dZ (16 x 16 KT) * W, W in shared memory as [out][in] rows
-// (B operand K = out, N = in: row-major K x N, loaded transposed).
-template <int KT>
-__device__ __forceinline__ void layer_bwd(float (&c)[8][4], const uint32_t (&a)[KT][4],
-                                          const __nv_bfloat16* W, int stride, int lane) {
-#pragma unroll
-  for (int nt = 0; nt < 8; ++nt) {
-    c[nt][0] = c[nt][1] = c[nt][2] = c[nt][3] = 0.f;
-#pragma unroll
-    for (int kt = 0; kt < KT; ++kt) {
-      uint32_t w0, w1;
-      ldsm_x2_t(w0, w1, W + (kt * 16 + (lane & 15)) * stride + nt * 8);
-      mma(c[nt], a[kt], w0, w1);
-    }
-  }
+__device__ __forceinline__ void product(uint32_t tmem, uint32_t dcol, uint32_t a, uint32_t sboa,
+                                        uint32_t b, uint32_t sbob, uint32_t n, int ksteps,
+                                        uint32_t mbar) {
+  issue(tmem, dcol, a, sboa, b, sbob, n, ksteps);
+  tc::commit(mbar);
 }
 
-// Mask a delta tile by (activation > 0), round to BF16 and pack as A fragments.
-__device__ __forceinline__ void mask_pack(uint32_t (&dz)[4][4], const float (&c)[8][4],
-                                          const uint32_t (&h)[4][4]) {
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    const uint32_t* hk = h[k];
-    dz[k][0] = pack2(lo_f(hk[0]) > 0.f ? c[2 * k][0] : 0.f, hi_f(hk[0]) > 0.f ? c[2 * k][1] : 0.f);
-    dz[k][1] = pack2(lo_f(hk[1]) > 0.f ? c[2 * k][2] : 0.f, hi_f(hk[1]) > 0.f ? c[2 * k][3] : 0.f);
-    dz[k][2] = pack2(lo_f(hk[2]) > 0.f ? c[2 * k + 1][0] : 0.f,
-                     hi_f(hk[2]) > 0.f ? c[2 * k + 1][1] : 0.f);
-    dz[k][3] = pack2(lo_f(hk[3]) > 0.f ? c[2 * k + 1][2] : 0.f,
-                     hi_f(hk[3]) > 0.f ? c[2 * k + 1][3] : 0.f);
-  }
-}
+// Tensor-memory columns of the weight gradient gW_l^T (layer products use
+// columns [0, 64)).
+__device__ __forceinline__ uint32_t gcol(int l) { return l == 3 ? 64u : 128u + 64u * l; }
 
-// Weight gradient tile dW[m0..m0+15][n0..n0+7] += dZ^T X over kSamples rows:
-// A = dZ^T (m = output, k = sample) and B = X (k = sample, n = input) are both
-// read transposed from their row-per-sample shared-memory layout.
-__device__ __forceinline__ void dw_tile(float (&acc)[4], const __nv_bfloat16* dz, int sdz,
-                                        const __nv_bfloat16* x, int sx, int m0, int n0, int lane) {
-  acc[0] = acc[1] = acc[2] = acc[3] = 0.f;
-#pragma unroll
-  for (int k0 = 0; k0 < kSamples; k0 += 16) {
-    uint32_t a[4];
-    ldsm_x4_t(a, dz + (k0 + (lane & 7) + ((lane >> 4) << 3)) * sdz + m0 + ((lane >> 3) & 1) * 8);
-    uint32_t b0, b1;
-    ldsm_x2_t(b0, b1, x + (k0 + (lane & 15)) * sx + n0);
-    mma(acc, a, b0, b1);
-  }
-}
-
-// One batch of samples (kSamples per CTA): forward, backward, and atomic
-// accumulation of the gradient of L = 1/(2 batch) sum (y - t)^2.
-__global__ void __launch_bounds__(kThreads, 1) k_mlp_grad(Dev d, VertexPtrs v, const float* tr,
-                                                          const float* tg, const float* tb,
-                                                          const int32_t* idx, uint32_t batch) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  SmemTrain& s = *reinterpret_cast<SmemTrain*>(smem_raw);
-  load_weights(s.w, d.wb);
-  for (int i = threadIdx.x; i < kSamples * sDy / 2; i += blockDim.x)
-    reinterpret_cast<uint32_t*>(s.dy)[i] = 0u;
+__device__ __forceinline__ void sync_tc() {
+  tc::fence_smem_async();
+  tc::fence_before();
   __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int g = lane >> 2, t = lane & 3;
-  const int r0 = warp * 16;
-  const uint32_t s0 = blockIdx.x * kSamples + r0;
-  const int64_t ja = s0 + g < batch ? idx[s0 + g] : -1;
-  const int64_t jb = s0 + g + 8 < batch ? idx[s0 + g + 8] : -1;
-  uint32_t x0[5][4];
-  encode_frag(x0, load_vertex(d, v, ja), load_vertex(d, v, jb), t);
-  store_frag<5>(s.x0, sIn, r0, x0, lane);
-  float y[1][4];
-  Hidden h;
-  forward16(y, h, x0, s.w, d.master, lane);
-  store_frag<4>(s.h1, sHid, r0, h.h1, lane);
-  store_frag<4>(s.h2, sHid, r0, h.h2, lane);
-  store_frag<4>(s.h3, sHid, r0, h.h3, lane);
-  // output delta (y - target) / batch for columns 0..2, BF16
-  const float invb = 1.0f / static_cast<float>(batch);
-  float dy[4] = {0.f, 0.f, 0.f, 0.f};
-  if (t < 2) {
-#pragma unroll
-    for (int r = 0; r < 2; ++r) {
-      const int64_t j = r ? jb : ja;
-      if (j < 0) continue;
-      const float t0 = t == 0 ? __ldg(tr + j) : __ldg(tb + j);
-      const float t1 = t == 0 ? __ldg(tg + j) : 0.f;
-      dy[2 * r] = (y[0][2 * r] - t0) * invb;
-      dy[2 * r + 1] = t == 0 ? (y[0][2 * r + 1] - t1) * invb : 0.f;
-    }
+  tc::fence_after();
+}
+}  // namespace tct
+
+__global__ void __launch_bounds__(128, 1) k_mlp_grad_tc(Dev d, VertexPtrs v, const float* tr,
+                                                        const float* tg, const float* tb,
+                                                        const int32_t* idx, uint32_t batch) {
+  extern __shared__ unsigned char smem_raw[];
+  tct::Smem& s = *reinterpret_cast<tct::Smem*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~static_cast<uintptr_t>(127));
+  const int tid = threadIdx.x, warp = tid >> 5;
+  // weights: W_l as in inference, and W_l^T for the backward products
+  const uint4* wb4 = reinterpret_cast<const uint4*>(d.wb);
+  for (int c = tid; c < 64 * kIn / 8; c += blockDim.x)
+    tc::st16(s.w1, tc::cm(c / 10, 8 * (c % 10), kIn), __ldg(wb4 + bW1 / 8 + c));
+  for (int c = tid; c < 64 * kHid / 8; c += blockDim.x) {
+    tc::st16(s.w2, tc::cm(c / 8, 8 * (c % 8), kHid), __ldg(wb4 + bW2 / 8 + c));
+    tc::st16(s.w3, tc::cm(c / 8, 8 * (c % 8), kHid), __ldg(wb4 + bW3 / 8 + c));
   }
-  uint32_t ady[1][4];
-  ady[0][0] = pack2(dy[0], dy[1]);
-  ady[0][1] = pack2(dy[2], dy[3]);
-  ady[0][2] = 0u;
-  ady[0][3] = 0u;
-  put2(s.dy, r0 + g, 2 * t, sDy, ady[0][0]);
-  put2(s.dy, r0 + g + 8, 2 * t, sDy, ady[0][1]);
-  // delta chain: dH3 = dY W4, dZ3 = mask; dH2 = dZ3 W3; ... ; dZ1
-  float c[8][4];
-  uint32_t dz[4][4];
-  layer_bwd<1>(c, ady, s.w.w4, sHid, lane);
-  mask_pack(dz, c, h.h3);
-  store_frag<4>(s.z3, sHid, r0, dz, lane);
-  layer_bwd<4>(c, dz, s.w.w3, sHid, lane);
-  mask_pack(dz, c, h.h2);
-  store_frag<4>(s.z2, sHid, r0, dz, lane);
-  layer_bwd<4>(c, dz, s.w.w2, sHid, lane);
-  mask_pack(dz, c, h.h1);
-  store_frag<4>(s.z1, sHid, r0, dz, lane);
-  __syncthreads();
-  // weight gradients over the CTA's samples: 40 + 32 + 32 + 4 tiles of 16 x 8
-  for (int tile = warp; tile < 108; tile += kWarps) {
-    const __nv_bfloat16 *dzs, *xs;
-    int sx, off, in_dim, m0, n0, mmax;
-    if (tile < 40) {
-      dzs = s.z1; xs = s.x0; sx = sIn; off = oW1; in_dim = kIn; m0 = (tile / 10) * 16; n0 = (tile % 10) * 8; mmax = 64;
-    } else if (tile < 72) {
-      const int u = tile - 40;
-      dzs = s.z2; xs = s.h1; sx = sHid; off = oW2; in_dim = kHid; m0 = (u / 8) * 16; n0 = (u % 8) * 8; mmax = 64;
-    } else if (tile < 104) {
-      const int u = tile - 72;
-      dzs = s.z3; xs = s.h2; sx = sHid; off = oW3; in_dim = kHid; m0 = (u / 8) * 16; n0 = (u % 8) * 8; mmax = 64;
+  for (int c = tid; c < 16 * kHid / 8; c += blockDim.x)
+    tc::st16(s.w4, tc::cm(c / 8, 8 * (c % 8), kHid), __ldg(wb4 + bW4 / 8 + c));
+  // W[o][in] -> W^T[in][o]: 8 inputs of one output per 16-byte load
+  auto scatter_t = [&](unsigned char* dst, int K, int o, int in0, uint4 w) {
+    const uint32_t q[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      *reinterpret_cast<uint16_t*>(dst + tc::cm(in0 + 2 * e, o, K)) = static_cast<uint16_t>(q[e]);
+      *reinterpret_cast<uint16_t*>(dst + tc::cm(in0 + 2 * e + 1, o, K)) = static_cast<uint16_t>(q[e] >> 16);
+    }
+  };
+#pragma unroll 4
+  for (int c = tid; c < 64 * 64 / 8; c += blockDim.x) {
+    scatter_t(s.wt2, 64, c / 8, 8 * (c % 8), __ldg(wb4 + bW2 / 8 + c));
+    scatter_t(s.wt3, 64, c / 8, 8 * (c % 8), __ldg(wb4 + bW3 / 8 + c));
+  }
+  for (int c = tid; c < 16 * 64 / 8; c += blockDim.x)
+    scatter_t(s.wt4, 16, c / 8, 8 * (c % 8), __ldg(wb4 + bW4 / 8 + c));
+  for (int i = tid; i < 3 * 64 + 16; i += blockDim.x) {
+    float b = 0.f;
+    if (i < 64) b = d.master[oB1 + i];
+    else if (i < 128) b = d.master[oB2 + i - 64];
+    else if (i < 192) b = d.master[oB3 + i - 128];
+    else if (i < 192 + kOut) b = d.master[oB4 + i - 192];
+    s.bias[i] = b;
+  }
+  const uint32_t mbar = smem_u32(&s.mbar);
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncwarp();
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&s.tmem)),
+                 "r"(tct::kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  // this thread's sample: encoded row and its transpose
+  const uint32_t si = blockIdx.x * 128u + tid;
+  const int64_t j = si < batch ? idx[si] : -1;
+  const VertexIn vi = load_vertex(d, v, j);
+  tc::encode_row(s.act, tid, vi, j >= 0);
+  __syncwarp();
+  for (int f = 0; f < kIn; ++f)
+    *reinterpret_cast<__nv_bfloat16*>(s.xt0 + tc::cm(f, tid, 128)) =
+        *reinterpret_cast<const __nv_bfloat16*>(s.act + tc::cm(tid, f, kIn));
+  tct::sync_tc();
+  const uint32_t tmem = s.tmem;
+  const uint32_t trow = tmem + (static_cast<uint32_t>(warp * 32) << 16);
+  uint32_t parity = 0;
+  bool ok = true;
+  auto wait = [&]() {
+    ok = ok && __syncthreads_and(tc::mbar_wait(mbar, parity)) != 0;
+    parity ^= 1u;
+    tc::fence_after();
+  };
+  uint32_t acc[64];
+  // ---- forward
+  for (int layer = 0; layer < 3 && ok; ++layer) {
+    if (tid == 0)
+      tct::product(tmem, 0, smem_u32(s.act), layer == 0 ? 1280u : 1024u,
+                   smem_u32(layer == 0 ? s.w1 : layer == 1 ? s.w2 : s.w3),
+                   layer == 0 ? 1280u : 1024u, 64, layer == 0 ? 5 : 4, mbar);
+    wait();
+    if (!ok) break;
+    tc::tmem_ld_x64(trow, acc);
+    tc::tmem_wait_ld();
+    tc::hidden_row(s.act, tid, acc, s.bias + 64 * layer);
+    __syncwarp();
+    for (int f = 0; f < 64; ++f)
+      *reinterpret_cast<__nv_bfloat16*>(s.ht[layer] + tc::cm(f, tid, 128)) =
+          *reinterpret_cast<const __nv_bfloat16*>(s.act + tc::cm(tid, f, 64));
+    tct::sync_tc();
+  }
+  float dy[3] = {0.f, 0.f, 0.f};
+  if (ok) {
+    if (tid == 0)
+      tct::product(tmem, 0, smem_u32(s.act), 1024u, smem_u32(s.w4), 1024u, 16, 4, mbar);
+    wait();
+  }
+  if (ok) {
+    uint32_t y[16];
+    tc::tmem_ld_x16(trow, y);
+    tc::tmem_wait_ld();
+    // output delta (y - target) / batch, rounded to BF16; K = 16 tile and its transpose
+    const float invb = 1.0f / static_cast<float>(batch);
+    if (j >= 0) {
+      const float t3[3] = {__ldg(tr + j), __ldg(tg + j), __ldg(tb + j)};
+#pragma unroll
+      for (int o = 0; o < 3; ++o)
+        dy[o] = __bfloat162float(__float2bfloat16_rn(
+            (__uint_as_float(y[o]) + s.bias[192 + o] - t3[o]) * invb));
+    }
+    tc::st16(s.dz, tc::cm(tid, 0, 16), make_uint4(pack2(dy[0], dy[1]), pack2(dy[2], 0.f), 0u, 0u));
+    tc::st16(s.dz, tc::cm(tid, 8, 16), make_uint4(0u, 0u, 0u, 0u));
+#pragma unroll
+    for (int o = 0; o < 16; ++o) tct::st_b16(s.dyt, tc::cm(o, tid, 128), o < 3 ? dy[o] : 0.f);
+    tct::sync_tc();
+  }
+  // ---- backward: dH_l = dZ_{l+1} W_{l+1}, masked by H_l > 0 and rounded; each
+  // step also computes the weight gradient of the layer whose delta it reads,
+  // gW_{l+1}^T = X_{l+1}^T dZ_{l+1} (K = 128 samples), into its own columns
+  auto grad_out = [&](int l) {  // atomics of gW_l^T from tensor-memory columns gcol(l)
+    const int in_dim = l == 0 ? kIn : kHid;
+    const int off = l == 0 ? oW1 : l == 1 ? oW2 : l == 2 ? oW3 : oW4;
+    const uint32_t col = tct::gcol(l);
+    if (l < 3) {
+      tc::tmem_ld_x64(trow + col, acc);
+      tc::tmem_wait_ld();
+      if (tid < in_dim)
+        for (int o = 0; o < 64; ++o) atomicAdd(d.grad + off + o * in_dim + tid, __uint_as_float(acc[o]));
     } else {
-      const int u = tile - 104;  // output layer: m = 0..15 (0..2 real), n = 0..63
-      dzs = s.dy; xs = s.h3; sx = sHid; off = oW4; in_dim = kHid; m0 = 0; n0 = u * 16; mmax = kOut;
+      uint32_t g4[16];
+      tc::tmem_ld_x16(trow + col, g4);
+      tc::tmem_wait_ld();
+      if (tid < in_dim)
+        for (int o = 0; o < kOut; ++o) atomicAdd(d.grad + off + o * in_dim + tid, __uint_as_float(g4[o]));
     }
-    const int sdz = dzs == s.dy ? sDy : sHid;
-    const int reps = tile >= 104 ? 2 : 1;  // output-layer tiles cover 16 inputs
-    for (int rep = 0; rep < reps; ++rep) {
-      float acc[4];
-      dw_tile(acc, dzs, sdz, xs, sx, m0, n0 + rep * 8, lane);
-      const int m_a = m0 + g, m_b = m0 + g + 8, n_a = n0 + rep * 8 + 2 * t;
-      if (m_a < mmax) {
-        atomicAdd(d.grad + off + m_a * in_dim + n_a, acc[0]);
-        atomicAdd(d.grad + off + m_a * in_dim + n_a + 1, acc[1]);
+  };
+  auto grad_issue = [&](int l) {  // gW_l^T = X_l^T dZ_l (l = 3: dY)
+    const unsigned char* ga = l == 0 ? s.xt0 : s.ht[l - 1];
+    const unsigned char* gb = l < 3 ? s.dzt[l] : s.dyt;
+    tct::issue(tmem, tct::gcol(l), smem_u32(ga), 2048u, smem_u32(gb), 2048u, l < 3 ? 64u : 16u, 8);
+  };
+  for (int l = 2; l >= 0 && ok; --l) {  // produces dZ3 (l = 2), dZ2, dZ1
+    if (tid == 0) {
+      if (l == 2)
+        tct::issue(tmem, 0, smem_u32(s.dz), 256u, smem_u32(s.wt4), 256u, 64, 1);
+      else
+        tct::issue(tmem, 0, smem_u32(s.dz), 1024u, smem_u32(l == 1 ? s.wt3 : s.wt2), 1024u, 64, 4);
+      grad_issue(l + 1);
+      tc::commit(mbar);
+    }
+    wait();
+    if (!ok) break;
+    tc::tmem_ld_x64(trow, acc);
+    tc::tmem_wait_ld();
+    float z[64];
+#pragma unroll
+    for (int f = 0; f < 64; ++f) {
+      const float h = tct::ld_b16(s.ht[l], tc::cm(f, tid, 128));
+      z[f] = __bfloat162float(__float2bfloat16_rn(h > 0.f ? __uint_as_float(acc[f]) : 0.f));
+    }
+    // the products above have completed: dz may be overwritten
+    if (l > 0) {
+#pragma unroll
+      for (int kb = 0; kb < 8; ++kb)
+        tc::st16(s.dz, tc::cm(tid, 8 * kb, 64),
+                 make_uint4(pack2(z[8 * kb], z[8 * kb + 1]), pack2(z[8 * kb + 2], z[8 * kb + 3]),
+                            pack2(z[8 * kb + 4], z[8 * kb + 5]), pack2(z[8 * kb + 6], z[8 * kb + 7])));
+    }
+#pragma unroll
+    for (int f = 0; f < 64; ++f) tct::st_b16(s.dzt[l], tc::cm(f, tid, 128), z[f]);
+    grad_out(l + 1);
+    tct::sync_tc();
+  }
+  if (ok) {
+    if (tid == 0) {
+      grad_issue(0);
+      tc::commit(mbar);
+    }
+    wait();
+    if (ok) grad_out(0);
+  }
+  // ---- bias gradients: sums of the rounded deltas over the samples
+  if (ok) {
+    for (int c = tid; c < 3 * kHid + kOut; c += blockDim.x) {
+      const unsigned char* row = c < 192 ? s.dzt[c / 64] : s.dyt;
+      const int o = c < 192 ? c % 64 : c - 192;
+      const int ob = c < 64 ? oB1 : c < 128 ? oB2 : c < 192 ? oB3 : oB4;
+      float sum = 0.f;
+      for (int kb = 0; kb < 16; ++kb) {  // 8 samples per 16-byte chunk
+        const uint4 q = *reinterpret_cast<const uint4*>(row + tc::cm(o, 8 * kb, 128));
+        sum += (lo_f(q.x) + hi_f(q.x)) + (lo_f(q.y) + hi_f(q.y)) + (lo_f(q.z) + hi_f(q.z)) +
+               (lo_f(q.w) + hi_f(q.w));
       }
-      if (m_b < mmax) {
-        atomicAdd(d.grad + off + m_b * in_dim + n_a, acc[2]);
-        atomicAdd(d.grad + off + m_b * in_dim + n_a + 1, acc[3]);
-      }
+      atomicAdd(d.grad + ob + o, sum);
     }
   }
-  // bias gradients: column sums of the deltas
-  for (int col = threadIdx.x; col < 3 * kHid + kOut; col += blockDim.x) {
-    const __nv_bfloat16* z;
-    int stride, cc, off;
-    if (col < 64) { z = s.z1; stride = sHid; cc = col; off = oB1; }
-    else if (col < 128) { z = s.z2; stride = sHid; cc = col - 64; off = oB2; }
-    else if (col < 192) { z = s.z3; stride = sHid; cc = col - 128; off = oB3; }
-    else { z = s.dy; stride = sDy; cc = col - 192; off = oB4; }
-    float sum = 0.f;
-    for (int r = 0; r < kSamples; ++r) sum += __bfloat162float(z[r * stride + cc]);
-    atomicAdd(d.grad + off + cc, sum);
-  }
+  if (!ok && tid == 0) atomicOr(d.err, 1u);
+  tc::fence_before();
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(tct::kTmemCols)
+                 : "memory");
 }
 
-// Adam on the FP32 master weights; clears the gradient and refreshes the BF16
-// copies.  bc1 = 1 - beta1^step, bc2 = 1 - beta2^step.
 __global__ void k_mlp_adam(Dev d, float lr, float b1, float b2, float eps, float bc1, float bc2,
                            int apply) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -837,7 +784,6 @@ int check_mlp(pps_mlp* m) {
   return PPS_OK;
 }
 
-size_t grad_smem() { return sizeof(pps::mlp::SmemTrain); }
 
 int refresh_bf16(pps_mlp* m, cudaStream_t st) {
   pps::mlp::k_mlp_adam<<<(pps::mlp::kP + 255) / 256, 256, 0, st>>>(m->dev, 0.f, 0.f, 0.f, 0.f, 1.f,
@@ -901,10 +847,10 @@ int pps_mlp_create(pps_mlp** out, const pps_mlp_params* p, const float* init_hos
   }
   if (e == cudaSuccess) e = cudaMemcpy(m->dev.master, w.data(), P * sizeof(float), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) {
-    if (cudaFuncSetAttribute(pps::mlp::k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             static_cast<int>(grad_smem())) != cudaSuccess ||
-        cudaFuncSetAttribute(pps::mlp::k_mlp_infer_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             static_cast<int>(pps::mlp::tc::kSmemBytes)) != cudaSuccess)
+    if (cudaFuncSetAttribute(pps::mlp::k_mlp_infer_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(pps::mlp::tc::kSmemBytes)) != cudaSuccess ||
+        cudaFuncSetAttribute(pps::mlp::k_mlp_grad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(pps::mlp::tct::kSmemBytes)) != cudaSuccess)
       e = cudaGetLastError();
   }
   if (e == cudaSuccess && refresh_bf16(m, nullptr) != PPS_OK) e = cudaErrorUnknown;
@@ -982,8 +928,8 @@ int pps_mlp_gradient(pps_mlp* m, const pps_vertices* v, const float* tr, const f
   MLP_CUDA(cudaMemsetAsync(grad_out, 0, pps::mlp::kP * sizeof(float), st));
   pps::mlp::Dev d = m->dev;
   d.grad = grad_out;
-  pps::mlp::k_mlp_grad<<<batch / pps::mlp::kSamples, pps::mlp::kThreads, grad_smem(), st>>>(
-      d, vptrs(v), tr, tg, tb, idx, batch);
+  pps::mlp::k_mlp_grad_tc<<<batch / 128, 128, pps::mlp::tct::kSmemBytes, st>>>(d, vptrs(v), tr, tg,
+                                                                              tb, idx, batch);
   MLP_CUDA(cudaGetLastError());
   return PPS_OK;
 }
@@ -1001,7 +947,7 @@ int pps_mlp_train(pps_mlp* m, const pps_vertices* v, size_t n, const pps_output*
     pps::mlp::k_mlp_select<<<(B + 255) / 256, 256, 0, st>>>(filtered->count, n, m->p.seed, frame, s,
                                                              B, m->p.train_min_count, m->dev.idx);
     MLP_CUDA(cudaGetLastError());
-    pps::mlp::k_mlp_grad<<<B / pps::mlp::kSamples, pps::mlp::kThreads, grad_smem(), st>>>(
+    pps::mlp::k_mlp_grad_tc<<<B / 128, 128, pps::mlp::tct::kSmemBytes, st>>>(
         m->dev, vptrs(v), filtered->r, filtered->g, filtered->b, m->dev.idx, B);
     MLP_CUDA(cudaGetLastError());
     ++m->step;
