@@ -36,7 +36,7 @@ What it computes, and from which passage
   resolution, both taken only where the vertex's own cell has fewer than a
   threshold of members.
 
-Readings where the paper is silent (all listed in the design doc):
+Readings where the paper is silent:
 * LOD: l(d) = floor(log2(s * theta_px * d)) read from the exponent bits of the
   FP32 product, clamped to [lod_min, lod_max]; the voxel edge is 2^l, i.e. the
   "s * 2^l" of Algorithm 1 with the projected-pixel footprint folded in, so the

@@ -360,7 +360,7 @@ __global__ void __launch_bounds__(128) k_mlp_infer_tc(Dev d, VertexPtrs v, const
                        k > 0 ? 1u : 0u);
         tc::commit(mbar);
       }
-      ok = __syncthreads_and(tc::mbar_wait(mbar, parity)) != 0;  // the same verdict in every thread
+      ok = __syncthreads_and(tc::mbar_wait(mbar, parity)) != 0;  // the same outcome in every thread
       parity ^= 1u;
       if (!ok) break;
       tc::fence_after();
