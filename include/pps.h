@@ -493,7 +493,8 @@ int pps_mlp_forward(pps_mlp *m, const pps_vertices *v, size_t n, float *r, float
 
 /* pps_mlp_gradient: the loss gradient (13,699 floats, device) over `batch`
  * samples: vertex idx[i] (-1: left out) with target (tr, tg, tb)[idx[i]],
- * normalised by `batch` (a multiple of 128).  No weights change. */
+ * normalised by `batch` (a multiple of 128).  No weights change.  grad_out
+ * must be 16-byte aligned (PPS_EINVAL otherwise). */
 int pps_mlp_gradient(pps_mlp *m, const pps_vertices *v, const float *tr, const float *tg,
                      const float *tb, const int32_t *idx, uint32_t batch, float *grad_out,
                      void *stream);

@@ -48,7 +48,6 @@ struct Dev {
   float* v;       // [kP] Adam second moment
   float* grad;    // [kP] gradient accumulator
   __nv_bfloat16* wb;  // [kWb] BF16 weights
-  int32_t* idx;   // [batch] training sample vertex indices
   unsigned int* err;  // device error word (a tensor-core wait that gave up)
   float lo[3], inv[3];
 };
@@ -402,97 +401,133 @@ __global__ void __launch_bounds__(128) k_mlp_infer_tc(Dev d, VertexPtrs v, const
 // ---------------------------------------------------------------- training
 // Training samples: for sample i, the first of 16 candidate vertices (Philox,
 // key (seed, frame), counter (i, step, try, 0); index = high half of x0 * n)
-// whose cell count is >= min_count; -1 if none.
-__global__ void k_mlp_select(const uint32_t* count, size_t n, uint32_t seed, uint32_t frame,
-                             uint32_t step, uint32_t batch, uint32_t min_count, int32_t* idx) {
-  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= batch) return;
-  int32_t pick = -1;
-  for (uint32_t tr = 0; tr < 16 && pick < 0; ++tr) {
-    uint32_t x0 = i, x1 = step, x2 = tr, x3 = 0u, k0 = seed, k1 = frame;
+// whose cell count is >= min_count; -1 if none.  Candidates are drawn four at
+// a time, their counts fetched together, and the search stops at the first
+// group that holds an eligible one (the same answer as drawing all 16).
+struct SampleSel {
+  const uint32_t* count;
+  size_t n;
+  uint32_t seed, frame, step, min_count;
+};
+
+__device__ __forceinline__ uint32_t sample_candidate(const SampleSel& q, uint32_t i, uint32_t tr) {
+  uint32_t x0 = i, x1 = q.step, x2 = tr, x3 = 0u, k0 = q.seed, k1 = q.frame;
 #pragma unroll
-    for (int r = 0; r < 10; ++r) {
-      if (r) {
-        k0 += 0x9E3779B9u;
-        k1 += 0xBB67AE85u;
-      }
-      const uint32_t lo0 = 0xD2511F53u * x0, hi0 = __umulhi(0xD2511F53u, x0);
-      const uint32_t lo1 = 0xCD9E8D57u * x2, hi1 = __umulhi(0xCD9E8D57u, x2);
-      const uint32_t n0 = hi1 ^ x1 ^ k0, n2 = hi0 ^ x3 ^ k1;
-      x0 = n0;
-      x1 = lo1;
-      x2 = n2;
-      x3 = lo0;
+  for (int r = 0; r < 10; ++r) {
+    if (r) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
     }
-    const uint32_t cand = static_cast<uint32_t>((static_cast<unsigned long long>(x0) * n) >> 32);
-    if (count[cand] >= min_count) pick = static_cast<int32_t>(cand);
+    const uint32_t lo0 = 0xD2511F53u * x0, hi0 = __umulhi(0xD2511F53u, x0);
+    const uint32_t lo1 = 0xCD9E8D57u * x2, hi1 = __umulhi(0xCD9E8D57u, x2);
+    const uint32_t n0 = hi1 ^ x1 ^ k0, n2 = hi0 ^ x3 ^ k1;
+    x0 = n0;
+    x1 = lo1;
+    x2 = n2;
+    x3 = lo0;
   }
-  idx[i] = pick;
+  return static_cast<uint32_t>((static_cast<unsigned long long>(x0) * q.n) >> 32);
+}
+
+__device__ __forceinline__ int32_t select_sample(const SampleSel& q, uint32_t i) {
+#pragma unroll 1
+  for (uint32_t t0 = 0; t0 < 16; t0 += 4) {
+    uint32_t cand[4], cnt[4];
+#pragma unroll
+    for (uint32_t e = 0; e < 4; ++e) cand[e] = sample_candidate(q, i, t0 + e);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) cnt[e] = __ldg(q.count + cand[e]);
+    int32_t pick = -1;
+#pragma unroll
+    for (int e = 3; e >= 0; --e)
+      if (cnt[e] >= q.min_count) pick = static_cast<int32_t>(cand[e]);
+    if (pick >= 0) return pick;
+  }
+  return -1;
 }
 
 // ---------------------------------------------------------------- training on tcgen05
-// One CTA of 128 threads takes 128 samples (the MMA's M).  Every operand is a
-// K-major BF16 tile in the canonical no-swizzle layout, so the products that
-// run over the samples read transposed copies that the epilogues write beside
-// the row-per-sample tiles:
-//   forward   Z_l = X_l W_l^T        A = X_l   [sample][in],  B = W_l   [out][in]
-//   backward  dH_l = dZ_{l+1} W_{l+1} A = dZ    [sample][out], B = W^T   [in][out]
-//   gradient  gW_l^T = X_l^T dZ_l    A = X_l^T [in][sample],  B = dZ^T  [out][sample]
-// (M = 128 rows for the gradients: rows past the layer's inputs read the next
-// tile and are ignored).  Deltas are rounded to BF16 where the oracle rounds
-// them; weight and bias gradients are summed over the CTA's samples in FP32
-// and added to the gradient with atomics.
+// One CTA of 128 threads takes 128 samples (the MMA's M).  Every tile is kept
+// once, row per sample (or per output for the weights), in the canonical
+// no-swizzle layout with the row's elements in 16-byte groups; a product that
+// runs over the other dimension reads the same bytes as an MN-major operand
+// (instruction-descriptor bits 15 / 16), so nothing is transposed:
+//   forward   Z_l = X_l W_l^T     A = X_l  K-major,   B = W_l K-major      (M = samples)
+//   backward  dX_l = dZ_l W_l      A = dZ_l K-major,   B = W_l MN-major     (M = samples)
+//   gradient  gW_l = dZ_l^T X_l    A = dZ_l MN-major,  B = X_l MN-major     (M = outputs)
+//   bias      gb_l = dZ_l^T 1      A = dZ_l MN-major,  B = a tile of ones   (M = outputs)
+// (M = 128 for the gradients: rows past the layer's outputs read past the
+// delta tile and are ignored; a pad behind the tiles keeps those reads inside
+// the CTA's shared memory).  Deltas are rounded to BF16 where the oracle
+// rounds them; the products sum over the CTA's samples in FP32, and each
+// output's gradient row goes to the global gradient with vector reductions.
 namespace tct {
-constexpr uint32_t kTmemCols = 512;  // [0, 64): layer products, then the four gradients
+// tensor-memory columns: [0, 64) the layer products; then per layer l its
+// weight gradient (in(l) columns) and a 16-column block holding its bias
+// gradient in every column
+constexpr uint32_t kTmemCols = 512;
+__host__ __device__ constexpr uint32_t gcol(int l) { return l == 0 ? 64u : 160u + 96u * (l - 1); }
+__host__ __device__ constexpr uint32_t bcol(int l) { return l == 0 ? 144u : gcol(l) + 64u; }
+static_assert(bcol(3) + 16 <= kTmemCols, "tensor-memory columns");
+
+// Read-past room behind the tiles: a gradient operand of M = 128 reads up to
+// 16 row groups of 8 past its start at either descriptor stride.
+constexpr int kPad = 32 * 1024;
 
 struct Smem {
-  alignas(128) unsigned char act[128 * 80 * 2];  // X0, then H1..H3 [sample][feature]
-  alignas(128) unsigned char xt0[80 * 128 * 2];  // X0^T [feature][sample]
-  alignas(128) unsigned char ht[3][64 * 128 * 2];  // H1^T..H3^T
-  alignas(128) unsigned char dz[128 * 64 * 2];   // dY (K = 16), then dZ3, dZ2 [sample][out]
-  alignas(128) unsigned char dzt[3][64 * 128 * 2];  // dZ1^T..dZ3^T [out][sample]
-  alignas(128) unsigned char dyt[16 * 128 * 2];  // dY^T [out][sample]
-  alignas(128) unsigned char w1[64 * 80 * 2];    // W_l [out][in]
+  alignas(128) unsigned char w4[16 * 64 * 2];  // W_l [out][in]
+  alignas(128) unsigned char w1[64 * 80 * 2];
   alignas(128) unsigned char w2[64 * 64 * 2];
   alignas(128) unsigned char w3[64 * 64 * 2];
-  alignas(128) unsigned char w4[16 * 64 * 2];
-  alignas(128) unsigned char wt2[64 * 64 * 2];   // W_l^T [in][out]
-  alignas(128) unsigned char wt3[64 * 64 * 2];
-  alignas(128) unsigned char wt4[64 * 16 * 2];
+  alignas(128) unsigned char x0[128 * 80 * 2];  // X_0 [sample][in]
+  alignas(128) unsigned char h[3][128 * 64 * 2];  // X_1..X_3 (hidden outputs) [sample][feature]
+  alignas(128) unsigned char ones[128 * 16 * 2];
+  alignas(128) unsigned char dz[128 * 64 * 2];  // dY (16 wide), then dZ_2, dZ_1, dZ_0 [sample][out]
+  alignas(128) unsigned char pad[kPad];
   float bias[3 * 64 + 16];
   alignas(8) unsigned long long mbar;
   uint32_t tmem;
 };
 constexpr size_t kSmemBytes = sizeof(Smem) + 128;
 
-__device__ __forceinline__ void st_b16(unsigned char* base, uint32_t off, float x) {
-  *reinterpret_cast<__nv_bfloat16*>(base + off) = __float2bfloat16_rn(x);
-}
-__device__ __forceinline__ float ld_b16(const unsigned char* base, uint32_t off) {
-  return __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(base + off));
+// descriptor with explicit leading and stride byte offsets
+__device__ __forceinline__ uint64_t desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  return static_cast<uint64_t>((saddr >> 4) & 0x3FFFu) |
+         (static_cast<uint64_t>((lbo >> 4) & 0x3FFFu) << 16) |
+         (static_cast<uint64_t>((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
 }
 
-// Issue `ksteps` MMAs of K = 16 (A and B advance two core matrices, 256 bytes,
-// per step) into tensor-memory column `dcol`; product() also commits them to
-// the mbarrier.
-__device__ __forceinline__ void issue(uint32_t tmem, uint32_t dcol, uint32_t a, uint32_t sboa,
-                                      uint32_t b, uint32_t sbob, uint32_t n, int ksteps) {
-  const uint32_t id = tc::idesc(128, n);
+// An operand tile of R rows by C columns (C contiguous in 16-byte groups).
+// As a K-major operand (K = C): core matrices along K are 128 bytes apart
+// (LBO), row groups of 8 are C/8 x 128 bytes apart (SBO); a K step of 16
+// advances two core matrices.  As an MN-major operand (MN = C, K = R): groups
+// of 8 along MN are 128 bytes apart (SBO), groups of 8 along K are C/8 x 128
+// bytes apart (LBO); a K step of 16 advances two such groups.
+struct Operand {
+  uint32_t addr, lbo, sbo, kstep;
+};
+__device__ __forceinline__ Operand kmajor(const void* p, uint32_t C) {
+  return Operand{smem_u32(p), 128u, C * 16u, 256u};
+}
+__device__ __forceinline__ Operand mnmajor(const void* p, uint32_t C) {
+  return Operand{smem_u32(p), C * 16u, 128u, C * 32u};
+}
+
+// Issue `ksteps` MMAs of K = 16 into tensor-memory column `dcol`.
+__device__ __forceinline__ void issue(uint32_t tmem, uint32_t dcol, Operand a, Operand b, uint32_t n,
+                                      int ksteps, bool a_mn, bool b_mn) {
+  const uint32_t id = tc::idesc(128, n) | (a_mn ? 1u << 15 : 0u) | (b_mn ? 1u << 16 : 0u);
   for (int k = 0; k < ksteps; ++k)
-    tc::mma_bf16(tmem + dcol, tc::sdesc(a + 256u * k, sboa), tc::sdesc(b + 256u * k, sbob), id,
-                 k > 0 ? 1u : 0u);
+    tc::mma_bf16(tmem + dcol, desc(a.addr + a.kstep * k, a.lbo, a.sbo),
+                 desc(b.addr + b.kstep * k, b.lbo, b.sbo), id, k > 0 ? 1u : 0u);
 }
 
-__device__ __forceinline__ void product(uint32_t tmem, uint32_t dcol, uint32_t a, uint32_t sboa,
-                                        uint32_t b, uint32_t sbob, uint32_t n, int ksteps,
-                                        uint32_t mbar) {
-  issue(tmem, dcol, a, sboa, b, sbob, n, ksteps);
-  tc::commit(mbar);
+__device__ __forceinline__ void red_v4(float* p, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
+  asm volatile("red.relaxed.gpu.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p),
+               "f"(__uint_as_float(a)), "f"(__uint_as_float(b)), "f"(__uint_as_float(c)),
+               "f"(__uint_as_float(d))
+               : "memory");
 }
-
-// Tensor-memory columns of the weight gradient gW_l^T (layer products use
-// columns [0, 64)).
-__device__ __forceinline__ uint32_t gcol(int l) { return l == 3 ? 64u : 128u + 64u * l; }
 
 __device__ __forceinline__ void sync_tc() {
   tc::fence_smem_async();
@@ -502,14 +537,20 @@ __device__ __forceinline__ void sync_tc() {
 }
 }  // namespace tct
 
+// Samples: idx[] when given, else drawn with select_sample.  The gradient
+// d.grad must be 16-byte aligned (vector reductions).
 __global__ void __launch_bounds__(128, 1) k_mlp_grad_tc(Dev d, VertexPtrs v, const float* tr,
                                                         const float* tg, const float* tb,
-                                                        const int32_t* idx, uint32_t batch) {
+                                                        const int32_t* idx, SampleSel sel,
+                                                        uint32_t batch) {
   extern __shared__ unsigned char smem_raw[];
   tct::Smem& s = *reinterpret_cast<tct::Smem*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~static_cast<uintptr_t>(127));
   const int tid = threadIdx.x, warp = tid >> 5;
-  // weights: W_l as in inference, and W_l^T for the backward products
+  // this thread's sample first (its loads overlap the weight staging)
+  const uint32_t si = blockIdx.x * 128u + tid;
+  const int64_t j = si >= batch ? -1 : idx ? idx[si] : select_sample(sel, si);
+  const VertexIn vi = load_vertex(d, v, j);
   const uint4* wb4 = reinterpret_cast<const uint4*>(d.wb);
   for (int c = tid; c < 64 * kIn / 8; c += blockDim.x)
     tc::st16(s.w1, tc::cm(c / 10, 8 * (c % 10), kIn), __ldg(wb4 + bW1 / 8 + c));
@@ -519,22 +560,8 @@ __global__ void __launch_bounds__(128, 1) k_mlp_grad_tc(Dev d, VertexPtrs v, con
   }
   for (int c = tid; c < 16 * kHid / 8; c += blockDim.x)
     tc::st16(s.w4, tc::cm(c / 8, 8 * (c % 8), kHid), __ldg(wb4 + bW4 / 8 + c));
-  // W[o][in] -> W^T[in][o]: 8 inputs of one output per 16-byte load
-  auto scatter_t = [&](unsigned char* dst, int K, int o, int in0, uint4 w) {
-    const uint32_t q[4] = {w.x, w.y, w.z, w.w};
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      *reinterpret_cast<uint16_t*>(dst + tc::cm(in0 + 2 * e, o, K)) = static_cast<uint16_t>(q[e]);
-      *reinterpret_cast<uint16_t*>(dst + tc::cm(in0 + 2 * e + 1, o, K)) = static_cast<uint16_t>(q[e] >> 16);
-    }
-  };
-#pragma unroll 4
-  for (int c = tid; c < 64 * 64 / 8; c += blockDim.x) {
-    scatter_t(s.wt2, 64, c / 8, 8 * (c % 8), __ldg(wb4 + bW2 / 8 + c));
-    scatter_t(s.wt3, 64, c / 8, 8 * (c % 8), __ldg(wb4 + bW3 / 8 + c));
-  }
-  for (int c = tid; c < 16 * 64 / 8; c += blockDim.x)
-    scatter_t(s.wt4, 16, c / 8, 8 * (c % 8), __ldg(wb4 + bW4 / 8 + c));
+  for (int c = tid; c < 128 * 16 / 8; c += blockDim.x)  // BF16 1.0 pairs
+    tc::st16(s.ones, 16u * c, make_uint4(0x3F803F80u, 0x3F803F80u, 0x3F803F80u, 0x3F803F80u));
   for (int i = tid; i < 3 * 64 + 16; i += blockDim.x) {
     float b = 0.f;
     if (i < 64) b = d.master[oB1 + i];
@@ -556,15 +583,7 @@ __global__ void __launch_bounds__(128, 1) k_mlp_grad_tc(Dev d, VertexPtrs v, con
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
-  // this thread's sample: encoded row and its transpose
-  const uint32_t si = blockIdx.x * 128u + tid;
-  const int64_t j = si < batch ? idx[si] : -1;
-  const VertexIn vi = load_vertex(d, v, j);
-  tc::encode_row(s.act, tid, vi, j >= 0);
-  __syncwarp();
-  for (int f = 0; f < kIn; ++f)
-    *reinterpret_cast<__nv_bfloat16*>(s.xt0 + tc::cm(f, tid, 128)) =
-        *reinterpret_cast<const __nv_bfloat16*>(s.act + tc::cm(tid, f, kIn));
+  tc::encode_row(s.x0, tid, vi, j >= 0);
   tct::sync_tc();
   const uint32_t tmem = s.tmem;
   const uint32_t trow = tmem + (static_cast<uint32_t>(warp * 32) << 16);
@@ -575,35 +594,39 @@ __global__ void __launch_bounds__(128, 1) k_mlp_grad_tc(Dev d, VertexPtrs v, con
     parity ^= 1u;
     tc::fence_after();
   };
+  // layer l's input X_l and weight W_l
+  auto X = [&](int l) -> const unsigned char* { return l == 0 ? s.x0 : s.h[l - 1]; };
+  auto W = [&](int l) -> const unsigned char* {
+    return l == 0 ? s.w1 : l == 1 ? s.w2 : l == 2 ? s.w3 : s.w4;
+  };
   uint32_t acc[64];
-  // ---- forward
-  for (int layer = 0; layer < 3 && ok; ++layer) {
-    if (tid == 0)
-      tct::product(tmem, 0, smem_u32(s.act), layer == 0 ? 1280u : 1024u,
-                   smem_u32(layer == 0 ? s.w1 : layer == 1 ? s.w2 : s.w3),
-                   layer == 0 ? 1280u : 1024u, 64, layer == 0 ? 5 : 4, mbar);
+  // ---- forward: X_{l+1} = ReLU(X_l W_l^T + b_l), l = 0..2
+  for (int l = 0; l < 3 && ok; ++l) {
+    const uint32_t C = l == 0 ? kIn : kHid;
+    if (tid == 0) {
+      tct::issue(tmem, 0, tct::kmajor(X(l), C), tct::kmajor(W(l), C), 64, C / 16, false, false);
+      tc::commit(mbar);
+    }
     wait();
     if (!ok) break;
     tc::tmem_ld_x64(trow, acc);
     tc::tmem_wait_ld();
-    tc::hidden_row(s.act, tid, acc, s.bias + 64 * layer);
-    __syncwarp();
-    for (int f = 0; f < 64; ++f)
-      *reinterpret_cast<__nv_bfloat16*>(s.ht[layer] + tc::cm(f, tid, 128)) =
-          *reinterpret_cast<const __nv_bfloat16*>(s.act + tc::cm(tid, f, 64));
+    tc::hidden_row(s.h[l], tid, acc, s.bias + 64 * l);
     tct::sync_tc();
   }
   float dy[3] = {0.f, 0.f, 0.f};
   if (ok) {
-    if (tid == 0)
-      tct::product(tmem, 0, smem_u32(s.act), 1024u, smem_u32(s.w4), 1024u, 16, 4, mbar);
+    if (tid == 0) {
+      tct::issue(tmem, 0, tct::kmajor(s.h[2], kHid), tct::kmajor(s.w4, kHid), 16, 4, false, false);
+      tc::commit(mbar);
+    }
     wait();
   }
   if (ok) {
     uint32_t y[16];
     tc::tmem_ld_x16(trow, y);
     tc::tmem_wait_ld();
-    // output delta (y - target) / batch, rounded to BF16; K = 16 tile and its transpose
+    // output delta (y - target) / batch, rounded to BF16, as a 16-wide tile
     const float invb = 1.0f / static_cast<float>(batch);
     if (j >= 0) {
       const float t3[3] = {__ldg(tr + j), __ldg(tg + j), __ldg(tb + j)};
@@ -614,65 +637,70 @@ __global__ void __launch_bounds__(128, 1) k_mlp_grad_tc(Dev d, VertexPtrs v, con
     }
     tc::st16(s.dz, tc::cm(tid, 0, 16), make_uint4(pack2(dy[0], dy[1]), pack2(dy[2], 0.f), 0u, 0u));
     tc::st16(s.dz, tc::cm(tid, 8, 16), make_uint4(0u, 0u, 0u, 0u));
-#pragma unroll
-    for (int o = 0; o < 16; ++o) tct::st_b16(s.dyt, tc::cm(o, tid, 128), o < 3 ? dy[o] : 0.f);
     tct::sync_tc();
   }
-  // ---- backward: dH_l = dZ_{l+1} W_{l+1}, masked by H_l > 0 and rounded; each
-  // step also computes the weight gradient of the layer whose delta it reads,
-  // gW_{l+1}^T = X_{l+1}^T dZ_{l+1} (K = 128 samples), into its own columns
-  auto grad_out = [&](int l) {  // atomics of gW_l^T from tensor-memory columns gcol(l)
-    const int in_dim = l == 0 ? kIn : kHid;
+  // gradient of layer l: gW_l = dZ_l^T X_l and gb_l = dZ_l^T 1 from the delta in s.dz
+  auto grad_issue = [&](int l) {
+    const uint32_t co = l == 3 ? 16u : 64u, ci = l == 0 ? kIn : kHid;
+    tct::issue(tmem, tct::gcol(l), tct::mnmajor(s.dz, co), tct::mnmajor(X(l), ci), ci, 8, true, true);
+    tct::issue(tmem, tct::bcol(l), tct::mnmajor(s.dz, co), tct::mnmajor(s.ones, 16), 16, 8, true, true);
+  };
+  // row o of gW_l (thread o) and gb_l[o] into the global gradient
+  auto grad_out = [&](int l) {
+    const int out_dim = l == 3 ? kOut : kHid, in_dim = l == 0 ? kIn : kHid;
+    if (warp * 32 >= out_dim) return;  // warp-uniform: rows past the outputs are not read
     const int off = l == 0 ? oW1 : l == 1 ? oW2 : l == 2 ? oW3 : oW4;
-    const uint32_t col = tct::gcol(l);
-    if (l < 3) {
-      tc::tmem_ld_x64(trow + col, acc);
-      tc::tmem_wait_ld();
-      if (tid < in_dim)
-        for (int o = 0; o < 64; ++o) atomicAdd(d.grad + off + o * in_dim + tid, __uint_as_float(acc[o]));
-    } else {
-      uint32_t g4[16];
-      tc::tmem_ld_x16(trow + col, g4);
-      tc::tmem_wait_ld();
-      if (tid < in_dim)
-        for (int o = 0; o < kOut; ++o) atomicAdd(d.grad + off + o * in_dim + tid, __uint_as_float(g4[o]));
+    const int boff = l == 0 ? oB1 : l == 1 ? oB2 : l == 2 ? oB3 : oB4;
+    uint32_t g[64], e[16], bq[16];
+    tc::tmem_ld_x64(trow + tct::gcol(l), g);
+    tc::tmem_ld_x16(trow + tct::gcol(l) + 64, e);  // layer 0: inputs 64..79, else the bias block
+    if (l == 0) tc::tmem_ld_x16(trow + tct::bcol(0), bq);
+    tc::tmem_wait_ld();
+    if (tid < out_dim) {
+      float* row = d.grad + off + tid * in_dim;
+#pragma unroll
+      for (int q = 0; q < 16; ++q) tct::red_v4(row + 4 * q, g[4 * q], g[4 * q + 1], g[4 * q + 2], g[4 * q + 3]);
+      if (l == 0) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          tct::red_v4(row + 64 + 4 * q, e[4 * q], e[4 * q + 1], e[4 * q + 2], e[4 * q + 3]);
+        atomicAdd(d.grad + boff + tid, __uint_as_float(bq[0]));
+      } else {
+        atomicAdd(d.grad + boff + tid, __uint_as_float(e[0]));
+      }
     }
   };
-  auto grad_issue = [&](int l) {  // gW_l^T = X_l^T dZ_l (l = 3: dY)
-    const unsigned char* ga = l == 0 ? s.xt0 : s.ht[l - 1];
-    const unsigned char* gb = l < 3 ? s.dzt[l] : s.dyt;
-    tct::issue(tmem, tct::gcol(l), smem_u32(ga), 2048u, smem_u32(gb), 2048u, l < 3 ? 64u : 16u, 8);
-  };
-  for (int l = 2; l >= 0 && ok; --l) {  // produces dZ3 (l = 2), dZ2, dZ1
+  // ---- backward: for l = 3, 2, 1 the delta dZ_l in s.dz gives dX_l = dZ_l W_l
+  // and the gradients of layer l in one commit; then dZ_{l-1} = dX_l masked
+  // by X_l > 0 and rounded replaces it
+  for (int l = 3; l >= 1 && ok; --l) {
     if (tid == 0) {
-      if (l == 2)
-        tct::issue(tmem, 0, smem_u32(s.dz), 256u, smem_u32(s.wt4), 256u, 64, 1);
-      else
-        tct::issue(tmem, 0, smem_u32(s.dz), 1024u, smem_u32(l == 1 ? s.wt3 : s.wt2), 1024u, 64, 4);
-      grad_issue(l + 1);
+      const uint32_t co = l == 3 ? 16u : 64u;
+      tct::issue(tmem, 0, tct::kmajor(s.dz, co), tct::mnmajor(W(l), kHid), 64, co / 16, false, true);
+      grad_issue(l);
       tc::commit(mbar);
     }
     wait();
     if (!ok) break;
     tc::tmem_ld_x64(trow, acc);
+    const unsigned char* xl = X(l);
+    uint4 hq[8];
+#pragma unroll
+    for (int kb = 0; kb < 8; ++kb) hq[kb] = *reinterpret_cast<const uint4*>(xl + tc::cm(tid, 8 * kb, 64));
     tc::tmem_wait_ld();
-    float z[64];
 #pragma unroll
-    for (int f = 0; f < 64; ++f) {
-      const float h = tct::ld_b16(s.ht[l], tc::cm(f, tid, 128));
-      z[f] = __bfloat162float(__float2bfloat16_rn(h > 0.f ? __uint_as_float(acc[f]) : 0.f));
+    for (int kb = 0; kb < 8; ++kb) {
+      const uint32_t hw[4] = {hq[kb].x, hq[kb].y, hq[kb].z, hq[kb].w};
+      uint32_t zw[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int c = 8 * kb + 2 * q;
+        zw[q] = pack2(lo_f(hw[q]) > 0.f ? __uint_as_float(acc[c]) : 0.f,
+                      hi_f(hw[q]) > 0.f ? __uint_as_float(acc[c + 1]) : 0.f);
+      }
+      tc::st16(s.dz, tc::cm(tid, 8 * kb, 64), make_uint4(zw[0], zw[1], zw[2], zw[3]));
     }
-    // the products above have completed: dz may be overwritten
-    if (l > 0) {
-#pragma unroll
-      for (int kb = 0; kb < 8; ++kb)
-        tc::st16(s.dz, tc::cm(tid, 8 * kb, 64),
-                 make_uint4(pack2(z[8 * kb], z[8 * kb + 1]), pack2(z[8 * kb + 2], z[8 * kb + 3]),
-                            pack2(z[8 * kb + 4], z[8 * kb + 5]), pack2(z[8 * kb + 6], z[8 * kb + 7])));
-    }
-#pragma unroll
-    for (int f = 0; f < 64; ++f) tct::st_b16(s.dzt[l], tc::cm(f, tid, 128), z[f]);
-    grad_out(l + 1);
+    grad_out(l);
     tct::sync_tc();
   }
   if (ok) {
@@ -682,21 +710,6 @@ __global__ void __launch_bounds__(128, 1) k_mlp_grad_tc(Dev d, VertexPtrs v, con
     }
     wait();
     if (ok) grad_out(0);
-  }
-  // ---- bias gradients: sums of the rounded deltas over the samples
-  if (ok) {
-    for (int c = tid; c < 3 * kHid + kOut; c += blockDim.x) {
-      const unsigned char* row = c < 192 ? s.dzt[c / 64] : s.dyt;
-      const int o = c < 192 ? c % 64 : c - 192;
-      const int ob = c < 64 ? oB1 : c < 128 ? oB2 : c < 192 ? oB3 : oB4;
-      float sum = 0.f;
-      for (int kb = 0; kb < 16; ++kb) {  // 8 samples per 16-byte chunk
-        const uint4 q = *reinterpret_cast<const uint4*>(row + tc::cm(o, 8 * kb, 128));
-        sum += (lo_f(q.x) + hi_f(q.x)) + (lo_f(q.y) + hi_f(q.y)) + (lo_f(q.z) + hi_f(q.z)) +
-               (lo_f(q.w) + hi_f(q.w));
-      }
-      atomicAdd(d.grad + ob + o, sum);
-    }
   }
   if (!ok && tid == 0) atomicOr(d.err, 1u);
   tc::fence_before();
@@ -739,7 +752,6 @@ struct pps_mlp {
   pps_mlp_params p{};
   int device = 0;
   pps::mlp::Dev dev{};
-  size_t idx_cap = 0;
   uint32_t step = 0;  // Adam steps taken
   int sms = 0;                  // multiprocessors of the device
   int32_t* list = nullptr;      // inference: indices of the vertices to evaluate
@@ -823,7 +835,6 @@ int pps_mlp_create(pps_mlp** out, const pps_mlp_params* p, const float* init_hos
   if (e == cudaSuccess) e = cudaMalloc(&m->dev.v, P * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc(&m->dev.grad, P * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc(&m->dev.wb, pps::mlp::kWb * sizeof(__nv_bfloat16));
-  if (e == cudaSuccess) e = cudaMalloc(&m->dev.idx, p->batch * sizeof(int32_t));
   if (e == cudaSuccess) e = cudaMalloc(&m->dev.err, sizeof(unsigned int));
   if (e == cudaSuccess) e = cudaMalloc(&m->counter, sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMemset(m->dev.err, 0, sizeof(unsigned int));
@@ -861,7 +872,6 @@ int pps_mlp_create(pps_mlp** out, const pps_mlp_params* p, const float* init_hos
     cudaFree(m->dev.v);
     cudaFree(m->dev.grad);
     cudaFree(m->dev.wb);
-    cudaFree(m->dev.idx);
     cudaFree(m->dev.err);
     cudaFree(m->counter);
     delete m;
@@ -869,7 +879,6 @@ int pps_mlp_create(pps_mlp** out, const pps_mlp_params* p, const float* init_hos
     return mfail(e == cudaErrorMemoryAllocation ? PPS_ENOMEM : PPS_ECUDA,
                  std::string("pps_mlp_create: ") + cudaGetErrorString(e));
   }
-  m->idx_cap = p->batch;
   *out = m;
   return PPS_OK;
 }
@@ -882,7 +891,6 @@ int pps_mlp_destroy(pps_mlp* m) {
   cudaFree(m->dev.v);
   cudaFree(m->dev.grad);
   cudaFree(m->dev.wb);
-  cudaFree(m->dev.idx);
   cudaFree(m->dev.err);
   cudaFree(m->counter);
   cudaFree(m->list);
@@ -922,14 +930,15 @@ int pps_mlp_gradient(pps_mlp* m, const pps_vertices* v, const float* tr, const f
                      void* stream) {
   if (int rc = check_mlp(m)) return rc;
   if (!v || !tr || !tg || !tb || !idx || !grad_out) return mfail(PPS_EINVAL, "NULL argument");
+  if (reinterpret_cast<uintptr_t>(grad_out) % 16) return mfail(PPS_EINVAL, "grad_out must be 16-byte aligned");
   if (batch == 0 || batch % pps::mlp::kSamples)
     return mfail(PPS_EINVAL, "batch must be a positive multiple of 128");
   const cudaStream_t st = static_cast<cudaStream_t>(stream);
   MLP_CUDA(cudaMemsetAsync(grad_out, 0, pps::mlp::kP * sizeof(float), st));
   pps::mlp::Dev d = m->dev;
   d.grad = grad_out;
-  pps::mlp::k_mlp_grad_tc<<<batch / 128, 128, pps::mlp::tct::kSmemBytes, st>>>(d, vptrs(v), tr, tg,
-                                                                              tb, idx, batch);
+  pps::mlp::k_mlp_grad_tc<<<batch / 128, 128, pps::mlp::tct::kSmemBytes, st>>>(
+      d, vptrs(v), tr, tg, tb, idx, pps::mlp::SampleSel{}, batch);
   MLP_CUDA(cudaGetLastError());
   return PPS_OK;
 }
@@ -944,11 +953,9 @@ int pps_mlp_train(pps_mlp* m, const pps_vertices* v, size_t n, const pps_output*
   const cudaStream_t st = static_cast<cudaStream_t>(stream);
   const uint32_t B = m->p.batch;
   for (uint32_t s = 0; s < m->p.steps; ++s) {
-    pps::mlp::k_mlp_select<<<(B + 255) / 256, 256, 0, st>>>(filtered->count, n, m->p.seed, frame, s,
-                                                             B, m->p.train_min_count, m->dev.idx);
-    MLP_CUDA(cudaGetLastError());
+    const pps::mlp::SampleSel sel{filtered->count, n, m->p.seed, frame, s, m->p.train_min_count};
     pps::mlp::k_mlp_grad_tc<<<B / 128, 128, pps::mlp::tct::kSmemBytes, st>>>(
-        m->dev, vptrs(v), filtered->r, filtered->g, filtered->b, m->dev.idx, B);
+        m->dev, vptrs(v), filtered->r, filtered->g, filtered->b, nullptr, sel, B);
     MLP_CUDA(cudaGetLastError());
     ++m->step;
     const float bc1 = 1.f - std::pow(m->p.beta1, static_cast<float>(m->step));
