@@ -24,6 +24,10 @@ What it computes, and from which passage
   Sec. 3.3.1) reaches up to summation order.
 * Temporal blending (Sec. 3.4.1): c = alpha c_old + (1 - alpha) c_new, or the
   integrating weight alpha = N_old / (N_old + N_new).
+* Changes in resolution across frames (Sec. 3.4.2): a cell without history
+  of its own adds up the sums and counts of its eight finer children, or else
+  takes its coarser parent's average with the parent's count shared among
+  eight children.
 * Overflow audit (Sec. 3.2: the probe limit, after which a vertex keeps its
   own unfiltered contribution): a helper that checks a table dump.
 * History eviction (Sec. 3.4.3): a sequential model of a history table whose
@@ -435,14 +439,68 @@ class History:
                        np.zeros(0, dtype=np.int64))
 
 
+def migrated_history(history: History, tuples: np.ndarray):
+    """Changes in resolution across frames (Sec. 3.4.2) for cells `tuples`
+    that have no history entry of their own, read from `history` as it was
+    before this frame.
+
+    Resolution decreased (the cell is coarser than before): its eight finer
+    children (2 x~ + d, d in {0, 1}^3, level l' - 1, the other tuple entries
+    equal) that have history are added up -- sums and counts, so the value is
+    sum(N_i c_i) / sum(N_i) and the count sum(N_i).  Otherwise, resolution
+    increased (the cell is finer than before): its coarser parent (floor(x~ /
+    2), level l' + 1) passes on its average, its count shared among its eight
+    children, ceil(N / 8).  Returns (c_old (m, 3), n_old (m,), found (m,))."""
+    m = tuples.shape[0]
+    c = np.zeros((m, 3))
+    n = np.zeros(m, dtype=np.int64)
+    if history.tuples.shape[0] == 0 or m == 0:
+        return c, n, np.zeros(m, dtype=bool)
+    hk = _row_keys(history.tuples)
+    order = np.argsort(hk, kind="stable")
+    sk = hk[order]
+
+    def lookup(q):
+        qk = _row_keys(q)
+        pos = np.searchsorted(sk, qk)
+        posc = np.minimum(pos, sk.shape[0] - 1)
+        hit = (pos < sk.shape[0]) & (sk[posc] == qk)
+        return np.where(hit, order[posc], -1)
+
+    sum_nc = np.zeros((m, 3))
+    sum_n = np.zeros(m, dtype=np.int64)
+    for d in np.array([(dx, dy, dz) for dx in (0, 1) for dy in (0, 1) for dz in (0, 1)]):
+        q = tuples.copy()
+        q[:, :3] = 2 * q[:, :3] + d
+        q[:, 3] -= 1
+        idx = lookup(q)
+        hit = idx >= 0
+        sum_nc[hit] += history.n[idx[hit], None] * history.c[idx[hit]]
+        sum_n[hit] += history.n[idx[hit]]
+    kids = sum_n > 0
+    c[kids] = sum_nc[kids] / sum_n[kids, None]
+    n[kids] = sum_n[kids]
+    q = tuples.copy()
+    q[:, :3] = np.floor_divide(q[:, :3], 2)
+    q[:, 3] += 1
+    idx = lookup(q)
+    par = ~kids & (idx >= 0)
+    c[par] = history.c[idx[par]]
+    n[par] = (history.n[idx[par]] + 7) // 8
+    return c, n, kids | par
+
+
 def blend(history: History, fr: FrameResult, alpha: float, fp16: bool = False,
-          n_cap: Optional[int] = None) -> Tuple[History, np.ndarray, np.ndarray]:
+          n_cap: Optional[int] = None, migrate: bool = False
+          ) -> Tuple[History, np.ndarray, np.ndarray]:
     """c = alpha c_old + (1 - alpha) c_new per cell present in this frame.
 
     alpha < 0 selects the integrating weight N_old / (N_old + N_new).  A cell
     without history takes c_new; cells absent this frame keep their history.
     N <- N_old + N_new (capped at `n_cap` if given).  With `fp16` the stored
     average is rounded to binary16, as a half-precision history store does.
+    With `migrate` a cell without history of its own takes the one of its
+    finer children or coarser parent (migrated_history) as (c_old, N_old).
     Returns (new history, blended value per vertex (N, 3), count per vertex)."""
     H = history.tuples.shape[0]
     allk = np.concatenate([history.tuples, fr.tuples]) if H else fr.tuples
@@ -461,6 +519,12 @@ def blend(history: History, fr: FrameResult, alpha: float, fp16: bool = False,
     c_old = c[inw]
     n_old = N[inw]
     had = has_old[inw]
+    if migrate and not had.all():
+        need = np.nonzero(~had)[0]
+        mc, mn, mf = migrated_history(history, fr.tuples[need])
+        c_old[need[mf]] = mc[mf]
+        n_old[need[mf]] = mn[mf]
+        had[need[mf]] = True
     if alpha < 0:
         a = (n_old / np.maximum(n_old + n_new, 1))[:, None]
     else:
