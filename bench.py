@@ -232,6 +232,12 @@ def run_ours(args):
         for fb in ("coarse", "neighbors"):
             fallbacks[fb] = fallback_leg(frames, cfg, calls, fsteps, args.warmup, fb,
                                          out["status"])
+    hvariants = {}
+    if not args.no_fallbacks:
+        hvariants["evict"] = history_leg(frames, cfg, calls, fsteps, args.warmup,
+                                         hist_evict=True, log2_hist_slots=23)
+        hvariants["migrate"] = history_leg(frames, cfg, calls, fsteps, args.warmup,
+                                           hist_migrate=True)
     ms, job_n = reduce_ranks(ms, float(total_n), dev)
     value = job_n / (ms / 1e3)
     ms_step = ms / args.steps
@@ -308,6 +314,11 @@ def run_ours(args):
                 "workload": "the headline temporal HD frames with a low-count fallback "
                             "(count < 4): coarse = multi-level accumulation, neighbors = "
                             "3x3x3 neighborhood search", **fallbacks}
+        if hvariants:
+            line["history_variants"] = {
+                "workload": "the headline temporal HD frames with an evicting history of "
+                            "2^23 cells (evict) or a history that follows changes of "
+                            "resolution (migrate)", **hvariants}
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(frames[0], w, args.cpu_sample)
         if not args.no_mlp:
@@ -395,6 +406,41 @@ def fallback_leg(frames, cfg, calls, steps, warmup, fallback, status):
     tab.close()
     return {"ms_per_frame": ms, "vertices_per_s": total / steps / (ms * 1e-3),
             "fallback_share": share}
+
+
+def history_leg(frames, cfg, calls, steps, warmup, **table_kw):
+    """The headline workload with a history variant: "evict" = an evicting
+    history of 2^23 cells (Sec. 3.4.3), "migrate" = the history following
+    changes of resolution (Sec. 3.4.2; split kernels, two blend launches).
+    Same timing as the headline."""
+    import ctypes
+    import torch
+    from paper_1902_05942_gb300 import pps
+    tab = pps.Table(cfg, **table_kw)
+    L = pps.lib()
+    stream = torch.cuda.current_stream()
+
+    def step(i):
+        cam, vs, n, os_ = calls[i % len(calls)]
+        rc = L.pps_filter(tab.handle, ctypes.byref(cam), i, ctypes.byref(vs), n, 1, cfg.alpha,
+                          ctypes.byref(os_), stream.cuda_stream)
+        if rc:
+            raise pps.PPSError(rc, pps.last_error())
+        return n
+
+    for i in range(warmup):
+        step(i)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    total = sum(step(warmup + i) for i in range(steps))
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / steps
+    st = tab.stats()
+    tab.close()
+    return {"ms_per_frame": ms, "vertices_per_s": total / steps / (ms * 1e-3),
+            "hist_occupied": st["hist_occupied"], "hist_overflow_cells": st["hist_overflow"]}
 
 
 MLP_FWD_FLOP = 2 * (80 * 64 + 64 * 64 + 64 * 64 + 64 * 3)  # per sample, algorithmic

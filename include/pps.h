@@ -129,6 +129,20 @@ extern "C" {
  *                     afresh there (no history).  Entries found are refreshed
  *                     to this epoch.  Needs hist_mode != NONE.  0: no eviction
  *                     (history entries live as long as the table).
+ *  hist_migrate       1: history follows changes of resolution across frames
+ *                     (Sec. 3.4.2).  A cell whose history entry is new this
+ *                     frame takes as its old value the history of its eight
+ *                     finer children (2 x~ + {0,1}^3 at level l' - 1, same
+ *                     quantized normal) added up -- sum(N_i c_i) / sum(N_i)
+ *                     with count sum(N_i) -- or, with no such child, the
+ *                     average of its coarser parent (floor(x~ / 2) at level
+ *                     l' + 1) with count ceil(N_parent / 8).  The lookups read
+ *                     the history as it was before this frame's blend.  Needs
+ *                     hist_mode != NONE and hist_evict = 0; frames run through
+ *                     the split kernels (pps_filter does so itself), which then
+ *                     keep each cell's quantized key (16 B per cell); no extra
+ *                     key word (pps_vertices.extra) is accepted; pps_batch_create
+ *                     and pps_filter_noalloc reject such tables.
  *  reserved           must be zero.
  */
 typedef struct pps_params {
@@ -149,6 +163,7 @@ typedef struct pps_params {
   uint32_t log2_hist_slots;
   uint32_t fallback;
   uint32_t hist_evict;
+  uint32_t hist_migrate;
   uint32_t reserved[1];
 } pps_params;
 

@@ -62,6 +62,7 @@ class FilterConfig:
     alpha: Optional[float] = None  # temporal blend weight of the old value (< 0: integrate)
     fallback: str = "none"  # low-count vertices: "none", "coarse" (Sec. 3.3.3), "neighbors" (3.3.2)
     hist_evict: bool = False  # history evicts its least recently used entries (Sec. 3.4.3)
+    hist_migrate: bool = False  # history follows changes of resolution (Sec. 3.4.2)
 
     def oracle_kwargs(self) -> dict:
         """Plain keyword arguments for the oracle's key parameters."""

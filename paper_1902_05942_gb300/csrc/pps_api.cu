@@ -101,6 +101,9 @@ int check_params(const pps_params* p) {
   if (p->hist_evict > 1) return fail(PPS_EINVAL, "hist_evict must be 0 or 1");
   if (p->hist_evict && p->hist_mode == PPS_HIST_NONE)
     return fail(PPS_EINVAL, "hist_evict needs a history (hist_mode != NONE)");
+  if (p->hist_migrate > 1) return fail(PPS_EINVAL, "hist_migrate must be 0 or 1");
+  if (p->hist_migrate && (p->hist_mode == PPS_HIST_NONE || p->hist_evict))
+    return fail(PPS_EINVAL, "hist_migrate needs a history without eviction");
   if (p->fallback == PPS_FALLBACK_COARSE && !std::isfinite(2.0f * p->voxel_scale))
     return fail(PPS_EINVAL, "voxel_scale too large for a coarser level");
   for (uint32_t r : p->reserved)
@@ -177,7 +180,7 @@ int reset_frame(pps_table* t, cudaStream_t st) {
 }
 
 // Make the dense cell arrays hold at least `need` cells, keeping the first
-// `keep` cells (accumulators, cell info and tile counts).  New accumulators
+// `keep` cells (accumulators, cell info, tile counts and quantized keys).  New accumulators
 // start at zero.
 int ensure_dense(pps_table* t, size_t need, size_t keep, cudaStream_t st) {
   if (need <= t->D) return PPS_OK;
@@ -187,10 +190,12 @@ int ensure_dense(pps_table* t, size_t need, size_t keep, cudaStream_t st) {
   if (cap > 0xFFFFFFF0ull) cap = 0xFFFFFFF0ull;
   const size_t acc_b = t->dev.fixed ? 32 : 16;
   const size_t nb = cap / 4 + 16;  // tile counts: one per block of >= 4 cells
-  void *acc = nullptr, *info = nullptr, *bc = nullptr;
+  void *acc = nullptr, *info = nullptr, *bc = nullptr, *kw = nullptr, *hold = nullptr;
   cudaError_t e = cudaMalloc(&acc, cap * acc_b);
   if (e == cudaSuccess) e = cudaMalloc(&info, cap * sizeof(uint4));
   if (e == cudaSuccess) e = cudaMalloc(&bc, nb * sizeof(uint32_t));
+  if (e == cudaSuccess && t->dev.hist_migrate) e = cudaMalloc(&kw, cap * sizeof(uint4));
+  if (e == cudaSuccess && t->dev.hist_migrate) e = cudaMalloc(&hold, cap * sizeof(float4));
   if (e == cudaSuccess) e = cudaMemsetAsync(acc, 0, cap * acc_b, st);
   void* old_acc = t->dev.fixed ? static_cast<void*>(t->dev.acc64) : static_cast<void*>(t->dev.acc);
   if (e == cudaSuccess && keep) {
@@ -200,18 +205,26 @@ int ensure_dense(pps_table* t, size_t need, size_t keep, cudaStream_t st) {
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(bc, t->dev.bcount, (t->D / 4 + 16) * sizeof(uint32_t),
                           cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess && kw)
+      e = cudaMemcpyAsync(kw, t->dev.kw, keep * sizeof(uint4), cudaMemcpyDeviceToDevice, st);
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) {
     cudaFree(acc);
     cudaFree(info);
     cudaFree(bc);
+    cudaFree(kw);
+    cudaFree(hold);
     cudaGetLastError();
     return fail(PPS_ENOMEM, std::string("dense cell arrays: ") + cudaGetErrorString(e));
   }
   cudaFree(old_acc);
   cudaFree(t->dev.info);
   cudaFree(t->dev.bcount);
+  cudaFree(t->dev.kw);
+  cudaFree(t->dev.hold);
+  t->dev.kw = static_cast<uint4*>(kw);
+  t->dev.hold = static_cast<float4*>(hold);
   if (t->dev.fixed)
     t->dev.acc64 = static_cast<unsigned long long*>(acc);
   else
@@ -235,6 +248,8 @@ void free_all(pps_table* t) {
   cudaFree(t->dev.acc64);
   cudaFree(t->dev.info);
   cudaFree(t->dev.bcount);
+  cudaFree(t->dev.kw);
+  cudaFree(t->dev.hold);
   cudaFree(t->dev.hcells);
   cudaFree(t->dev.ctrl);
   cudaFree(t->gstash);
@@ -324,6 +339,7 @@ int pps_create(pps_table** out, const pps_params* p) {
   };
   const bool fixed = p->accum_mode == PPS_ACCUM_FIXED;
   t->dev.fixed = fixed;
+  t->dev.hist_migrate = p->hist_migrate ? 1 : 0;  // before the dense arrays are made
   t->dev.hstride = p->hist_mode == PPS_HIST_FP16 ? 16u : 32u;
   t->dev.hfp_off = p->hist_mode == PPS_HIST_FP16 ? 8u : 16u;
   cudaError_t e = alloc(reinterpret_cast<void**>(&t->dev.slots), T * sizeof(unsigned long long));
@@ -401,6 +417,8 @@ int pps_insert(pps_table* t, const pps_vertices* v, size_t n, uint32_t* slot_out
   if (int rc = check_table(t)) return rc;
   if (int rc = check_vertices(v, n)) return rc;
   if (t->state != kOpen) return fail(PPS_ESTATE, "pps_insert needs pps_build first (and no pps_blend since)");
+  if (t->dev.hist_migrate && v->extra)
+    return fail(PPS_EINVAL, "a table with hist_migrate takes no extra key word");
   const cudaStream_t st = static_cast<cudaStream_t>(stream);
   const size_t tile = static_cast<size_t>(pps::tile_size());
   const size_t tiles = (n + tile - 1) / tile;
@@ -418,7 +436,8 @@ int pps_blend(pps_table* t, float alpha, void* stream) {
   if (!std::isfinite(alpha) || alpha > 1.0f) return fail(PPS_EINVAL, "alpha must be finite and <= 1");
   if (t->state != kOpen) return fail(PPS_ESTATE, "pps_blend needs an open frame (pps_build, pps_insert)");
   if (int rc = next_epoch(t, static_cast<cudaStream_t>(stream))) return rc;
-  PPS_CUDA(pps::launch_blend(t->dev, t->frame_tiles, alpha, static_cast<cudaStream_t>(stream)));
+  PPS_CUDA(pps::launch_blend(t->kc, t->dev, t->frame_tiles, alpha,
+                             static_cast<cudaStream_t>(stream)));
   t->state = kBlended;
   if (t->coarse) return pps_blend(t->coarse, alpha, stream);
   return PPS_OK;
@@ -502,8 +521,9 @@ int pps_filter(pps_table* t, const pps_camera* cam, uint32_t frame, const pps_ve
   if (blend && (!std::isfinite(alpha) || alpha > 1.0f))
     return fail(PPS_EINVAL, "alpha must be finite and <= 1");
   const cudaStream_t st = static_cast<cudaStream_t>(stream);
-  if (v->dist || v->extra) {
-    // key variants: the split kernels (the persistent ones are built without them)
+  if (v->dist || v->extra || t->dev.hist_migrate) {
+    // key variants and history migration: the split kernels (the persistent
+    // ones are built without them)
     if (int rc = pps_build(t, cam, frame, stream)) return rc;
     if (int rc = pps_insert(t, v, n, nullptr, stream)) return rc;
     if (blend)
@@ -686,8 +706,9 @@ int table_for_batch(pps_table* t, size_t n, ViewDesc* vd, int* batch, bool* temp
                     cudaStream_t st) {
   if (int rc = check_table(t)) return rc;
   if (t->state != kClean) return fail(PPS_ESTATE, "a table of a batch is in the middle of a frame");
-  if (t->p.fallback != PPS_FALLBACK_NONE || t->p.hist_evict)
-    return fail(PPS_EINVAL, "batched views take tables without a low-count fallback or eviction");
+  if (t->p.fallback != PPS_FALLBACK_NONE || t->p.hist_evict || t->p.hist_migrate)
+    return fail(PPS_EINVAL,
+                "batched views take tables without a low-count fallback, eviction or migration");
   const size_t ftile = static_cast<size_t>(fused_tile_size());
   if (int rc = ensure_dense(t, (n + ftile - 1) / ftile * ftile, 0, st)) return rc;
   vd->kc = t->kc;

@@ -64,6 +64,10 @@ enum : unsigned int {
 // lines.  The cells themselves live in dense arrays indexed by the cell id:
 //   acc   {sum r, sum g, sum b, count} FP32 (16 B), or int64 sums (32 B, fixed)
 //   info  {slot, home hash, fingerprint, history cell} (16 B)
+//   kw    the cell's quantized key {x~x, x~y, x~z, l' & 0xFF | q(n) << 8}
+//         (16 B, tables whose history follows changes of resolution)
+//   hold  the old value {c r, c g, c b, N} the cell's blend starts from
+//         (16 B, same tables)
 // Ids are handed out per block of vertices: a CTA (or a tile of the split
 // path) owns the id range [block * B, block * B + count[block]), where B is its
 // vertex count, so a frame's cells occupy a few contiguous runs and the
@@ -77,6 +81,8 @@ struct TableDev {
   float4* acc;                // [D] FP32 accumulators (FP32 mode)
   unsigned long long* acc64;  // [D][4] fixed-point accumulators (fixed mode)
   uint4* info;                // [D] {slot, h1, fingerprint, history cell}
+  uint4* kw;                  // [D] quantized keys (hist_migrate)
+  float4* hold;               // [D] old values of the blend (hist_migrate)
   uint32_t* bcount;           // [blocks] cells claimed per id block
   unsigned char* hcells;      // [Th] history cells (temporal tables)
   Ctrl* ctrl;
@@ -90,6 +96,7 @@ struct TableDev {
   int hist_mode;              // 0 none, 1 FP32, 2 FP16
   int neighbors;              // low-count vertices take the 3x3x3 pooled average
   int hist_evict;             // history fingerprints carry a priority (evicting table)
+  int hist_migrate;           // history follows changes of resolution (Sec. 3.4.2)
   uint32_t hist_rank;         // evicting table: this frame's priority (blend epoch)
 };
 

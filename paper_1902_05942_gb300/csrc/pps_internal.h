@@ -62,7 +62,8 @@ cudaError_t launch_query(const KeyConst& kc, const TableDev& t, const VertexPtrs
                          cudaStream_t st);
 cudaError_t launch_keys(const KeyConst& kc, const VertexPtrs& v, size_t n, uint32_t* h_out,
                         uint32_t* f_out, cudaStream_t st);
-cudaError_t launch_blend(const TableDev& t, uint32_t ntiles, float alpha, cudaStream_t st);
+cudaError_t launch_blend(const KeyConst& kc, const TableDev& t, uint32_t ntiles, float alpha,
+                         cudaStream_t st);
 cudaError_t launch_clear(const TableDev& t, uint32_t ntiles, cudaStream_t st);
 // Evicting history: lower every entry's priority by `by` (epoch rebase).
 cudaError_t launch_hist_age(const TableDev& t, uint32_t by, cudaStream_t st);

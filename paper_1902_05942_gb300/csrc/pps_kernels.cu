@@ -141,7 +141,9 @@ struct Batch {
 // a frame that neither blends nor clears slot by slot never reads it.
 // KV: the vertices may carry the key variants (distance, extra word); the
 // persistent kernels are built without them.
-template <int W, bool KV = false>
+// KREC: also keep each new cell's quantized key in t.kw (for the history's
+// changes of resolution).
+template <int W, bool KV = false, bool KREC = false>
 __device__ __forceinline__ Batch<W> insert_batch(const KeyConst& kc, const TableDev& t,
                                                  const VertexPtrs& v, size_t j, size_t end,
                                                  bool vec, uint32_t id_base, uint32_t* claims,
@@ -156,13 +158,24 @@ __device__ __forceinline__ Batch<W> insert_batch(const KeyConst& kc, const Table
   uint32_t h1[W], f[W];
   bool lead[W];
   int of[W];
+  uint4 kr[W];  // KREC: the quantized keys
 #pragma unroll
   for (int q = 0; q < W; ++q) {
     const bool valid = j + q < end;
     Key k{0u, 0u};
-    if (valid)
-      k = vertex_key(kc, PX[q], PY[q], PZ[q], NX[q], NY[q], NZ[q], vertex_id(v, j + q),
-                     v.stream_id, KV ? key_extra(v, j + q) : KeyExtra{});
+    kr[q] = make_uint4(0u, 0u, 0u, 0u);
+    if (valid) {
+      if constexpr (KREC) {
+        const KeyWords w = key_words(kc, PX[q], PY[q], PZ[q], NX[q], NY[q], NZ[q],
+                                     vertex_id(v, j + q), v.stream_id,
+                                     KV ? key_extra(v, j + q) : KeyExtra{});
+        k = key_hash(kc, w);
+        kr[q] = make_uint4(w.X, w.Y, w.Z, (w.L & 0xFFu) | (w.NQ << 8));
+      } else {
+        k = vertex_key(kc, PX[q], PY[q], PZ[q], NX[q], NY[q], NZ[q], vertex_id(v, j + q),
+                       v.stream_id, KV ? key_extra(v, j + q) : KeyExtra{});
+      }
+    }
     h1[q] = k.h1;
     f[q] = k.fp;  // 0 marks an absent vertex (fingerprints are never 0)
     lead[q] = valid;
@@ -256,6 +269,8 @@ __device__ __forceinline__ Batch<W> insert_batch(const KeyConst& kc, const Table
     if (rec && my[q] != kOverflowSlot)
       __stcg(t.info + my[q], claimed[q] ? make_uint4(slot[q], h1[q], f[q], kOverflowSlot)
                                         : make_uint4(kNoSlot, 0u, 0u, kOverflowSlot));
+    if constexpr (KREC)
+      if (claimed[q]) __stcg(t.kw + my[q], kr[q]);
   }
 #pragma unroll
   for (int q = 0; q < W; ++q)
@@ -567,7 +582,7 @@ __device__ __forceinline__ void sweep_slots(const TableDev& t, size_t gid, size_
 }
 
 // ------------------------------------------------------------------ split path
-template <int W>
+template <int W, bool KREC>
 __global__ void __launch_bounds__(kBlock) k_insert(KeyConst kc, TableDev t, VertexPtrs v,
                                                    size_t n, uint32_t* id_out, int vec,
                                                    uint32_t tile_base) {
@@ -582,7 +597,8 @@ __global__ void __launch_bounds__(kBlock) k_insert(KeyConst kc, TableDev t, Vert
     for (int sub = 0; sub < 4; sub += W) {
       const size_t j = tile * kTile + threadIdx.x * 4 + sub;
       if (j < n) {
-        const Batch<W> b = insert_batch<W, true>(kc, t, v, j, n, vec != 0, tix * kTile, &s_claims, c);
+        const Batch<W> b =
+            insert_batch<W, true, KREC>(kc, t, v, j, n, vec != 0, tix * kTile, &s_claims, c);
         if (id_out) {
 #pragma unroll
           for (int q = 0; q < W; ++q)
@@ -656,6 +672,120 @@ __global__ void __launch_bounds__(kBlock) k_blend_sweep(TableDev t, uint32_t nti
       blend_range<4, false>(t, tile * kTile, t.bcount[tile], threadIdx.x, blockDim.x, alpha, n_hovf);
   const unsigned long long h = block_sum(n_hovf);
   if (threadIdx.x == 0 && h) atomicAdd(&t.ctrl->hist_overflow, h);
+}
+
+// Changes in resolution across frames (Sec. 3.4.2), for a cell whose history
+// entry is new this frame; `rec` is the cell's quantized key.  Resolution
+// decreased: the history of its eight finer children (2 x~ + {0,1}^3, level
+// l' - 1, same quantized normal) is added up, sums and counts, giving
+// sum(N_i c_i) / sum(N_i) with count sum(N_i) (FP32, children in the order
+// dx, dy, dz, the last fastest).  Otherwise, resolution increased: its coarser
+// parent (floor(x~ / 2), level l' + 1) passes on its average with count
+// ceil(N / 8).  Read-only probes; an entry claimed during this frame holds
+// N = 0 and counts as absent, so the result is the history as it was before
+// the frame.  Kept out of line: only new entries pay for it.
+__device__ __forceinline__ uint32_t hist_find(const TableDev& t, uint32_t home, uint32_t f) {
+  for (uint32_t p = 0; p < t.max_probes; ++p) {
+    const uint32_t h = (home + p) & t.hmask;
+    const uint32_t w = __ldcg(hist_fp(t, h));
+    if (w == 0u) return kOverflowSlot;
+    if (w == f) return h;
+  }
+  return kOverflowSlot;
+}
+
+__device__ __noinline__ HistRaw migrate_history(const KeyConst& kc, const TableDev& t, uint4 rec) {
+  KeyWords w;
+  w.X = rec.x;
+  w.Y = rec.y;
+  w.Z = rec.z;
+  w.L = static_cast<uint32_t>(static_cast<int32_t>(static_cast<int8_t>(rec.w & 0xFFu)));
+  w.NQ = rec.w >> 8;
+  w.EX = 0u;
+  w.has_ex = false;
+  float sr = 0.f, sg = 0.f, sb = 0.f;
+  uint32_t sn = 0u;
+  for (uint32_t d = 0; d < 8; ++d) {
+    KeyWords c = w;
+    c.X = 2u * w.X + (d >> 2);
+    c.Y = 2u * w.Y + ((d >> 1) & 1u);
+    c.Z = 2u * w.Z + (d & 1u);
+    c.L = w.L - 1u;
+    const Key k = key_hash(kc, c);
+    const uint32_t h = hist_find(t, k.h1 & t.hmask, k.fp);
+    if (h == kOverflowSlot) continue;
+    const HistRaw o = load_hist(t, h);
+    if (o.n == 0u) continue;
+    const float fn = __uint2float_rn(o.n);
+    sr = __fadd_rn(sr, __fmul_rn(fn, o.r));
+    sg = __fadd_rn(sg, __fmul_rn(fn, o.g));
+    sb = __fadd_rn(sb, __fmul_rn(fn, o.b));
+    sn += o.n;
+  }
+  if (sn) {
+    const float fn = __uint2float_rn(sn);
+    return HistRaw{__fdiv_rn(sr, fn), __fdiv_rn(sg, fn), __fdiv_rn(sb, fn), sn};
+  }
+  KeyWords p = w;
+  p.X = static_cast<uint32_t>(static_cast<int32_t>(w.X) >> 1);
+  p.Y = static_cast<uint32_t>(static_cast<int32_t>(w.Y) >> 1);
+  p.Z = static_cast<uint32_t>(static_cast<int32_t>(w.Z) >> 1);
+  p.L = w.L + 1u;
+  const Key k = key_hash(kc, p);
+  const uint32_t h = hist_find(t, k.h1 & t.hmask, k.fp);
+  if (h != kOverflowSlot) {
+    HistRaw o = load_hist(t, h);
+    if (o.n) {
+      o.n = (o.n + 7u) / 8u;
+      return o;
+    }
+  }
+  return HistRaw{0.f, 0.f, 0.f, 0u};
+}
+
+// The blend of a table whose history follows changes of resolution, in two
+// launches so that every migration reads the history as it was before the
+// frame: k_blend_lookup finds or claims each cell's history entry and keeps
+// the value its blend starts from (own, migrated, or none) in t.hold and the
+// entry in info.w; k_blend_apply blends and stores.
+__global__ void __launch_bounds__(kBlock) k_blend_lookup(KeyConst kc, TableDev t, uint32_t ntiles) {
+  unsigned long long n_hovf = 0;
+  for (uint32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const uint32_t base = tile * kTile, count = t.bcount[tile];
+    for (uint32_t k = threadIdx.x; k < count; k += blockDim.x) {
+      const uint32_t d = base + k;
+      const uint4 in = __ldcg(t.info + d);
+      if (in.x == kNoSlot) continue;
+      const uint32_t home = in.y & t.hmask, f = in.z;
+      const uint32_t old = atomicCAS(hist_fp(t, home), 0u, f);
+      const uint32_t h = old == 0u || old == f ? home : hist_probe_rest(t, home, f, 1u);
+      HistRaw hv{0.f, 0.f, 0.f, 0u};
+      if (h == kOverflowSlot) {
+        ++n_hovf;
+      } else {
+        hv = load_hist(t, h);
+        if (hv.n == 0u) hv = migrate_history(kc, t, __ldcg(t.kw + d));
+      }
+      __stcg(t.hold + d, make_float4(hv.r, hv.g, hv.b, __uint_as_float(hv.n)));
+      __stcg(&t.info[d].w, h);
+    }
+  }
+  const unsigned long long s = block_sum(n_hovf);
+  if (threadIdx.x == 0 && s) atomicAdd(&t.ctrl->hist_overflow, s);
+}
+
+__global__ void __launch_bounds__(kBlock) k_blend_apply(TableDev t, uint32_t ntiles, float alpha) {
+  for (uint32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const uint32_t base = tile * kTile, count = t.bcount[tile];
+    for (uint32_t k = threadIdx.x; k < count; k += blockDim.x) {
+      const uint32_t d = base + k;
+      const uint4 in = __ldcg(t.info + d);
+      if (in.x == kNoSlot) continue;
+      const AccRaw a = load_acc(t, d);
+      const float4 o = __ldcg(t.hold + d);
+      blend_store(t, d, in.w, mean_of(t, a), HistRaw{o.x, o.y, o.z, __float_as_uint(o.w)}, alpha);
+    }
+  }
 }
 
 __global__ void __launch_bounds__(kBlock) k_clear_sweep(TableDev t, uint32_t ntiles, int sweep) {
@@ -1051,10 +1181,16 @@ cudaError_t launch_insert(const KeyConst& kc, const TableDev& t, const VertexPtr
   if (n == 0) return cudaSuccess;
   const int grid = split_grid((n + 3) / 4);
   const int vec = vec_inputs(v) ? 1 : 0;
-  if (batch == 2)
-    k_insert<2><<<grid, kBlock, 0, st>>>(kc, t, v, n, id_out, vec, tile_base);
-  else
-    k_insert<4><<<grid, kBlock, 0, st>>>(kc, t, v, n, id_out, vec, tile_base);
+  if (t.hist_migrate) {
+    if (batch == 2)
+      k_insert<2, true><<<grid, kBlock, 0, st>>>(kc, t, v, n, id_out, vec, tile_base);
+    else
+      k_insert<4, true><<<grid, kBlock, 0, st>>>(kc, t, v, n, id_out, vec, tile_base);
+  } else if (batch == 2) {
+    k_insert<2, false><<<grid, kBlock, 0, st>>>(kc, t, v, n, id_out, vec, tile_base);
+  } else {
+    k_insert<4, false><<<grid, kBlock, 0, st>>>(kc, t, v, n, id_out, vec, tile_base);
+  }
   return cudaGetLastError();
 }
 
@@ -1076,10 +1212,16 @@ cudaError_t launch_keys(const KeyConst& kc, const VertexPtrs& v, size_t n, uint3
   return cudaGetLastError();
 }
 
-cudaError_t launch_blend(const TableDev& t, uint32_t ntiles, float alpha, cudaStream_t st) {
+cudaError_t launch_blend(const KeyConst& kc, const TableDev& t, uint32_t ntiles, float alpha,
+                         cudaStream_t st) {
   if (ntiles == 0) return cudaSuccess;
   const uint32_t grid = std::min<uint32_t>(ntiles, static_cast<uint32_t>(sm_count()) * 8);
-  k_blend_sweep<<<grid, kBlock, 0, st>>>(t, ntiles, alpha);
+  if (t.hist_migrate) {
+    k_blend_lookup<<<grid, kBlock, 0, st>>>(kc, t, ntiles);
+    k_blend_apply<<<grid, kBlock, 0, st>>>(t, ntiles, alpha);
+  } else {
+    k_blend_sweep<<<grid, kBlock, 0, st>>>(t, ntiles, alpha);
+  }
   return cudaGetLastError();
 }
 

@@ -41,7 +41,7 @@ class pps_params(ctypes.Structure):
                 ("normal_in_home_hash", _u32), ("lod_min", _i32), ("lod_max", _i32),
                 ("accum_mode", _u32), ("hist_mode", _u32), ("lowcount_threshold", _u32),
                 ("log2_hist_slots", _u32), ("fallback", _u32), ("hist_evict", _u32),
-                ("reserved", _u32 * 1)]
+                ("hist_migrate", _u32), ("reserved", _u32 * 1)]
 
 
 class pps_camera(ctypes.Structure):
@@ -209,18 +209,21 @@ def make_output(out: Dict[str, torch.Tensor], n: int, device=True) -> pps_output
 
 def make_params(cfg, hist_mode: Optional[int] = None, accum_fixed: Optional[bool] = None,
                 log2_hist_slots: Optional[int] = None, fallback: Optional[str] = None,
-                hist_evict: Optional[bool] = None) -> pps_params:
+                hist_evict: Optional[bool] = None,
+                hist_migrate: Optional[bool] = None) -> pps_params:
     """pps_params from a FilterConfig-like object (attribute names as in configs.py)."""
     hm = cfg.hist_mode if hist_mode is None else hist_mode
     fx = cfg.accum_fixed if accum_fixed is None else accum_fixed
     lh = cfg.log2_hist_slots if log2_hist_slots is None else log2_hist_slots
     fb = getattr(cfg, "fallback", "none") if fallback is None else fallback
     ev = getattr(cfg, "hist_evict", False) if hist_evict is None else hist_evict
+    mg = getattr(cfg, "hist_migrate", False) if hist_migrate is None else hist_migrate
     return pps_params(cfg.log2_slots, cfg.max_probes, cfg.voxel_scale, cfg.pixel_angle,
                       int(cfg.jitter), cfg.seed & 0xFFFFFFFF, cfg.hash_seed_home & 0xFFFFFFFF,
                       cfg.hash_seed_fp & 0xFFFFFFFF, int(cfg.normal_in_home_hash), cfg.lod_min,
                       cfg.lod_max, ACCUM_FIXED if fx else ACCUM_FP32, hm,
-                      cfg.lowcount_threshold, lh, FALLBACKS[fb], int(bool(ev)), (_u32 * 1)(0))
+                      cfg.lowcount_threshold, lh, FALLBACKS[fb], int(bool(ev)), int(bool(mg)),
+                      (_u32 * 1)(0))
 
 
 def camera(pos: Sequence[float]) -> pps_camera:
@@ -457,9 +460,9 @@ class Table:
 
     def __init__(self, cfg, hist_mode: Optional[int] = None, accum_fixed: Optional[bool] = None,
                  log2_hist_slots: Optional[int] = None, fallback: Optional[str] = None,
-                 hist_evict: Optional[bool] = None):
+                 hist_evict: Optional[bool] = None, hist_migrate: Optional[bool] = None):
         self.params = make_params(cfg, hist_mode, accum_fixed, log2_hist_slots, fallback,
-                                  hist_evict)
+                                  hist_evict, hist_migrate)
         self.handle = pps_create(self.params)
         self.T = 1 << self.params.log2_slots
         self.fixed = self.params.accum_mode == ACCUM_FIXED

@@ -126,3 +126,15 @@ def test_eviction_needs_a_history():
     h = ctypes.c_void_p()
     assert L.pps_create(ctypes.byref(h), ctypes.byref(p)) == pps.PPS_EINVAL
     assert "hist_evict" in pps.last_error()
+
+
+@pytest.mark.parametrize("bad", [dict(hist_migrate=2), dict(hist_migrate=1, hist_mode=0),
+                                 dict(hist_migrate=1, hist_mode=1, hist_evict=1)])
+def test_migration_needs_a_plain_history(bad):
+    pps, L = _lib()
+    p = _params(pps)
+    for k, v in bad.items():
+        setattr(p, k, v)
+    h = ctypes.c_void_p()
+    assert L.pps_create(ctypes.byref(h), ctypes.byref(p)) == pps.PPS_EINVAL
+    assert "hist_migrate" in pps.last_error()
