@@ -55,6 +55,8 @@ struct pps_table {
   size_t D = 0;              // capacity of the dense cell arrays
   uint32_t* gstash = nullptr;
   size_t gstash_cap = 0;
+  uint32_t* split_ids = nullptr;  // pps_filter on the split kernels: each vertex's cell id
+  size_t split_ids_cap = 0;
   void* stage = nullptr;  // pps_filter_host device staging
   size_t stage_cap = 0;
   unsigned long long* scratch_u64 = nullptr;  // 1 word for occupancy counting
@@ -253,6 +255,7 @@ void free_all(pps_table* t) {
   cudaFree(t->dev.hcells);
   cudaFree(t->dev.ctrl);
   cudaFree(t->gstash);
+  cudaFree(t->split_ids);
   cudaFree(t->stage);
   cudaFree(t->scratch_u64);
   cudaFree(t->fb);
@@ -523,12 +526,23 @@ int pps_filter(pps_table* t, const pps_camera* cam, uint32_t frame, const pps_ve
   const cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (v->dist || v->extra || t->dev.hist_migrate) {
     // key variants and history migration: the split kernels (the persistent
-    // ones are built without them)
+    // ones are built without them); the insert's cell ids spare the lookup
+    // its keys and probes
+    if (t->split_ids_cap < n) {
+      cudaFree(t->split_ids);
+      t->split_ids = nullptr;
+      t->split_ids_cap = 0;
+      if (cudaMalloc(reinterpret_cast<void**>(&t->split_ids), n * sizeof(uint32_t)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(PPS_ENOMEM, "pps_filter: cell-id scratch allocation failed");
+      }
+      t->split_ids_cap = n;
+    }
     if (int rc = pps_build(t, cam, frame, stream)) return rc;
-    if (int rc = pps_insert(t, v, n, nullptr, stream)) return rc;
+    if (int rc = pps_insert(t, v, n, t->split_ids, stream)) return rc;
     if (blend)
       if (int rc = pps_blend(t, alpha, stream)) return rc;
-    return pps_query(t, v, n, nullptr, out, stream);
+    return pps_query(t, v, n, t->split_ids, out, stream);
   }
   if (!t->coarse) return filter_one(t, cam, frame, v, n, blend, alpha, to_dev(out), st);
   // multi-level: both resolutions, then the choice per vertex

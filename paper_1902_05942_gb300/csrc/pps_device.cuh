@@ -42,13 +42,14 @@ struct Ctrl {
   unsigned long long overflow_vertices;
   unsigned long long vertices;
   unsigned long long hist_overflow;
-  unsigned long long tile_next;  // persistent kernel: next vertex tile to hand out
+  unsigned long long tile_next;   // persistent kernel: next vertex tile to hand out
+  unsigned long long blend_next;  // persistent kernel: next tile whose cells to blend
   unsigned int error;
   unsigned int bar_count;
   unsigned int bar_gen;
-  unsigned int pad[5];
+  unsigned int pad[3];
 };
-constexpr size_t kCtrlFrameBytes = 5 * sizeof(unsigned long long);  // reset per frame
+constexpr size_t kCtrlFrameBytes = 6 * sizeof(unsigned long long);  // reset per frame
 
 enum : unsigned int {
   kErrBarrierTimeout = 1u,

@@ -897,7 +897,10 @@ __global__ void __launch_bounds__(kFusedBlock, W == 4 ? 1 : 2) k_fused(FusedArgs
       }
     }
     __syncthreads();
-    if (threadIdx.x == 0) ++s_taken;
+    if (threadIdx.x == 0) {
+      if (TEMPORAL && a.blend) __stcg(t.bcount + tile, s_claims[k]);  // any CTA may blend it
+      ++s_taken;
+    }
   }
   {
     const unsigned long long o = block_sum(static_cast<unsigned long long>(c.ovf));
@@ -911,13 +914,23 @@ __global__ void __launch_bounds__(kFusedBlock, W == 4 ? 1 : 2) k_fused(FusedArgs
   if (!grid_barrier(t.ctrl, gridDim.x)) return;
   const uint32_t taken = s_taken;
 
-  // Phase B: temporal blend of the cells this CTA's tiles created.
+  // Phase B: temporal blend of the frame's cells, tile by tile from a second
+  // counter, so that CTAs whose tiles created few cells take more.
   const bool blended = TEMPORAL && a.blend;
   if (blended) {
     unsigned long long n_hovf = 0;
-    for (uint32_t k = 0; k < taken; ++k)
-      blend_range<W, EVICT>(t, s_tile[k] * static_cast<uint32_t>(kFusedTile), s_claims[k],
+    for (;;) {
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        const unsigned long long b = atomicAdd(&t.ctrl->blend_next, 1ull);
+        s_cur = b < ntiles ? static_cast<uint32_t>(b) : ntiles;
+      }
+      __syncthreads();
+      const uint32_t tile = s_cur;
+      if (tile >= ntiles) break;
+      blend_range<W, EVICT>(t, tile * static_cast<uint32_t>(kFusedTile), __ldcg(t.bcount + tile),
                             threadIdx.x, blockDim.x, a.alpha, n_hovf);
+    }
     const unsigned long long h = block_sum(n_hovf);
     if (threadIdx.x == 0 && h) atomicAdd(&t.ctrl->hist_overflow, h);
     if (!grid_barrier(t.ctrl, gridDim.x)) return;
