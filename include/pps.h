@@ -514,6 +514,24 @@ int pps_mlp_gradient(pps_mlp *m, const pps_vertices *v, const float *tr, const f
                      const float *tb, const int32_t *idx, uint32_t batch, float *grad_out,
                      void *stream);
 
+/*
+ * pps_selftest_wait: exercise one of the library's bounded device waits on a
+ * condition that never comes true, so that callers can check that a stuck
+ * wait ends with an error status instead of a hang.
+ *   kind 0  the persistent kernels' grid barrier, waiting for one CTA more
+ *           than the launch has (the barrier of the fused filter);
+ *   kind 1  the tensor-core kernels' mbarrier wait, on a phase that no
+ *           operation completes (the learned fallback's kernels).
+ * The wait gives up after limit_us microseconds (1 .. 2,000,000) and the
+ * kernel returns.  *error_word (host) receives the device error word the
+ * kernel left: for kind 0 the filter's barrier-timeout bit (1), for kind 1
+ * the learned fallback's wait-timeout bit (1); 0 would mean the wait did not
+ * give up.  Synchronous on the current device; uses its own device memory.
+ * PPS_EINVAL for a bad kind, limit or NULL error_word (checked before any
+ * CUDA call).
+ */
+int pps_selftest_wait(int kind, uint32_t limit_us, uint32_t *error_word);
+
 #ifdef __cplusplus
 }
 #endif

@@ -661,7 +661,8 @@ __device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int* p) {
 // the others wait for the generation to change.  The wait is bounded (about
 // two seconds of wall time): on timeout the CTA raises kErrBarrierTimeout in
 // the device error word and every CTA returns false, so the launch ends.
-__device__ __forceinline__ bool grid_barrier(Ctrl* c, unsigned int nblocks) {
+__device__ __forceinline__ bool grid_barrier(Ctrl* c, unsigned int nblocks,
+                                             unsigned long long limit_ns = 2000000000ull) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -680,7 +681,7 @@ __device__ __forceinline__ bool grid_barrier(Ctrl* c, unsigned int nblocks) {
           ok = 0;
           break;
         }
-        if (globaltimer_ns() - t0 > 2000000000ull) {
+        if (globaltimer_ns() - t0 > limit_ns) {
           atomicOr(&c->error, kErrBarrierTimeout);
           ok = 0;
           break;

@@ -86,6 +86,9 @@ bool aligned16(const void* p);
 
 int record_error(int code, const char* msg);  // message for pps_last_error()
 
+// Self-test of the tensor-core kernels' bounded mbarrier wait (pps_mlp.cu).
+cudaError_t launch_selftest_mbar(unsigned long long limit_ns, unsigned int* err, cudaStream_t st);
+
 }  // namespace pps
 
 struct pps_table;

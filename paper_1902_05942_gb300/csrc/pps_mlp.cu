@@ -203,8 +203,10 @@ __device__ __forceinline__ void fence_smem_async() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
-// Wait for the mbarrier phase `parity`; gives up after about two seconds.
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
+// Wait for the mbarrier phase `parity`; gives up after `limit_ns` (two
+// seconds unless given).
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity,
+                                          unsigned long long limit_ns = 2000000000ull) {
   const unsigned long long t0 = globaltimer_ns();
   for (;;) {
     uint32_t done;
@@ -215,7 +217,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
         : "r"(mbar), "r"(parity)
         : "memory");
     if (done) return true;
-    if (globaltimer_ns() - t0 > 2000000000ull) return false;
+    if (globaltimer_ns() - t0 > limit_ns) return false;
   }
 }
 
@@ -744,7 +746,25 @@ __global__ void k_mlp_adam(Dev d, float lr, float b1, float b2, float eps, float
   if (dst >= 0) d.wb[dst] = __float2bfloat16_rn(w);
 }
 
+// Self-test of the bounded wait: an mbarrier that nothing completes; the wait
+// gives up after `limit_ns` and the kernel reports it in *err (bit 0).
+__global__ void k_selftest_mbar(unsigned long long limit_ns, unsigned int* err) {
+  __shared__ alignas(8) unsigned long long mbar;
+  const uint32_t a = smem_u32(&mbar);
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(a) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && !tc::mbar_wait(a, 0u, limit_ns)) atomicOr(err, 1u);
+}
+
 }  // namespace mlp
+
+cudaError_t launch_selftest_mbar(unsigned long long limit_ns, unsigned int* err, cudaStream_t st) {
+  mlp::k_selftest_mbar<<<1, 32, 0, st>>>(limit_ns, err);
+  return cudaGetLastError();
+}
 }  // namespace pps
 
 // ---------------------------------------------------------------- C ABI

@@ -126,6 +126,7 @@ SIGNATURES = {
                          ctypes.c_int),
     "pps_batch_run": ([_vp, ctypes.POINTER(pps_camera), _u32, _vp], ctypes.c_int),
     "pps_batch_destroy": ([_vp], ctypes.c_int),
+    "pps_selftest_wait": ([ctypes.c_int, _u32, ctypes.POINTER(_u32)], ctypes.c_int),
     "pps_bench_rate": ([ctypes.c_int, ctypes.c_size_t, ctypes.c_size_t, _vp, _vp,
                         ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
 }
@@ -233,6 +234,15 @@ def camera(pos: Sequence[float]) -> pps_camera:
 # ---------------------------------------------------------------- C-named calls
 def pps_version() -> str:
     return lib().pps_version().decode()
+
+
+def pps_selftest_wait(kind: int, limit_us: int) -> int:
+    """Run one bounded device wait on a condition that never comes true
+    (0: grid barrier, 1: tensor-core mbarrier) and return the device error
+    word it left (1 when the wait gave up as it should)."""
+    w = _u32(0)
+    _check(lib().pps_selftest_wait(int(kind), int(limit_us), ctypes.byref(w)))
+    return int(w.value)
 
 
 def pps_create(params: pps_params) -> int:

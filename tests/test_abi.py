@@ -138,3 +138,10 @@ def test_migration_needs_a_plain_history(bad):
     h = ctypes.c_void_p()
     assert L.pps_create(ctypes.byref(h), ctypes.byref(p)) == pps.PPS_EINVAL
     assert "hist_migrate" in pps.last_error()
+
+
+@pytest.mark.parametrize("kind, limit", [(2, 1000), (-1, 1000), (0, 0), (1, 2000001)])
+def test_selftest_wait_checks_its_arguments(kind, limit):
+    pps, L = _lib()
+    w = ctypes.c_uint32(7)
+    assert L.pps_selftest_wait(kind, limit, ctypes.byref(w)) == pps.PPS_EINVAL
