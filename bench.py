@@ -238,6 +238,12 @@ def run_ours(args):
                                          hist_evict=True, log2_hist_slots=23)
         hvariants["migrate"] = history_leg(frames, cfg, calls, fsteps, args.warmup,
                                            hist_migrate=True)
+    precision = {}
+    if not args.no_fallbacks:
+        precision["fixed_point_plain"] = history_leg(frames, cfg, calls, fsteps, args.warmup,
+                                                     blend=0, hist_mode=0, accum_fixed=True)
+        precision["fp16_history"] = history_leg(frames, cfg, calls, fsteps, args.warmup,
+                                                hist_mode=2)
     ms, job_n = reduce_ranks(ms, float(total_n), dev)
     value = job_n / (ms / 1e3)
     ms_step = ms / args.steps
@@ -319,6 +325,10 @@ def run_ours(args):
                 "workload": "the headline temporal HD frames with an evicting history of "
                             "2^23 cells (evict) or a history that follows changes of "
                             "resolution (migrate)", **hvariants}
+        if precision:
+            line["precision"] = {
+                "workload": "the headline HD frames: fixed-point (int64) accumulation without "
+                            "history, and the temporal frame with an FP16 history", **precision}
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(frames[0], w, args.cpu_sample)
         if not args.no_mlp:
@@ -408,11 +418,12 @@ def fallback_leg(frames, cfg, calls, steps, warmup, fallback, status):
             "fallback_share": share}
 
 
-def history_leg(frames, cfg, calls, steps, warmup, **table_kw):
-    """The headline workload with a history variant: "evict" = an evicting
-    history of 2^23 cells (Sec. 3.4.3), "migrate" = the history following
-    changes of resolution (Sec. 3.4.2; split kernels, two blend launches).
-    Same timing as the headline."""
+def history_leg(frames, cfg, calls, steps, warmup, blend=1, **table_kw):
+    """The headline workload with a table variant, same timing as the
+    headline: "evict" = an evicting history of 2^23 cells (Sec. 3.4.3),
+    "migrate" = the history following changes of resolution (Sec. 3.4.2;
+    split kernels, two blend launches); the precision modes: fixed-point
+    accumulation (plain frame) and an FP16 history."""
     import ctypes
     import torch
     from paper_1902_05942_gb300 import pps
@@ -422,8 +433,8 @@ def history_leg(frames, cfg, calls, steps, warmup, **table_kw):
 
     def step(i):
         cam, vs, n, os_ = calls[i % len(calls)]
-        rc = L.pps_filter(tab.handle, ctypes.byref(cam), i, ctypes.byref(vs), n, 1, cfg.alpha,
-                          ctypes.byref(os_), stream.cuda_stream)
+        rc = L.pps_filter(tab.handle, ctypes.byref(cam), i, ctypes.byref(vs), n, blend,
+                          cfg.alpha, ctypes.byref(os_), stream.cuda_stream)
         if rc:
             raise pps.PPSError(rc, pps.last_error())
         return n
