@@ -57,6 +57,8 @@ struct pps_table {
   size_t gstash_cap = 0;
   uint32_t* split_ids = nullptr;  // pps_filter on the split kernels: each vertex's cell id
   size_t split_ids_cap = 0;
+  uint32_t* neigh_q = nullptr;  // neighborhood search: queue of low-count vertices
+  size_t neigh_q_cap = 0;
   void* stage = nullptr;  // pps_filter_host device staging
   size_t stage_cap = 0;
   unsigned long long* scratch_u64 = nullptr;  // 1 word for occupancy counting
@@ -256,6 +258,7 @@ void free_all(pps_table* t) {
   cudaFree(t->dev.ctrl);
   cudaFree(t->gstash);
   cudaFree(t->split_ids);
+  cudaFree(t->neigh_q);
   cudaFree(t->stage);
   cudaFree(t->scratch_u64);
   cudaFree(t->fb);
@@ -502,10 +505,20 @@ int filter_one(pps_table* t, const pps_camera* cam, uint32_t frame, const pps_ve
     }
     t->gstash_cap = stash_need;
   }
+  if (t->dev.neighbors && t->neigh_q_cap < n) {
+    cudaFree(t->neigh_q);
+    t->neigh_q = nullptr;
+    t->neigh_q_cap = 0;
+    if (cudaMalloc(reinterpret_cast<void**>(&t->neigh_q), n * sizeof(uint32_t)) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(PPS_ENOMEM, "pps_filter: neighborhood queue allocation failed");
+    }
+    t->neigh_q_cap = n;
+  }
   if (blend)
     if (int rc = next_epoch(t, st)) return rc;
   PPS_CUDA(pps::launch_fused(t->kc, t->dev, to_dev(v), n, out, temporal(t), blend != 0, alpha,
-                             plan, t->gstash, st));
+                             plan, t->gstash, t->neigh_q, st));
   t->state = kClean;
   return PPS_OK;
 }

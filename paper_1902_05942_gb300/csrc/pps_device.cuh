@@ -44,12 +44,13 @@ struct Ctrl {
   unsigned long long hist_overflow;
   unsigned long long tile_next;   // persistent kernel: next vertex tile to hand out
   unsigned long long blend_next;  // persistent kernel: next tile whose cells to blend
+  unsigned long long neigh_count;  // persistent kernel: low-count vertices queued for the search
   unsigned int error;
   unsigned int bar_count;
   unsigned int bar_gen;
-  unsigned int pad[3];
+  unsigned int pad[1];
 };
-constexpr size_t kCtrlFrameBytes = 6 * sizeof(unsigned long long);  // reset per frame
+constexpr size_t kCtrlFrameBytes = 7 * sizeof(unsigned long long);  // reset per frame
 
 enum : unsigned int {
   kErrBarrierTimeout = 1u,

@@ -78,7 +78,7 @@ cudaError_t plan_fused(size_t n, bool temporal, int batch, FusedPlan* plan, bool
                        bool neigh = false);
 cudaError_t launch_fused(const KeyConst& kc, const TableDev& t, const VertexPtrs& v, size_t n,
                          const OutPtrs& o, bool temporal, bool blend, float alpha,
-                         const FusedPlan& plan, uint32_t* gstash, cudaStream_t st);
+                         const FusedPlan& plan, uint32_t* gstash, uint32_t* nq, cudaStream_t st);
 
 int tile_size();        // vertices (and cell ids) per tile of the split path
 int fused_tile_size();  // vertices (and cell ids) per tile of the persistent kernel

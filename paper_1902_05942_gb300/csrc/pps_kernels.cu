@@ -303,8 +303,8 @@ struct Result {
 // fixed-point sums with one rounding at the end); after a blend it pools the
 // blended values weighted by their counts N.  Cells are visited in a fixed
 // order (dx, dy, dz each -1, 0, +1, dz fastest), each found by a read-only
-// probe.  Kept out of line: only low-count vertices pay for it.
-__device__ __noinline__ Result neighbor_pool(const KeyConst& kc, const TableDev& t,
+// probe.  Inlined into k_neighbors; the split lookup calls it out of line.
+__device__ __forceinline__ Result neighbor_pool_inl(const KeyConst& kc, const TableDev& t,
                                              const VertexPtrs& v, size_t j, bool blended,
                                              Result own) {
   const KeyWords w0 =
@@ -385,6 +385,14 @@ __device__ __noinline__ Result neighbor_pool(const KeyConst& kc, const TableDev&
   return r;
 }
 
+// The same out of line, for the split lookup (k_query), whose other work
+// should not pay the search's registers.
+__device__ __noinline__ Result neighbor_pool(const KeyConst& kc, const TableDev& t,
+                                             const VertexPtrs& v, size_t j, bool blended,
+                                             Result own) {
+  return neighbor_pool_inl(kc, t, v, j, blended, own);
+}
+
 // Vertex j with cell `id`: if its cell is low-count, replace its outputs by
 // the neighborhood-search result.
 __device__ __forceinline__ void neighbors_of_vertex(const KeyConst& kc, const TableDev& t,
@@ -407,7 +415,7 @@ __device__ __forceinline__ void neighbors_of_vertex(const KeyConst& kc, const Ta
 __device__ __forceinline__ void neighbors_of_queued(const KeyConst& kc, const TableDev& t,
                                                     const VertexPtrs& v, const OutPtrs& o,
                                                     uint32_t j, bool blended) {
-  const Result r = neighbor_pool(kc, t, v, j, blended, Result{o.r[j], o.g[j], o.b[j], 0u, 1});
+  const Result r = neighbor_pool_inl(kc, t, v, j, blended, Result{o.r[j], o.g[j], o.b[j], 0u, 1});
   o.r[j] = r.r;
   o.g[j] = r.g;
   o.b[j] = r.b;
@@ -788,6 +796,16 @@ __global__ void __launch_bounds__(kBlock) k_blend_apply(TableDev t, uint32_t nti
   }
 }
 
+// Neighborhood search of the low-count vertices that the persistent kernel
+// queued, one per thread.
+__global__ void __launch_bounds__(kBlock) k_neighbors(KeyConst kc, TableDev t, VertexPtrs v,
+                                                      OutPtrs o, const uint32_t* nq, int blended) {
+  const unsigned long long cnt = __ldcg(&t.ctrl->neigh_count);
+  for (unsigned long long i = blockIdx.x * static_cast<unsigned long long>(blockDim.x) + threadIdx.x;
+       i < cnt; i += static_cast<unsigned long long>(gridDim.x) * blockDim.x)
+    neighbors_of_queued(kc, t, v, o, __ldcs(nq + i), blended != 0);
+}
+
 __global__ void __launch_bounds__(kBlock) k_clear_sweep(TableDev t, uint32_t ntiles, int sweep) {
   for (uint32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x)
     clear_range(t, tile * kTile, t.bcount[tile], threadIdx.x, blockDim.x, sweep != 0);
@@ -822,6 +840,17 @@ __global__ void __launch_bounds__(kBlock) k_count_nonzero(const unsigned char* b
   if (threadIdx.x == 0 && s) atomicAdd(out, s);
 }
 
+// Empty the cells of the persistent kernel's tiles (kFusedTile ids each), for
+// the kernel variant that leaves them to a later launch.
+__global__ void __launch_bounds__(kBlock) k_clear_fused(TableDev t, uint32_t ntiles, int sweep) {
+  for (uint32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x)
+    clear_range(t, tile * static_cast<uint32_t>(kFusedTile), __ldcg(t.bcount + tile), threadIdx.x,
+                blockDim.x, sweep != 0);
+  if (sweep)
+    sweep_slots(t, blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x,
+                static_cast<size_t>(gridDim.x) * blockDim.x);
+}
+
 // ------------------------------------------------------------------ fused path
 // Next tile of the frame's tile counter (ntiles once all are taken).
 __device__ __forceinline__ uint32_t claim_tile(Ctrl* ctrl, uint32_t ntiles) {
@@ -839,7 +868,8 @@ struct FusedArgs {
   uint32_t* gstash;    // global stash (indexed by vertex) when it does not fit on chip
   float alpha;
   int vec, ovec, blend;
-  int sweep;  // zero the whole slot table at the end instead of slot by slot
+  int sweep;     // zero the whole slot table at the end instead of slot by slot
+  uint32_t* nq;  // neighborhood search: the queue of low-count vertices
 };
 
 // The persistent kernel.  Phase A hands out tiles of kFusedTile consecutive
@@ -898,7 +928,8 @@ __global__ void __launch_bounds__(kFusedBlock, W == 4 ? 1 : 2) k_fused(FusedArgs
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-      if (TEMPORAL && a.blend) __stcg(t.bcount + tile, s_claims[k]);  // any CTA may blend it
+      // for the blend, which any CTA may take, and for the separate clear
+      if ((TEMPORAL && a.blend) || NEIGH) __stcg(t.bcount + tile, s_claims[k]);
       ++s_taken;
     }
   }
@@ -955,15 +986,13 @@ __global__ void __launch_bounds__(kFusedBlock, W == 4 ? 1 : 2) k_fused(FusedArgs
       }
     }
   }
-  // Neighborhood search for this CTA's low-count vertices (the table is only
-  // read from phase C on, so no barrier is needed before it).  A separate
-  // kernel variant, so that the plain one carries no call.
-  // Low-count vertices are rare and scattered, so each warp first collects
-  // them in a queue of its own and runs the search 32 at a time, one per lane.
+  // Neighborhood search: this kernel variant only queues its low-count
+  // vertices (one atomic per warp); k_neighbors then searches the whole queue
+  // at full occupancy and k_clear_fused empties the cells, so that the
+  // irregular searches neither unbalance the persistent CTAs nor cost the
+  // persistent kernel registers.
   if constexpr (NEIGH) {
-    __shared__ uint32_t s_nq[kFusedBlock / 32][64];
-    const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
-    uint32_t qn = 0;
+    const int lane = threadIdx.x & 31;
     for (uint32_t k = 0; k < taken; ++k) {
       const size_t t0 = static_cast<size_t>(s_tile[k]) * kFusedTile;
       const size_t end = min(a.n, t0 + kFusedTile);
@@ -977,21 +1006,15 @@ __global__ void __launch_bounds__(kFusedBlock, W == 4 ? 1 : 2) k_fused(FusedArgs
                 value_of(t, load_value(t, id, blended), blended).n < t.lowcount;
         }
         const unsigned mask = __ballot_sync(0xFFFFFFFFu, low);
-        if (low) s_nq[wq][qn + __popc(mask & ((1u << lane) - 1u))] = static_cast<uint32_t>(j);
-        qn += __popc(mask);
-        __syncwarp();
-        if (qn >= 32) {
-          neighbors_of_queued(a.kc, t, a.v, a.o, s_nq[wq][lane], blended);
-          __syncwarp();
-          const uint32_t moved = lane + 32 < qn ? s_nq[wq][lane + 32] : 0u;
-          __syncwarp();
-          if (lane + 32 < qn) s_nq[wq][lane] = moved;
-          qn -= 32;
-          __syncwarp();
+        if (mask) {
+          unsigned long long b0 = 0ull;
+          if (lane == 0) b0 = atomicAdd(&t.ctrl->neigh_count, static_cast<unsigned long long>(__popc(mask)));
+          b0 = __shfl_sync(0xFFFFFFFFu, b0, 0);
+          if (low) a.nq[b0 + __popc(mask & ((1u << lane) - 1u))] = static_cast<uint32_t>(j);
         }
       }
     }
-    if (lane < qn) neighbors_of_queued(a.kc, t, a.v, a.o, s_nq[wq][lane], blended);
+    return;
   }
   if (!grid_barrier(t.ctrl, gridDim.x)) return;
 
@@ -1395,7 +1418,7 @@ cudaError_t plan_fused(size_t n, bool temporal, int batch, FusedPlan* plan, bool
 
 cudaError_t launch_fused(const KeyConst& kc, const TableDev& t, const VertexPtrs& v, size_t n,
                          const OutPtrs& o, bool temporal, bool blend, float alpha,
-                         const FusedPlan& plan, uint32_t* gstash, cudaStream_t st) {
+                         const FusedPlan& plan, uint32_t* gstash, uint32_t* nq, cudaStream_t st) {
   FusedArgs a;
   a.kc = kc;
   a.t = t;
@@ -1409,9 +1432,19 @@ cudaError_t launch_fused(const KeyConst& kc, const TableDev& t, const VertexPtrs
   a.ovec = vec_outputs(o) ? 1 : 0;
   a.blend = blend ? 1 : 0;
   a.sweep = sweep_pays(t, n) ? 1 : 0;
+  a.nq = nq;
   void* args[] = {&a};
-  return cudaLaunchCooperativeKernel(fused_kernel(temporal, plan.batch, plan.evict, plan.neigh),
-                                     dim3(plan.grid), dim3(plan.block), args, plan.smem, st);
+  cudaError_t e = cudaLaunchCooperativeKernel(
+      fused_kernel(temporal, plan.batch, plan.evict, plan.neigh), dim3(plan.grid), dim3(plan.block),
+      args, plan.smem, st);
+  if (e != cudaSuccess || !plan.neigh) return e;
+  // the queued neighborhood searches, then the clear the persistent kernel left
+  const int sms = sm_count();
+  k_neighbors<<<sms * 8, kBlock, 0, st>>>(kc, t, v, o, nq, blend ? 1 : 0);
+  const uint32_t ntiles = static_cast<uint32_t>((n + kFusedTile - 1) / kFusedTile);
+  k_clear_fused<<<std::min<uint32_t>(ntiles, static_cast<uint32_t>(sms) * 8), kBlock, 0, st>>>(
+      t, ntiles, a.sweep);
+  return cudaGetLastError();
 }
 
 bool vec_inputs_host(const VertexPtrs& v) { return vec_inputs(v); }

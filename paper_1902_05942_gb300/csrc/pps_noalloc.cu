@@ -164,7 +164,7 @@ extern "C" int pps_filter_noalloc(const pps_params* p, const pps_camera* cam, ui
   e = pps::plan_fused(n, false, 2, &plan);
   if (e == cudaSuccess)
     e = pps::launch_fused(kc, t, dv, n, dout, false, false, 0.0f, plan,
-                          reinterpret_cast<uint32_t*>(base + kOffStash), st);
+                          reinterpret_cast<uint32_t*>(base + kOffStash), nullptr, st);
   if (e != cudaSuccess)
     return noalloc_fail(PPS_ECUDA, std::string("pps_filter_noalloc: ") + cudaGetErrorString(e));
   return PPS_OK;
