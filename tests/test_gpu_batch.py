@@ -87,3 +87,52 @@ def test_batch_rejects_a_table_in_the_middle_of_a_frame():
         pps.Batch([(tab, d, pps.empty_output(d["px"].numel(), "cuda"))])
     assert e.value.code == pps.PPS_ESTATE
     tab.close()
+
+
+def test_full_size_batch_matches_one_call_per_view():
+    """The batched configuration at full size (8 views of uneven resolution,
+    ~37 M vertices) in the launch configuration bench.py times: one persistent
+    launch replayed from a CUDA graph.  Against each view filtered on its own
+    (pps_filter, whose parity with the oracle is tested elsewhere): counts
+    bit-exact, values within twice the FP32 summation bar (both sides add in
+    an unspecified order).  Vertices that overflowed their probe window on
+    either side are left out: which keys overflow depends on the order of
+    insertion (they must be a tiny share)."""
+    w = configs.batched()
+    views = []
+    for spec in w.streams:
+        v = scene.trace_stream(spec, 0, "cuda")
+        views.append(({k: v[k] for k in scene.STREAMS}, tuple(spec.view.eye)))
+    total = sum(v["px"].numel() for v, _ in views)
+    assert total > 30_000_000
+    outs = [pps.empty_output(v["px"].numel(), "cuda") for v, _ in views]
+    tabs = []
+    for cfg in w.filters:
+        t = pps.Table(cfg)
+        t.tune(2)
+        tabs.append(t)
+    b = pps.Batch([(tabs[i], views[i][0], outs[i]) for i in range(len(views))])
+    cams = [eye for _, eye in views]
+    for f in range(2):
+        b.run(cams, f)
+    torch.cuda.synchronize()
+    overflowed = 0
+    for i, (v, eye) in enumerate(views):
+        t = pps.Table(w.filters[i])
+        t.tune(2)
+        ref = t.filter(v, eye, 1)
+        torch.cuda.synchronize()
+        keep = (ref["status"] != 2) & (outs[i]["status"] != 2)
+        overflowed += int((~keep).sum().item())
+        assert torch.equal(outs[i]["count"][keep], ref["count"][keep]), i
+        n = ref["count"][keep].double()
+        tol = 2 * torch.clamp((n + 1) * 2.0 ** -24, min=1e-5)
+        for c in "rgb":
+            got, exp = outs[i][c][keep].double(), ref[c][keep].double()
+            rel = (got - exp).abs() / exp.abs()
+            assert bool((rel <= tol).all()), (i, c, float(rel.max()))
+        t.close()
+    assert overflowed <= 1e-4 * total, overflowed
+    b.close()
+    for t in tabs:
+        t.close()
