@@ -852,6 +852,15 @@ __global__ void __launch_bounds__(kBlock) k_clear_fused(TableDev t, uint32_t nti
 }
 
 // ------------------------------------------------------------------ fused path
+// Offset in its tile of the first of the W vertices a thread takes in
+// sub-batch `sub` (0, W, ..): sub-batch k covers the k-th run of
+// kFusedBlock * W vertices, W consecutive ones per thread, so that each
+// warp's loads and stores of a stream are one contiguous run.
+template <int W>
+__device__ __forceinline__ uint32_t fused_offset(int sub) {
+  return static_cast<uint32_t>(sub / W) * (kFusedBlock * W) + threadIdx.x * W;
+}
+
 // Next tile of the frame's tile counter (ntiles once all are taken).
 __device__ __forceinline__ uint32_t claim_tile(Ctrl* ctrl, uint32_t ntiles) {
   const unsigned long long k = atomicAdd(&ctrl->tile_next, 1ull);
@@ -917,7 +926,7 @@ __global__ void __launch_bounds__(kFusedBlock, W == 4 ? 1 : 2) k_fused(FusedArgs
     uint32_t* stash = a.gstash ? a.gstash + t0 : s_stash + static_cast<size_t>(k) * kFusedTile;
 #pragma unroll 1
     for (int sub = 0; sub < 4; sub += W) {
-      const size_t j = t0 + threadIdx.x * 4 + sub;
+      const size_t j = t0 + fused_offset<W>(sub);
       if (j < end) {
         const Batch<W> b = insert_batch<W>(a.kc, t, a.v, j, end, vec, static_cast<uint32_t>(t0),
                                            &s_claims[k], c,
@@ -975,7 +984,7 @@ __global__ void __launch_bounds__(kFusedBlock, W == 4 ? 1 : 2) k_fused(FusedArgs
     const uint32_t* stash = a.gstash ? a.gstash + t0 : s_stash + static_cast<size_t>(k) * kFusedTile;
 #pragma unroll 1
     for (int sub = 0; sub < 4; sub += W) {
-      const size_t j = t0 + threadIdx.x * 4 + sub;
+      const size_t j = t0 + fused_offset<W>(sub);
       if (j < end) {
         uint32_t id[W];
 #pragma unroll
@@ -1088,7 +1097,7 @@ __global__ void __launch_bounds__(kFusedBlock, W == 4 ? 1 : 2) k_fused_multi(Mul
     Counters c;
 #pragma unroll 1
     for (int sub = 0; sub < 4; sub += W) {
-      const size_t j = t0 + threadIdx.x * 4 + sub;
+      const size_t j = t0 + fused_offset<W>(sub);
       if (j < end) {
         const Batch<W> b = insert_batch<W>(s_vd.kc, s_vd.t, s_vd.v, j, end, s_vd.vec != 0,
                                            static_cast<uint32_t>(t0), &s_claims[k], c);
@@ -1145,7 +1154,7 @@ __global__ void __launch_bounds__(kFusedBlock, W == 4 ? 1 : 2) k_fused_multi(Mul
     const bool blended = TEMPORAL && s_vd.blended;
 #pragma unroll 1
     for (int sub = 0; sub < 4; sub += W) {
-      const size_t j = t0 + threadIdx.x * 4 + sub;
+      const size_t j = t0 + fused_offset<W>(sub);
       if (j < end) {
         uint32_t id[W];
 #pragma unroll
