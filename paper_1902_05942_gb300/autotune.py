@@ -31,6 +31,18 @@ def _time(fn, reps: int) -> float:
     return e0.elapsed_time(e1) / reps
 
 
+def choose(trials: List[dict], max_overflow: float) -> dict:
+    """The fastest trial whose overflowing share of vertices is at most
+    `max_overflow`; if none qualifies, the one with the least overflow (ties:
+    the fastest)."""
+    if not trials:
+        raise ValueError("no trials")
+    ok = [t for t in trials if t["overflow"] <= max_overflow]
+    if ok:
+        return min(ok, key=lambda t: t["ms"])
+    return min(trials, key=lambda t: (t["overflow"], t["ms"]))
+
+
 def tune_view(cfg, v: Dict[str, torch.Tensor], eye, log2_range=(21, 24),
               probes: Sequence[int] = (8, 16, 32), reps: int = 3, max_overflow: float = 1e-5):
     """Best (log2_slots, max_probes) for one view; returns (config, table of trials)."""
@@ -45,8 +57,7 @@ def tune_view(cfg, v: Dict[str, torch.Tensor], eye, log2_range=(21, 24),
             ovf = tab.stats()["overflow_vertices"] / max(n, 1)
             tab.close()
             trials.append({"log2_slots": lg, "max_probes": P, "ms": ms, "overflow": ovf})
-    ok = [t for t in trials if t["overflow"] <= max_overflow]
-    best = min(ok, key=lambda t: t["ms"]) if ok else min(trials, key=lambda t: (t["overflow"], t["ms"]))
+    best = choose(trials, max_overflow)
     return dataclasses.replace(cfg, log2_slots=best["log2_slots"], max_probes=best["max_probes"]), trials
 
 
