@@ -171,12 +171,14 @@ def level_of_detail(cx, cy, cz, x, y, z, k, lod_min, lod_max) -> np.ndarray:
     rounded to nearest; floor(log2 F) of the positive FP32 F = k * d is its
     unbiased exponent field (0 and subnormals read as -127 and clamp to
     lod_min; inf/NaN read as 128 and clamp to lod_max)."""
-    dx = F32(cx) - x
-    dy = F32(cy) - y
-    dz = F32(cz) - z
-    d2 = (dx * dx + dy * dy) + dz * dz
-    d = np.sqrt(d2)
-    F = F32(k) * d
+    # FP32 overflow to inf is part of the definition (it reads as level 128)
+    with np.errstate(over="ignore"):
+        dx = F32(cx) - x
+        dy = F32(cy) - y
+        dz = F32(cz) - z
+        d2 = (dx * dx + dy * dy) + dz * dz
+        d = np.sqrt(d2)
+        F = F32(k) * d
     e = ((F.view(U32) >> U32(23)) & U32(0xFF)).astype(np.int32) - 127
     return np.clip(e, lod_min, lod_max).astype(np.int32)
 
