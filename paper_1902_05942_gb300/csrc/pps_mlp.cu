@@ -6,14 +6,14 @@
 // normalized to a box (72), the normal (3), 5 zeros; three hidden layers of
 // 64 with ReLU; linear RGB output.  BF16 weights and activations, FP32
 // accumulation, on the fifth-generation tensor cores: tcgen05.mma from
-// shared-memory tiles in the canonical K-major layout into tensor memory,
+// shared-memory tiles in the canonical no-swizzle layout into tensor memory,
 // tcgen05.ld back to registers for the bias / ReLU / rounding epilogues.
 // Inference: a CTA of 128 threads evaluates 128 vertices per tile.
-// Training: a CTA of 128 threads takes 128 samples through the forward pass,
-// the delta chain and the weight gradients X^T dZ (products over the samples,
-// from transposed tiles the epilogues write), reduced into an FP32 gradient
-// with atomics; Adam updates FP32 master weights and refreshes the BF16
-// copies.
+// Training: a CTA of 128 threads draws 128 samples and takes them through the
+// forward pass, the delta chain and the weight and bias gradients dZ^T X and
+// dZ^T 1 (products over the samples, reading the row-per-sample tiles as
+// MN-major operands), added to an FP32 gradient with vector reductions; Adam
+// updates FP32 master weights and refreshes the BF16 copies.
 //
 // Parameter vector (FP32, this order): W1 [64][80], b1 [64], W2 [64][64], b2,
 // W3 [64][64], b3, W4 [3][64], b4 [3]  (W as [out][in]).
