@@ -59,12 +59,43 @@ def _peaks():
 KERNEL_SOURCES = ("pps_device.cuh", "pps_internal.h", "pps_kernels.cu")
 
 
-def _source_hash() -> str:
+def _strip_comments(src: str) -> str:
+    """C++ source without its comments (string and character literals kept),
+    so that editing a comment does not count as changing a kernel."""
+    out, i, n = [], 0, len(src)
+    while i < n:
+        c = src[i]
+        if c in "\"'":
+            j = i + 1
+            while j < n and src[j] != c:
+                j += 2 if src[j] == "\\" else 1
+            out.append(src[i:j + 1])
+            i = j + 1
+        elif src.startswith("//", i):
+            j = src.find("\n", i)
+            i = n if j < 0 else j
+        elif src.startswith("/*", i):
+            j = src.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+        else:
+            out.append(c)
+            i += 1
+    return "".join(out)
+
+
+def _source_hash(texts=None) -> str:
+    """Hash of the code (comments and blank space at line ends left out) of
+    the sources that define k_fused."""
     h = hashlib.sha256()
     for f in KERNEL_SOURCES:
-        with open(os.path.join(CSRC, f), "rb") as fh:
-            h.update(f.encode())
-            h.update(fh.read())
+        if texts is None:
+            with open(os.path.join(CSRC, f), encoding="utf-8") as fh:
+                src = fh.read()
+        else:
+            src = texts[f]
+        code = "\n".join(line.rstrip() for line in _strip_comments(src).splitlines() if line.strip())
+        h.update(f.encode())
+        h.update(code.encode())
     return h.hexdigest()[:16]
 
 

@@ -9,13 +9,21 @@
 //  k_clear_sweep   empties the frame's cells for the next frame.
 //  k_fused         the whole frame in one persistent cooperative launch: the
 //                  four steps above separated by grid barriers; each vertex's
-//                  cell id stays in shared memory between the phases and each
-//                  CTA blends and clears the cells it created.
+//                  cell id stays in shared memory between the phases; the
+//                  blend's tiles come from a second counter, and each CTA
+//                  clears the cells its own tiles created.
+//  k_fused<NEIGH>, k_neighbors, k_clear_fused
+//                  neighborhood-search frames: the persistent kernel queues
+//                  its low-count vertices after the lookups, a separate launch
+//                  searches them, a third empties the cells.
+//  k_blend_lookup, k_blend_apply
+//                  the blend of a history that follows changes of resolution.
 //
-// Vertex streams are read four consecutive vertices per thread with 128-bit
-// streaming loads (ld.global.cs) when the arrays are 16-byte aligned; table
-// words are read at L2 (ld.relaxed.gpu / ld.global.cg) because other CTAs
-// write them.
+// Vertex streams are read with streaming loads (ld.global.cs): in the split
+// kernels four consecutive vertices per thread (128-bit when the arrays are
+// 16-byte aligned), in the persistent kernels W consecutive vertices per
+// thread with each warp's sub-batch one contiguous run; table words are read
+// at L2 (ld.relaxed.gpu / ld.global.cg) because other CTAs write them.
 #include <algorithm>
 
 #include "pps_internal.h"
@@ -884,8 +892,9 @@ struct FusedArgs {
 // The persistent kernel.  Phase A hands out tiles of kFusedTile consecutive
 // vertices from a per-frame counter, so CTAs that meet cheap (coherent)
 // vertices take more tiles; each CTA remembers its tiles, keeps every vertex's
-// cell id in its shared-memory stash, and later blends, looks up and clears
-// exactly those tiles.  A tile's new cells take ids from the tile's own range
+// cell id in its shared-memory stash, and later looks up and clears exactly
+// those tiles (the blend hands tiles out again from a second counter).  A
+// tile's new cells take ids from the tile's own range
 // [tile * kFusedTile, tile * kFusedTile + claims).
 template <bool TEMPORAL, int W, bool EVICT = false, bool NEIGH = false>
 __global__ void __launch_bounds__(kFusedBlock, W == 4 ? 1 : 2) k_fused(FusedArgs a) {
