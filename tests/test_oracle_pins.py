@@ -397,3 +397,38 @@ def test_fingerprint_collisions_follow_the_birthday_bound():
     pairs = int((c * (c - 1) // 2).sum())
     mean = m * (m - 1) / 2 / 2 ** 32
     assert abs(pairs - mean) < 5 * np.sqrt(mean), (pairs, mean)
+
+
+def _one_cell_frame(tuple7, c_new, n_new):
+    """A frame of one cell (one vertex per member) with average c_new."""
+    return O.FrameResult(None, np.zeros(n_new, dtype=np.int64), np.array([tuple7], dtype=np.int64),
+                         np.full(n_new, n_new), np.tile(c_new, (n_new, 1)), None,
+                         np.array([n_new]), np.array([np.array(c_new) * n_new]), None, None, None)
+
+
+def test_fp16_history_rounds_to_binary16():
+    """FP16 history (Sec. 3.4.1 with half-precision storage): the stored and
+    returned value is the binary16 nearest to the blend.  0.1 = 1.6 * 2^-4 and
+    1.6 * 1024 = 1638.4 rounds to 1638, so binary16(0.1) = 1638 / 1024 * 2^-4 =
+    0.0999755859375; 0.75 is representable and survives every frame exactly."""
+    t = (1, 2, 3, 4, 5, 6, 7)
+    hist, val, _ = O.blend(O.History.empty(), _one_cell_frame(t, [0.1, 0.75, 2.0], 3), 0.2,
+                           fp16=True)
+    assert val[0, 0] == 0.0999755859375 and val[0, 1] == 0.75 and val[0, 2] == 2.0
+    for _ in range(5):
+        hist, val, _ = O.blend(hist, _one_cell_frame(t, [0.1, 0.75, 2.0], 3), 0.2, fp16=True)
+        assert val[0, 1] == 0.75 and val[0, 2] == 2.0
+        assert abs(val[0, 0] - 0.1) <= 2.0 ** -14  # within half a binary16 step at 0.1
+
+
+def test_count_cap_saturates_but_weight_uses_true_counts():
+    """N = N_old + N_new saturates at the cap (65535 for a 16-bit count) while
+    the integrating weight alpha = N_old / (N_old + N_new) uses the counts
+    before the cap."""
+    t = (0, 0, 0, 1, 2, 3, 4)
+    hist = O.History(np.array([t], dtype=np.int64), np.array([[1.0, 1.0, 1.0]]), np.array([65000]))
+    hist2, val, cnt = O.blend(hist, _one_cell_frame(t, [2.0, 2.0, 2.0], 1000), -1.0,
+                              n_cap=65535)
+    a = 65000 / 66000
+    assert cnt[0] == 65535 and hist2.n[0] == 65535
+    assert np.allclose(val[0], a * 1.0 + (1 - a) * 2.0, rtol=1e-15)
