@@ -432,3 +432,30 @@ def test_count_cap_saturates_but_weight_uses_true_counts():
     a = 65000 / 66000
     assert cnt[0] == 65535 and hist2.n[0] == 65535
     assert np.allclose(val[0], a * 1.0 + (1 - a) * 2.0, rtol=1e-15)
+
+
+def test_pow2_matches_ldexp_over_the_normal_range():
+    """2^l built from the exponent bits equals the library's ldexp for every
+    integer l of the normal FP32 range."""
+    ls = np.arange(-126, 128)
+    assert np.array_equal(O.pow2_f32(ls), np.ldexp(np.float32(1), ls).astype(np.float32))
+
+
+def test_level_at_a_given_distance_matches_frexp():
+    """floor(log2(k d)) for given distances, against the library's frexp of the
+    FP32 product (frexp returns e with 2^(e-1) <= x < 2^e), and clamped."""
+    rng = np.random.default_rng(17)
+    d = (rng.uniform(0.5, 1.0, 4000) * 2.0 ** rng.integers(-20, 30, 4000)).astype(np.float32)
+    k = np.float32(0.0039)
+    F = (k * d).astype(np.float32)
+    ref = np.clip(np.frexp(F)[1] - 1, -24, 24)
+    assert np.array_equal(O.level_of_detail_at(d, k, -24, 24), ref)
+
+
+def test_fixed_point_mean_of_dyadic_values_is_exact():
+    """Fixed-point sums of a dyadic value c (c 2^24 an integer) are exact, so
+    the average fl32(fl32(sum) 2^-24) / fl32(n) is c itself for any count."""
+    for c in (0.75, 3.5, 0.0009765625):
+        for n in (1, 3, 1000, 12345):
+            s = np.array([[round(c * 2 ** 24) * n] * 3], dtype=np.int64)
+            assert np.all(O.fixed_mean_f32(s, np.array([n])) == np.float32(c)), (c, n)
