@@ -669,7 +669,7 @@ def neighbor_cells(tuples: np.ndarray, centers: np.ndarray) -> np.ndarray:
     return out
 
 
-def neighborhood(fr: FrameResult, threshold: int, cell_value=None, cell_weight=None):
+def neighborhood(fr: FrameResult, threshold: int, cell_value=None, cell_weight=None, only=None):
     """Neighborhood search (Sec. 3.3.2): a vertex whose own cell has fewer
     than `threshold` members takes the pooled average of the 3 x 3 x 3 block of
     cells around its cell at the same level and with the same quantized
@@ -683,6 +683,9 @@ def neighborhood(fr: FrameResult, threshold: int, cell_value=None, cell_weight=N
     `cell_value` (C, 3) and `cell_weight` (C,) -- blended values and their
     counts N after a temporal blend -- it is sum(N c) / sum(N) in FP64, and
     the low-count test reads N.
+
+    `only` (vertex indices): search only for those vertices (the others keep
+    their own cell's values); the results for them are the same.
 
     Returns (value64 (N, 3), value_fixed (N, 3) or None, count (N,), status)."""
     if cell_value is None:
@@ -701,6 +704,8 @@ def neighborhood(fr: FrameResult, threshold: int, cell_value=None, cell_weight=N
     status = np.zeros(fr.cell.shape[0], dtype=np.uint8)
     status[low] = STATUS_NEIGHBORS
     idx = np.nonzero(low)[0]
+    if only is not None:
+        idx = np.intersect1d(idx, np.asarray(only, dtype=np.int64))
     if idx.size == 0:
         return value64, value_fx, count, status
     nb = neighbor_cells(fr.tuples, fr.tuples[fr.cell[idx]])

@@ -198,3 +198,23 @@ def test_neighborhood_weights_blended_values_by_their_counts():
     assert np.array_equal(val[1], c[1]) and cnt[1] == 6
     assert np.allclose(val[2], c[2], rtol=1e-15) and cnt[2] == 1
     assert list(st) == [O.STATUS_NEIGHBORS, O.STATUS_OK, O.STATUS_NEIGHBORS]
+
+
+def test_neighborhood_for_a_subset_equals_the_full_search():
+    """Searching only for some vertices gives those vertices the same results
+    as the search over all of them."""
+    rng = np.random.default_rng(23)
+    p = (rng.normal(0, 0.3, (3000, 3)) + np.array([0.0, 1.0, 2.0])).astype(np.float32)
+    nrm = np.tile(np.array([[0.0, 1.0, 0.0]], dtype=np.float32), (3000, 1))
+    rgb = rng.lognormal(-1, 1.0, (3000, 3)).astype(np.float32)
+    v = {"px": p[:, 0], "py": p[:, 1], "pz": p[:, 2], "nx": nrm[:, 0], "ny": nrm[:, 1],
+         "nz": nrm[:, 2], "r": rgb[:, 0], "g": rgb[:, 1], "b": rgb[:, 2]}
+    par = O.KeyParams(log2_slots=16, max_probes=16, voxel_scale=2.0, pixel_angle=0.002,
+                      jitter=False, normal_in_home_hash=False)
+    fr = O.filter_frame(par, (0.0, 2.0, -6.0), 0, v)
+    full = O.neighborhood(fr, 4)
+    sub = rng.choice(3000, 700, replace=False)
+    part = O.neighborhood(fr, 4, only=sub)
+    assert (full[3][sub] == O.STATUS_NEIGHBORS).sum() > 100
+    for a, b in zip(full, part):
+        assert np.array_equal(a[sub], b[sub])

@@ -178,3 +178,38 @@ def test_batch_rejects_fallback_tables():
         pps.Batch([(tab, v, out)])
     assert e.value.code == pps.PPS_EINVAL
     tab.close()
+
+
+def test_neighborhood_full_size_hd_sampled():
+    """The HD frame (5.06 M vertices, T = 2^23) with the neighborhood fallback,
+    in the launch configuration bench.py times: the persistent kernel queues
+    the low-count vertices and k_neighbors searches them.  The one or two
+    vertices that meet the probe limit are left out and the oracle runs on
+    the rest (same jitter counters); 20,000 sampled vertices then match it:
+    counts and statuses bit-exact, values within the FP32 bar plus 27
+    roundings."""
+    w = configs.hd()
+    cfg = w.filters[0]
+    cfg.fallback = "neighbors"
+    spec = configs.frame_spec(w, 0, 0)
+    vt = scene.trace_stream(spec, 0, "cuda")
+    d = {k: vt[k].contiguous() for k in scene.STREAMS}
+    tab = pps.Table(cfg)
+    out = tab.filter(d, spec.view.eye, 0)
+    torch.cuda.synchronize()
+    vn = {k: d[k].cpu().numpy() for k in scene.STREAMS}
+    status = out["status"].cpu().numpy()
+    ovf = status == 2
+    assert ovf.sum() <= 10
+    keep = np.nonzero(~ovf)[0]
+    fr = O.filter_frame(O.KeyParams(**cfg.oracle_kwargs()), spec.view.eye, 0,
+                        {k: a[keep] for k, a in vn.items()}, ids=keep.astype(np.uint32))
+    pos = np.random.default_rng(31).choice(keep.shape[0], 20000, replace=False)
+    val64, _, cnt, st = O.neighborhood(fr, 4, only=pos)
+    j = keep[pos]
+    assert (st[pos] == O.STATUS_NEIGHBORS).sum() > 2000
+    assert np.array_equal(out["count"].cpu().numpy().astype(np.int64)[j], cnt[pos])
+    assert np.array_equal(status[j], st[pos])
+    _check(_rgb(out)[j], val64[pos], cnt[pos], extra=27 * U)
+    assert tab.stats()["device_error"] == 0
+    tab.close()
