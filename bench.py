@@ -412,8 +412,8 @@ def plain_leg(frames, cfg, calls, steps, warmup):
 def fallback_leg(frames, cfg, calls, steps, warmup, fallback, status):
     """The headline workload (temporal HD frames) with a low-count fallback:
     "coarse" = multi-level accumulation (a second table one level coarser,
-    Sec. 3.3.3), "neighbors" = neighborhood search over the 3x3x3 block
-    (Sec. 3.3.2).  Same timing as the headline; reports the share of vertices
+    Sec. 3.3.2), "neighbors" = neighborhood search over the 3x3x3 block
+    (Sec. 3.3.1).  Same timing as the headline; reports the share of vertices
     that took the fallback in the last frame."""
     import ctypes
     import torch

@@ -50,9 +50,9 @@ extern "C" {
                               /* unfiltered contribution returned (Sec. 3.2)   */
 #define PPS_STATUS_MLP 3      /* low count: the learned fallback's prediction  */
 #define PPS_STATUS_COARSE 4   /* low count: the next coarser resolution's cell */
-                              /* average (multi-level accumulation, 3.3.3)     */
+                              /* average (multi-level accumulation, 3.3.2)     */
 #define PPS_STATUS_NEIGHBORS 5 /* low count: pooled average of the 3x3x3 block */
-                              /* of cells around the vertex's (Sec. 3.3.2)     */
+                              /* of cells around the vertex's (Sec. 3.3.1)     */
 
 /* ---- modes -------------------------------------------------------------- */
 #define PPS_ACCUM_FP32 0  /* FP32 sums, FP32 count lane: red.add.v4.f32         */
@@ -61,8 +61,8 @@ extern "C" {
 #define PPS_HIST_FP32 1   /* history average FP32, count uint32                 */
 #define PPS_HIST_FP16 2   /* history average binary16, count uint16 saturating  */
 #define PPS_FALLBACK_NONE 0      /* low-count vertices keep their cell average  */
-#define PPS_FALLBACK_COARSE 1    /* multi-level accumulation (Sec. 3.3.3)       */
-#define PPS_FALLBACK_NEIGHBORS 2 /* neighborhood search (Sec. 3.3.2)            */
+#define PPS_FALLBACK_COARSE 1    /* multi-level accumulation (Sec. 3.3.2)       */
+#define PPS_FALLBACK_NEIGHBORS 2 /* neighborhood search (Sec. 3.3.1)            */
 
 /*
  * Table and key parameters (Algorithm 1; Sec. 3.1.1, 3.2, 3.2.1; Sec. 4).
@@ -99,7 +99,7 @@ extern "C" {
  *                     lowcount_threshold members (after a blend: N) receives
  *                     instead of its cell's average (Sec. 3.3):
  *                     PPS_FALLBACK_NONE       the cell average, status LOWCOUNT;
- *                     PPS_FALLBACK_COARSE     multi-level accumulation (3.3.3):
+ *                     PPS_FALLBACK_COARSE     multi-level accumulation (3.3.2):
  *                        the table keeps a second table for the next coarser
  *                        resolution (voxel_scale doubled, so every level of
  *                        detail grows by exactly one; same T, P, seeds, modes
@@ -107,7 +107,7 @@ extern "C" {
  *                        both, and a low-count vertex gets the coarser cell's
  *                        value and count, status COARSE (unless its coarse
  *                        insert overflowed: then LOWCOUNT as before);
- *                     PPS_FALLBACK_NEIGHBORS  neighborhood search (3.3.2): a
+ *                     PPS_FALLBACK_NEIGHBORS  neighborhood search (3.3.1): a
  *                        low-count vertex gets the pooled average of the
  *                        3 x 3 x 3 block of cells around its own (same level,
  *                        same quantized normal): the block's summed sums over

@@ -34,8 +34,8 @@ What it computes, and from which passage
   fingerprint words carry a priority (the frame of last use) in their top
   bits, so that a cell without room replaces the least recently used entry
   of its probe window.
-* Fallbacks for cells with few vertices (Sec. 3.3.2 neighborhood search,
-  Sec. 3.3.3 multi-level accumulation): the pooled average of the 3x3x3
+* Fallbacks for cells with few vertices (Sec. 3.3.1 neighborhood search,
+  Sec. 3.3.2 multi-level accumulation): the pooled average of the 3x3x3
   block of cells around a vertex's cell, and the average of the next coarser
   resolution, both taken only where the vertex's own cell has fewer than a
   threshold of members.
@@ -608,7 +608,7 @@ def simulate_linear_probing(home: np.ndarray, fp: np.ndarray, log2_slots: int,
 
 # ----------------------------------------------------------------------------
 # Fallbacks for cells with few vertices (Sec. 3.3): neighborhood search
-# (Sec. 3.3.2) and multi-level accumulation (Sec. 3.3.3).  Both replace the
+# (Sec. 3.3.1) and multi-level accumulation (Sec. 3.3.2).  Both replace the
 # value of a vertex only where its own cell has fewer than `threshold`
 # members.
 # ----------------------------------------------------------------------------
@@ -628,7 +628,7 @@ def coarse_params(p: KeyParams) -> KeyParams:
 
 
 def multilevel_select(fine_value, fine_count, coarse_value, coarse_count, threshold: int):
-    """Multi-level accumulation (Sec. 3.3.3): every vertex is accumulated at
+    """Multi-level accumulation (Sec. 3.3.2): every vertex is accumulated at
     its own resolution and at the next coarser one; a vertex whose own cell
     has fewer than `threshold` members takes the coarser cell's value and
     count instead (status COARSE).  Works on per-vertex arrays, so the
@@ -670,7 +670,7 @@ def neighbor_cells(tuples: np.ndarray, centers: np.ndarray) -> np.ndarray:
 
 
 def neighborhood(fr: FrameResult, threshold: int, cell_value=None, cell_weight=None, only=None):
-    """Neighborhood search (Sec. 3.3.2): a vertex whose own cell has fewer
+    """Neighborhood search (Sec. 3.3.1): a vertex whose own cell has fewer
     than `threshold` members takes the pooled average of the 3 x 3 x 3 block of
     cells around its cell at the same level and with the same quantized
     normal, i.e. the members of all those cells averaged together (cells that

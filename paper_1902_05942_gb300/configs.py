@@ -60,7 +60,7 @@ class FilterConfig:
     log2_hist_slots: int = 0
     lowcount_threshold: int = 4
     alpha: Optional[float] = None  # temporal blend weight of the old value (< 0: integrate)
-    fallback: str = "none"  # low-count vertices: "none", "coarse" (Sec. 3.3.3), "neighbors" (3.3.2)
+    fallback: str = "none"  # low-count vertices: "none", "coarse" (Sec. 3.3.2), "neighbors" (3.3.1)
     hist_evict: bool = False  # history evicts its least recently used entries (Sec. 3.4.3)
     hist_migrate: bool = False  # history follows changes of resolution (Sec. 3.4.2)
 

@@ -304,7 +304,7 @@ struct Result {
   uint8_t status;
 };
 
-// Neighborhood search (Sec. 3.3.2) for vertex j, whose own cell holds fewer
+// Neighborhood search (Sec. 3.3.1) for vertex j, whose own cell holds fewer
 // than t.lowcount members: the pooled average of the 3 x 3 x 3 block of cells
 // around its cell at the same level and with the same quantized normal.  A
 // plain frame pools the cells' sums and counts (FP32 sums, or exact int64

@@ -1,5 +1,5 @@
 """Pins of the oracle's low-density fallbacks (no GPU): multi-level
-accumulation (Sec. 3.3.3) and neighborhood search (Sec. 3.3.2).
+accumulation (Sec. 3.3.2) and neighborhood search (Sec. 3.3.1).
 
 The pins do not reuse the oracle's grouping: brute-force loops over tiny
 inputs compute levels with float64 logarithms and cells with float64 floors,

@@ -1,5 +1,5 @@
 """GPU parity of the low-count fallbacks against the oracle: multi-level
-accumulation (Sec. 3.3.3) and neighborhood search (Sec. 3.3.2), through the
+accumulation (Sec. 3.3.2) and neighborhood search (Sec. 3.3.1), through the
 fused launch and the split calls, with FP32 and fixed-point sums, and after
 temporal blends.
 
