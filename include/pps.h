@@ -43,6 +43,16 @@ extern "C" {
 #define PPS_EDEVICE 4 /* a kernel raised the table's device error word         */
 #define PPS_ESTATE 5  /* call out of order for the table's frame state         */
 
+/* ---- bits of the device error word (pps_stats_t.device_error) ----------- */
+#define PPS_DEVERR_BARRIER_TIMEOUT 1u  /* a grid-barrier wait gave up (~2 s);   */
+                                       /* the launch ended early                */
+#define PPS_DEVERR_BAD_SLOT 2u         /* a lookup got a cell id that is not    */
+                                       /* one of this frame's                   */
+#define PPS_DEVERR_COUNT_SATURATED 4u  /* FP32 accumulation: a cell reached     */
+                                       /* 2^24 members, past which its FP32     */
+                                       /* count (and so its average) is not     */
+                                       /* exact; PPS_ACCUM_FIXED has no limit   */
+
 /* ---- per-vertex status written by pps_query / pps_filter ---------------- */
 #define PPS_STATUS_OK 0       /* cell average returned                         */
 #define PPS_STATUS_LOWCOUNT 1 /* average returned, count < lowcount_threshold  */
@@ -55,7 +65,8 @@ extern "C" {
                               /* of cells around the vertex's (Sec. 3.3.1)     */
 
 /* ---- modes -------------------------------------------------------------- */
-#define PPS_ACCUM_FP32 0  /* FP32 sums, FP32 count lane: red.add.v4.f32         */
+#define PPS_ACCUM_FP32 0  /* FP32 sums, FP32 count lane: red.add.v4.f32; counts */
+                          /* exact below 2^24 members per cell (see above)      */
 #define PPS_ACCUM_FIXED 1 /* int64 sums of round(v * 2^24): order-free, exact   */
 #define PPS_HIST_NONE 0   /* no temporal state: every frame starts empty        */
 #define PPS_HIST_FP32 1   /* history average FP32, count uint32                 */
@@ -377,17 +388,35 @@ int pps_keys(pps_table *t, const pps_vertices *v, size_t n, uint32_t *h_out, uin
  *    26 MB), held by every GPU that loads the library until the process exits.
  *    Limits: log2_slots <= 20 and n <= 524,288; larger requests, another
  *    accum_mode, or a history return PPS_EINVAL.
- *  - The first call on a device (that device current) looks up the array's
- *    device address with cudaGetSymbolAddress; make that first call before any
- *    stream capture.
+ *  - The first call in a CUDA context (the device's primary context, that
+ *    device current) looks up the array's device address with
+ *    cudaGetSymbolAddress; make that first call before any stream capture.  A
+ *    context created later on the same device (after cudaDeviceReset) looks
+ *    it up again on its first call.
  *  - All calls share the array and each starts by clearing what it uses; two
  *    calls that overlap on the GPU (streams not ordered) race and give wrong
  *    results.
+ *  - The call's counters and device error word stay in the array until the
+ *    next call clears them: read them with pps_noalloc_stats in between.
  * Arguments as for pps_params / pps_filter; every pointer is the caller's.
- * Errors: PPS_EINVAL, PPS_ECUDA.
+ * Errors: PPS_EINVAL (the checks of pps_create, and the limits above),
+ * PPS_ECUDA.
  */
 int pps_filter_noalloc(const pps_params *p, const pps_camera *cam, uint32_t frame,
                        const pps_vertices *v, size_t n, const pps_output *out, void *stream);
+
+/*
+ * pps_noalloc_stats: synchronize `stream` and read what the last
+ * pps_filter_noalloc left in the library's static array: frame_cells,
+ * overflow_vertices, vertices and device_error (the other fields are 0).  No
+ * paper counterpart; like pps_filter_noalloc it allocates nothing.  Call it
+ * after a pps_filter_noalloc and before the next one, on a stream ordered
+ * after it.  Returns PPS_EDEVICE (message naming the bits) when a kernel
+ * raised the device error word -- a grid-barrier timeout, say -- so that a
+ * frame that went wrong on the GPU is not taken for a good one; the word is
+ * then cleared.  Errors: PPS_EINVAL (out NULL), PPS_ECUDA, PPS_EDEVICE.
+ */
+int pps_noalloc_stats(pps_stats_t *out, void *stream);
 
 /*
  * pps_stats: synchronize `stream` and read the table's counters.  Returns

@@ -153,6 +153,16 @@ class KeyParams:
     lod_max: int = 24
 
 
+def pixel_angle(fov_y_deg: float, height: int) -> float:
+    """theta_px: the height of one pixel's footprint at unit distance from a
+    pinhole camera, 2 tan(fov_y / 2) / height (fov_y the vertical field of
+    view in degrees, height the image height in pixels), in FP64.  Sec. 4
+    sizes voxels as s times "the projected size of a pixel"; with square
+    pixels the vertical extent fixes it."""
+    import math
+    return 2.0 * math.tan(math.radians(float(fov_y_deg)) / 2.0) / float(height)
+
+
 def pow2_f32(l) -> np.ndarray:
     """2^l as float32, exact for integer l in [-126, 127] (built from the bits)."""
     l = np.asarray(l, dtype=np.int64)
@@ -493,7 +503,7 @@ def migrated_history(history: History, tuples: np.ndarray):
 
 
 def blend(history: History, fr: FrameResult, alpha: float, fp16: bool = False,
-          n_cap: Optional[int] = None, migrate: bool = False
+          n_cap: Optional[int] = None, migrate: bool = False, c_new=None
           ) -> Tuple[History, np.ndarray, np.ndarray]:
     """c = alpha c_old + (1 - alpha) c_new per cell present in this frame.
 
@@ -503,6 +513,9 @@ def blend(history: History, fr: FrameResult, alpha: float, fp16: bool = False,
     average is rounded to binary16, as a half-precision history store does.
     With `migrate` a cell without history of its own takes the one of its
     finer children or coarser parent (migrated_history) as (c_old, N_old).
+    `c_new` (C, 3), if given, is this frame's average per cell instead of the
+    FP64 sum / count -- e.g. the fixed-point mode's average, which is what a
+    fixed-point table blends.
     Returns (new history, blended value per vertex (N, 3), count per vertex)."""
     H = history.tuples.shape[0]
     allk = np.concatenate([history.tuples, fr.tuples]) if H else fr.tuples
@@ -516,7 +529,10 @@ def blend(history: History, fr: FrameResult, alpha: float, fp16: bool = False,
     N = np.zeros(U, dtype=np.int64)
     c[io] = history.c
     N[io] = history.n
-    c_new = fr.cell_sum64 / fr.cell_count[:, None]
+    if c_new is None:
+        c_new = fr.cell_sum64 / fr.cell_count[:, None]
+    else:
+        c_new = np.asarray(c_new, dtype=np.float64)
     n_new = fr.cell_count
     c_old = c[inw]
     n_old = N[inw]

@@ -40,6 +40,21 @@ enum FrameState { kClean = 0, kOpen = 1, kBlended = 2 };
 namespace pps {
 // Record an error for pps_last_error() from another translation unit.
 int record_error(int code, const char* msg) { return fail(code, msg); }
+
+const char* last_error_text() { return g_err.c_str(); }
+
+// What the bits of a device error word mean, for pps_last_error().
+std::string device_error_text(unsigned int word) {
+  char buf[64];
+  std::snprintf(buf, sizeof(buf), "device error word 0x%x:", word);
+  std::string s = buf;
+  if (word & kErrBarrierTimeout) s += " a grid-barrier wait timed out;";
+  if (word & kErrBadSlot) s += " a lookup got a cell id not of this frame;";
+  if (word & kErrCountSaturated)
+    s += " a cell reached 2^24 members, past which FP32 counts are not exact"
+         " (use fixed-point accumulation);";
+  return s;
+}
 }  // namespace pps
 
 struct pps_table {
@@ -80,7 +95,7 @@ struct pps_table {
   size_t fb_cap = 0;            // vertices the scratch holds
 };
 
-namespace {
+namespace pps {
 
 int check_params(const pps_params* p) {
   if (!p) return fail(PPS_EINVAL, "params is NULL");
@@ -114,6 +129,12 @@ int check_params(const pps_params* p) {
     if (r) return fail(PPS_EINVAL, "reserved fields must be zero");
   return PPS_OK;
 }
+
+}  // namespace pps
+
+namespace {
+
+using pps::check_params;
 
 int check_table(pps_table* t) {
   if (!t) return fail(PPS_EINVAL, "table is NULL");
@@ -804,9 +825,7 @@ int pps_stats(pps_table* t, pps_stats_t* out, void* stream) {
     // clear the error word and the barrier state so the table stays usable
     PPS_CUDA(cudaMemsetAsync(&t->dev.ctrl->error, 0, 3 * sizeof(unsigned int), st));  // + barrier
     PPS_CUDA(cudaStreamSynchronize(st));
-    char buf[96];
-    std::snprintf(buf, sizeof(buf), "device error word 0x%x", c.error);
-    return fail(PPS_EDEVICE, buf);
+    return fail(PPS_EDEVICE, pps::device_error_text(c.error));
   }
   return PPS_OK;
 }

@@ -55,7 +55,13 @@ constexpr size_t kCtrlFrameBytes = 7 * sizeof(unsigned long long);  // reset per
 enum : unsigned int {
   kErrBarrierTimeout = 1u,
   kErrBadSlot = 2u,
+  // FP32 accumulation: a cell reached 2^24 members, past which adding 1.0f to
+  // its FP32 count no longer changes it, so its count and average are not
+  // exact (fixed-point accumulation counts in 64 bits and has no such limit)
+  kErrCountSaturated = 4u,
 };
+
+constexpr float kExactCountLimit = 16777216.0f;  // 2^24
 
 // Table layout.
 //
@@ -533,6 +539,7 @@ __device__ __forceinline__ long long bits64(float x, float y) {
 __device__ __forceinline__ CellMean mean_of(const TableDev& t, const AccRaw& a) {
   CellMean m;
   if (!t.fixed) {
+    if (a.lo.w >= kExactCountLimit) atomicOr(&t.ctrl->error, kErrCountSaturated);
     m.r = __fdiv_rn(a.lo.x, a.lo.w);
     m.g = __fdiv_rn(a.lo.y, a.lo.w);
     m.b = __fdiv_rn(a.lo.z, a.lo.w);

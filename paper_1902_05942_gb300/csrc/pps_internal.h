@@ -3,9 +3,12 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <string>
 #include <cuda_runtime.h>
 
 #include "pps_device.cuh"
+
+struct pps_params;
 
 namespace pps {
 
@@ -85,6 +88,11 @@ int fused_tile_size();  // vertices (and cell ids) per tile of the persistent ke
 bool aligned16(const void* p);
 
 int record_error(int code, const char* msg);  // message for pps_last_error()
+const char* last_error_text();                // the message pps_last_error() returns
+std::string device_error_text(unsigned int word);  // the bits of a device error word
+// Checks of table parameters shared by pps_create and pps_filter_noalloc
+// (PPS_OK, or PPS_EINVAL with the reason recorded for pps_last_error()).
+int check_params(const pps_params* p);
 
 // Self-test of the tensor-core kernels' bounded mbarrier wait (pps_mlp.cu).
 cudaError_t launch_selftest_mbar(unsigned long long limit_ns, unsigned int* err, cudaStream_t st);

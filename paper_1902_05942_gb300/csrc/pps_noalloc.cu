@@ -18,9 +18,19 @@
 // them) race on it and give wrong results.
 //
 // Host code cannot use the array's name as a device address: there it is a
-// host-side stand-in.  The first call on a device, with that device current,
-// therefore looks the device address up once with cudaGetSymbolAddress and
-// remembers it; that first call should come before any stream capture.
+// host-side stand-in.  The first call in a CUDA context (a device's primary
+// context, with that device current) therefore looks the device address up
+// with cudaGetSymbolAddress and remembers it for that context; that first call
+// should come before any stream capture.  A new context on the same device
+// (after cudaDeviceReset, say) loads the library's kernels anew, so the
+// address is looked up again there.
+//
+// pps_noalloc_stats reads the counters and the device error word that the
+// last call left in the array (they live there too), so that a call that went
+// wrong on the GPU is reported rather than overwritten by the next call.
+#include <cuda.h>
+
+#include <cstddef>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -49,24 +59,75 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 // The message is kept where pps_last_error() reads it.
 int noalloc_fail(int code, const std::string& msg) { return pps::record_error(code, msg.c_str()); }
 
-// Device address of the scratch array on the current device, looked up once.
-int scratch_address(unsigned char** out) {
+// The unique id of the calling thread's current CUDA context, through the
+// driver's entry points (fetched once; the library does not link the driver
+// library itself).  0 when there is no current context.
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+
+int current_context_id(const char* who, unsigned long long* id) {
+  static std::once_flag once;
+  static CtxGetCurrentFn get_current = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  std::call_once(once, [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      get_current = reinterpret_cast<CtxGetCurrentFn>(f);
+    f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<CtxGetIdFn>(f);
+  });
+  if (!get_current || !get_id)
+    return noalloc_fail(PPS_ECUDA, std::string(who) + ": driver context queries unavailable");
+  CUcontext ctx = nullptr;
+  if (get_current(&ctx) != CUDA_SUCCESS || !ctx) {
+    *id = 0;
+    return PPS_OK;
+  }
+  if (get_id(ctx, id) != CUDA_SUCCESS)
+    return noalloc_fail(PPS_ECUDA, std::string(who) + ": cuCtxGetId failed");
+  return PPS_OK;
+}
+
+// Device address of the scratch array in the current context: looked up once
+// per context (keyed by the context's unique id, so that a context created
+// after a reset of the device never gets the old context's address).
+int scratch_address(const char* who, unsigned char** out) {
   static std::mutex mu;
-  static unsigned char* addr[64] = {nullptr};
+  struct Entry {
+    unsigned long long ctx;
+    unsigned char* addr;
+  };
+  static Entry cache[64] = {};
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess || dev < 0 || dev >= 64)
-    return noalloc_fail(PPS_ECUDA, "pps_filter_noalloc: no usable current device");
+    return noalloc_fail(PPS_ECUDA, std::string(who) + ": no usable current device");
+  unsigned long long ctx = 0;
+  if (int rc = current_context_id(who, &ctx)) return rc;
+  if (ctx == 0) {
+    // no context current on this thread yet: bind (and if need be create)
+    // the device's primary context, which the runtime calls below use
+    e = cudaSetDevice(dev);
+    if (e != cudaSuccess)
+      return noalloc_fail(PPS_ECUDA, std::string(who) + ": " + cudaGetErrorString(e));
+    if (int rc = current_context_id(who, &ctx)) return rc;
+    if (ctx == 0) return noalloc_fail(PPS_ECUDA, std::string(who) + ": no current CUDA context");
+  }
   std::lock_guard<std::mutex> lock(mu);
-  if (!addr[dev]) {
+  if (cache[dev].ctx != ctx || !cache[dev].addr) {
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess || !p)
-      return noalloc_fail(PPS_ECUDA, std::string("pps_filter_noalloc: cudaGetSymbolAddress: ") +
+      return noalloc_fail(PPS_ECUDA, std::string(who) + ": cudaGetSymbolAddress: " +
                                          cudaGetErrorString(e));
-    addr[dev] = static_cast<unsigned char*>(p);
+    cache[dev].ctx = ctx;
+    cache[dev].addr = static_cast<unsigned char*>(p);
   }
-  *out = addr[dev];
+  *out = cache[dev].addr;
   return PPS_OK;
 }
 
@@ -75,7 +136,11 @@ int scratch_address(unsigned char** out) {
 extern "C" int pps_filter_noalloc(const pps_params* p, const pps_camera* cam, uint32_t frame,
                                   const pps_vertices* v, size_t n, const pps_output* out,
                                   void* stream) {
-  if (!p || !cam || !v || !out) return noalloc_fail(PPS_EINVAL, "NULL argument");
+  if (!p || !cam || !v || !out)
+    return noalloc_fail(PPS_EINVAL, "pps_filter_noalloc: params, camera, vertices and output "
+                                    "must not be NULL");
+  if (pps::check_params(p) != PPS_OK)
+    return noalloc_fail(PPS_EINVAL, std::string("pps_filter_noalloc: ") + pps::last_error_text());
   if (p->log2_slots < 4 || p->log2_slots > kNoAllocMaxLog2Slots)
     return noalloc_fail(PPS_EINVAL, "pps_filter_noalloc: log2_slots must be in [4, 20]");
   if (n > kNoAllocMaxVertices)
@@ -84,19 +149,13 @@ extern "C" int pps_filter_noalloc(const pps_params* p, const pps_camera* cam, ui
       p->fallback != PPS_FALLBACK_NONE || p->hist_evict != 0 || p->hist_migrate != 0)
     return noalloc_fail(PPS_EINVAL,
                         "pps_filter_noalloc: FP32 accumulation without history or fallback only");
-  for (uint32_t r : p->reserved)
-    if (r) return noalloc_fail(PPS_EINVAL, "pps_filter_noalloc: reserved fields must be zero");
-  if (p->max_probes < 1 || p->max_probes > (1u << p->log2_slots) || p->max_probes > 4096 ||
-      !(p->voxel_scale > 0.0f) || !(p->pixel_angle > 0.0f) || p->lod_min <= -126 ||
-      p->lod_max >= 127 || p->lod_min > p->lod_max || p->jitter > 1 || p->normal_in_home_hash > 1)
-    return noalloc_fail(PPS_EINVAL, "pps_filter_noalloc: bad parameters");
   if (v->dist || v->extra)
     return noalloc_fail(PPS_EINVAL, "pps_filter_noalloc: no dist or extra arrays");
   if (n && (!v->px || !v->py || !v->pz || !v->nx || !v->ny || !v->nz || !v->r || !v->g ||
             !v->b || !out->r || !out->g || !out->b))
     return noalloc_fail(PPS_EINVAL, "pps_filter_noalloc: vertex and output arrays are required");
   unsigned char* base = nullptr;
-  if (int rc = scratch_address(&base)) return rc;
+  if (int rc = scratch_address("pps_filter_noalloc", &base)) return rc;
   const cudaStream_t st = static_cast<cudaStream_t>(stream);
   const uint32_t T = 1u << p->log2_slots;
   const size_t tile = static_cast<size_t>(pps::fused_tile_size());
@@ -167,5 +226,32 @@ extern "C" int pps_filter_noalloc(const pps_params* p, const pps_camera* cam, ui
                           reinterpret_cast<uint32_t*>(base + kOffStash), nullptr, st);
   if (e != cudaSuccess)
     return noalloc_fail(PPS_ECUDA, std::string("pps_filter_noalloc: ") + cudaGetErrorString(e));
+  return PPS_OK;
+}
+
+extern "C" int pps_noalloc_stats(pps_stats_t* out, void* stream) {
+  if (!out) return noalloc_fail(PPS_EINVAL, "pps_noalloc_stats: out must not be NULL");
+  unsigned char* base = nullptr;
+  if (int rc = scratch_address("pps_noalloc_stats", &base)) return rc;
+  const cudaStream_t st = static_cast<cudaStream_t>(stream);
+  pps::Ctrl c;
+  cudaError_t e = cudaMemcpyAsync(&c, base + kOffCtrl, sizeof(c), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess)
+    return noalloc_fail(PPS_ECUDA, std::string("pps_noalloc_stats: ") + cudaGetErrorString(e));
+  std::memset(out, 0, sizeof(*out));
+  out->frame_cells = c.frame_cells;
+  out->overflow_vertices = c.overflow_vertices;
+  out->vertices = c.vertices;
+  out->device_error = c.error;
+  if (c.error) {
+    // clear the error word and the grid-barrier state for the next call
+    e = cudaMemsetAsync(base + kOffCtrl + offsetof(pps::Ctrl, error), 0, 3 * sizeof(unsigned int),
+                        st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess)
+      return noalloc_fail(PPS_ECUDA, std::string("pps_noalloc_stats: ") + cudaGetErrorString(e));
+    return noalloc_fail(PPS_EDEVICE, "pps_noalloc_stats: " + pps::device_error_text(c.error));
+  }
   return PPS_OK;
 }

@@ -108,6 +108,7 @@ SIGNATURES = {
     "pps_filter_noalloc": ([ctypes.POINTER(pps_params), ctypes.POINTER(pps_camera), _u32,
                             ctypes.POINTER(pps_vertices), ctypes.c_size_t,
                             ctypes.POINTER(pps_output), _vp], ctypes.c_int),
+    "pps_noalloc_stats": ([ctypes.POINTER(pps_stats_t), _vp], ctypes.c_int),
     "pps_get_tuning": ([_vp, ctypes.POINTER(pps_tuning)], ctypes.c_int),
     "pps_table_dump": ([_vp, _vp, _vp, _vp], ctypes.c_int),
     "pps_mlp_create": ([ctypes.POINTER(_vp), ctypes.POINTER(pps_mlp_params), _vp], ctypes.c_int),
@@ -303,6 +304,12 @@ def pps_filter_noalloc(params: pps_params, cam: pps_camera, frame: int, v: pps_v
                        out: pps_output, stream=None):
     _check(lib().pps_filter_noalloc(ctypes.byref(params), ctypes.byref(cam), frame & 0xFFFFFFFF,
                                     ctypes.byref(v), n, ctypes.byref(out), _stream(stream)))
+
+
+def pps_noalloc_stats(stream=None) -> dict:
+    s = pps_stats_t()
+    _check(lib().pps_noalloc_stats(ctypes.byref(s), _stream(stream)))
+    return {k: getattr(s, k) for k, _ in pps_stats_t._fields_}
 
 
 def pps_keys(handle, v: pps_vertices, n: int, h_out: torch.Tensor, f_out: torch.Tensor,

@@ -145,3 +145,27 @@ def test_selftest_wait_checks_its_arguments(kind, limit):
     pps, L = _lib()
     w = ctypes.c_uint32(7)
     assert L.pps_selftest_wait(kind, limit, ctypes.byref(w)) == pps.PPS_EINVAL
+
+
+@pytest.mark.parametrize("field,value", [("voxel_scale", float("inf")), ("pixel_angle", float("inf")),
+                                         ("log2_slots", 21), ("max_probes", 0), ("jitter", 2),
+                                         ("hist_mode", 1), ("accum_mode", 1)])
+def test_noalloc_checks_parameters_like_create_without_touching_the_gpu(field, value):
+    """pps_filter_noalloc applies pps_create's parameter checks (an infinite
+    voxel scale or pixel angle is refused as there) plus its own limits, each
+    message naming the call."""
+    pps, L = _lib()
+    p = _params(pps, **{field: value})
+    rc = L.pps_filter_noalloc(ctypes.byref(p), ctypes.byref(pps.pps_camera()), 0,
+                              ctypes.byref(pps.pps_vertices()), 0,
+                              ctypes.byref(pps.pps_output()), None)
+    assert rc == pps.PPS_EINVAL
+    assert pps.last_error().startswith("pps_filter_noalloc:")
+
+
+def test_noalloc_null_arguments_name_the_call():
+    pps, L = _lib()
+    assert L.pps_filter_noalloc(None, None, 0, None, 0, None, None) == pps.PPS_EINVAL
+    assert pps.last_error().startswith("pps_filter_noalloc:")
+    assert L.pps_noalloc_stats(None, None) == pps.PPS_EINVAL
+    assert pps.last_error().startswith("pps_noalloc_stats:")

@@ -1,5 +1,8 @@
 """Batched views: one persistent launch over several tables equals filtering
-each view on its own (bit-exact in fixed-point mode), frame after frame."""
+each view on its own (bit-exact in fixed-point mode), frame after frame, and
+every view of every frame matches the CPU oracle: bit-exact without a history,
+and with a history within the blend's rounding (8 u per blended frame) of the
+oracle's blend of the same fixed-point frame averages."""
 import numpy as np
 import pytest
 import torch
@@ -29,6 +32,30 @@ def _view(i, w, h, frame):
     return spec, {k: v[k] for k in scene.STREAMS}
 
 
+U = 2.0 ** -24
+
+
+def _against_oracle(out, cfg, view, cam, f, d, hist, blend):
+    """One view's batched results against the oracle; returns the updated
+    oracle history.  The oracle derives theta_px from the view itself."""
+    kw = cfg.oracle_kwargs()
+    kw["pixel_angle"] = O.pixel_angle(view.fov_y_deg, view.height)
+    fr = O.filter_frame(O.KeyParams(**kw), cam, f, {k: t.cpu().numpy() for k, t in d.items()})
+    st = out["status"].cpu().numpy()
+    assert not (st == 2).any()  # no probe overflow at these loads
+    cnt = out["count"].cpu().numpy().astype(np.int64)
+    got = torch.stack([out[c] for c in "rgb"], 1).cpu().numpy()
+    if not blend:
+        assert np.array_equal(cnt, fr.count)
+        assert np.array_equal(got, fr.mean_fixed)
+        return hist
+    hist, val, n = O.blend(hist, fr, 0.2, c_new=O.fixed_mean_f32(fr.cell_fixed, fr.cell_count))
+    assert np.array_equal(cnt, n)
+    rel = np.abs(got.astype(np.float64) - val) / np.abs(val)
+    assert np.all(rel <= 8 * U * (f + 1)), f"frame {f}: max rel {rel.max():.3e}"
+    return hist
+
+
 @pytest.mark.parametrize("hist,blend", [(0, False), (1, True)])
 def test_batch_equals_separate_views(hist, blend):
     frames = 3
@@ -46,6 +73,7 @@ def test_batch_equals_separate_views(hist, blend):
         outs.append(pps.empty_output(d["px"].numel(), "cuda"))
     batch = pps.Batch([(tabs_b[i], data[i][1], outs[i]) for i in range(len(SIZES))],
                       blend=blend, alpha=0.2)
+    ohist = [O.History.empty() for _ in SIZES]
     for f in range(frames):
         cams = []
         for i, (w, h, _) in enumerate(SIZES):
@@ -62,16 +90,8 @@ def test_batch_equals_separate_views(hist, blend):
                 assert torch.equal(outs[i][c], ref[c]), (f, i, c)
             st = tabs_b[i].stats()
             assert st["vertices"] == data[i][1]["px"].numel()
-    # one view against the oracle (last frame, no history)
-    if hist == 0:
-        spec, d = data[1]
-        fr = O.filter_frame(O.KeyParams(**cfgs[1].oracle_kwargs()), cams[1], frames - 1,
-                            {k: t.cpu().numpy() for k, t in d.items()})
-        st = outs[1]["status"].cpu().numpy()
-        ok = st != 2
-        assert np.array_equal(outs[1]["count"].cpu().numpy()[ok].astype(np.int64), fr.count[ok])
-        assert np.array_equal(torch.stack([outs[1][c] for c in "rgb"], 1).cpu().numpy()[ok],
-                              fr.mean_fixed[ok])
+            ohist[i] = _against_oracle(outs[i], cfgs[i], data[i][0].view, cams[i], f, data[i][1],
+                                       ohist[i], blend)
     batch.close()
     for t in tabs_b + tabs_s:
         t.close()

@@ -56,8 +56,19 @@ def _np(v, n=None):
     return {k: (v[k][:n] if n is not None else v[k]).cpu().numpy() for k in scene.STREAMS}
 
 
-def _oracle(cfg, cam, frame, v_np, ids=None):
-    return O.filter_frame(O.KeyParams(**cfg.oracle_kwargs()), cam, frame, v_np, ids=ids)
+def _kp(cfg, view=None):
+    """The oracle's key parameters.  With the view given, the oracle derives
+    theta_px from the view's vertical field of view and height itself, so the
+    value the library was handed must agree with the oracle's derivation for
+    the keys to match."""
+    kw = cfg.oracle_kwargs()
+    if view is not None:
+        kw["pixel_angle"] = O.pixel_angle(view.fov_y_deg, view.height)
+    return O.KeyParams(**kw)
+
+
+def _oracle(cfg, cam, frame, v_np, ids=None, view=None):
+    return O.filter_frame(_kp(cfg, view), cam, frame, v_np, ids=ids)
 
 
 def _rgb(out):
@@ -112,7 +123,7 @@ def test_keys_bit_exact(jitter, nih):
     tab = pps.Table(cfg)
     tab.build(spec.view.eye, 7)
     h, f = tab.keys(_dev(v, n))
-    kw = cfg.oracle_kwargs()
+    kw = _kp(cfg, spec.view).__dict__.copy()
     kw["log2_slots"] = 32  # full 32-bit home hash
     k = O.vertex_keys(O.KeyParams(**kw), spec.view.eye, 7,
                       *(v[c][:n].numpy() for c in ("px", "py", "pz", "nx", "ny", "nz")))
@@ -132,11 +143,11 @@ def test_keys_degenerate_inputs():
     nz = np.array([-1.0, -0.0, 1.0, 0.0, -0.0], np.float32)
     rgb = np.ones(5, np.float32)
     v = {k: torch.from_numpy(a) for k, a in zip(scene.STREAMS, (px, py, pz, nx, ny, nz, rgb, rgb, rgb))}
-    _, cfg = _small()
+    spec, cfg = _small()
     tab = pps.Table(cfg)
     tab.build(cam, 3)
     h, f = tab.keys(_dev(v))
-    kw = cfg.oracle_kwargs()
+    kw = _kp(cfg, spec.view).__dict__.copy()
     kw["log2_slots"] = 32
     k = O.vertex_keys(O.KeyParams(**kw), cam, 3, px, py, pz, nx, ny, nz)
     assert np.array_equal(h.cpu().numpy().view(np.uint32), k.home)
@@ -154,7 +165,7 @@ def test_fused_filter_matches_oracle(fixed, batch):
     tab.tune(batch)
     assert pps.pps_get_tuning(tab.handle)["batch"] == batch
     out = tab.filter(_dev(v, n), spec.view.eye, 2)
-    fr = _oracle(cfg, spec.view.eye, 2, _np(v, n))
+    fr = _oracle(cfg, spec.view.eye, 2, _np(v, n), view=spec.view)
     _check_frame(out, fr, fixed)
     st = tab.stats()
     assert st["frame_cells"] == fr.tuples.shape[0]
@@ -204,7 +215,7 @@ def test_split_path_matches_oracle_and_audit(fixed):
     tab.insert({k: d[k][half:] for k in d}, slots[half:], id_base=half)
     out1 = tab.query(d, slots)
     out2 = tab.query(d)  # re-probing lookup
-    fr = _oracle(cfg, spec.view.eye, 1, _np(v))
+    fr = _oracle(cfg, spec.view.eye, 1, _np(v), view=spec.view)
     _check_frame(out1, fr, fixed)
     _check_frame(out2, fr, fixed)
     if fixed:
@@ -221,6 +232,48 @@ def test_split_path_matches_oracle_and_audit(fixed):
     tab.build(spec.view.eye, 2)  # empties the frame through the dirty list
     fp2, acc2 = tab.dump()
     assert not fp2.any() and not acc2.any()
+    tab.close()
+
+
+def test_one_voxel_past_2_24_members():
+    """One voxel holding 2^24 + 5 vertices (all at one point with one normal,
+    jitter off, so every key is the same).  Fixed-point accumulation counts in
+    64 bits: every vertex gets count 2^24 + 5 and the global mean bit for bit
+    (the oracle's fixed-point mean of all contributions).  FP32 accumulation
+    keeps the count in an FP32 lane, exact only below 2^24: the lookup raises
+    the count-saturated bit of the device error word and pps_stats reports
+    PPS_EDEVICE instead of returning a wrong count silently."""
+    n = (1 << 24) + 5
+    rng = np.random.default_rng(11)
+    rgb = rng.lognormal(-1.0, 1.5, (n, 3)).astype(np.float32)
+    const = {"px": 0.3, "py": 0.0, "pz": 0.7, "nx": 0.0, "ny": 1.0, "nz": 0.0}
+    d = {k: torch.full((n,), c, dtype=torch.float32, device="cuda") for k, c in const.items()}
+    for i, c in enumerate("rgb"):
+        d[c] = torch.from_numpy(np.ascontiguousarray(rgb[:, i])).cuda()
+    fx = O.to_fixed(rgb).sum(axis=0, dtype=np.int64)
+    want = O.fixed_mean_f32(fx[None, :], np.array([n], dtype=np.int64))[0]
+    # the oracle's keys of a few of these vertices: one tuple
+    spec, cfg = _small(jitter=False, accum_fixed=True, log2_slots=16)
+    few = {k: np.full(8, c, np.float32) for k, c in const.items()}
+    few.update({c: rgb[:8, i].copy() for i, c in enumerate("rgb")})
+    assert _oracle(cfg, spec.view.eye, 0, few).tuples.shape[0] == 1
+    tab = pps.Table(cfg)
+    out = tab.filter(d, spec.view.eye, 0)
+    torch.cuda.synchronize()
+    assert bool((out["count"] == n).all())
+    assert bool((out["status"] == 0).all())
+    got = _rgb(out)
+    assert np.array_equal(got, np.broadcast_to(want, got.shape)), (got[0], want)
+    assert tab.stats()["device_error"] == 0
+    tab.close()
+    spec, cfg = _small(jitter=False, accum_fixed=False, log2_slots=16)
+    tab = pps.Table(cfg)
+    tab.filter(d, spec.view.eye, 0)
+    torch.cuda.synchronize()
+    with pytest.raises(pps.PPSError) as e:
+        tab.stats()
+    assert e.value.code == pps.PPS_EDEVICE and "2^24" in str(e.value)
+    assert tab.stats()["device_error"] == 0  # the word was cleared
     tab.close()
 
 
@@ -330,7 +383,7 @@ def test_temporal_blend_matches_oracle(hist_mode, alpha, fused, batch):
             tab.insert(d, slots)
             tab.blend(alpha)
             out = tab.query(d, slots)
-        fr = _oracle(cfg, spec.view.eye, f, _np(v))
+        fr = _oracle(cfg, spec.view.eye, f, _np(v), view=spec.view)
         hist, val, cnt = O.blend(hist, fr, alpha, fp16=hist_mode == 2,
                                  n_cap=65535 if hist_mode == 2 else None)
         assert np.array_equal(out["count"].cpu().numpy().astype(np.int64), cnt)
@@ -445,12 +498,12 @@ def test_hd_frame_full_size_in_bench_configuration():
         d = {k: v[k] for k in scene.STREAMS}
         out = tab.filter(d, spec.view.eye, f, blend=True, alpha=cfg.alpha)
         vn = _np(d)
-        fr_full = _oracle(cfg, spec.view.eye, f, vn)
+        fr_full = _oracle(cfg, spec.view.eye, f, vn, view=spec.view)
         ovf = _audit_overflow(out, vn, fr_full)
         assert ovf.sum() < 1e-5 * ovf.size  # rare at load 0.28 with 16 probes
         keep = np.nonzero(~ovf)[0]
         fr = _oracle(cfg, spec.view.eye, f, {k: a[keep] for k, a in vn.items()},
-                     ids=keep.astype(np.uint32))
+                     ids=keep.astype(np.uint32), view=spec.view)
         hist, val, cnt = O.blend(hist, fr, cfg.alpha)
         assert np.array_equal(out["count"].cpu().numpy().astype(np.int64)[keep], cnt)
         got = _rgb(out).astype(np.float64)[keep]

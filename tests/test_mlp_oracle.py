@@ -109,3 +109,161 @@ def test_sample_selection_picks_eligible_vertices_uniformly():
     assert ((h - e) ** 2 / e).sum() < elig.size + 6 * np.sqrt(2 * elig.size)  # chi-square
     assert np.array_equal(idx, M.select_samples(count, 11, 3, 1, 20000, 8))
     assert not np.array_equal(idx, M.select_samples(count, 11, 3, 2, 20000, 8))
+
+
+# ----------------------------------------------------------------------------
+# The per-element error bounds (forward_bounds, backward_bounds,
+# adam_first_step_bounds) against an independent FP32 evaluation of the same
+# network: products of BF16 numbers summed in FP32 in random orders, FP32 bias
+# additions, the encoding perturbed within its stated error before its BF16
+# rounding.  Every such evaluation must land inside the bounds, element by
+# element; planted mistakes must fall outside somewhere.
+# ----------------------------------------------------------------------------
+from mlp_cases import random_weights, structured_weights  # noqa: E402
+
+F = np.float32
+
+
+def _f32_sum(P, axis, rng):
+    """Sum float32 products along `axis` in a random order, rounding to FP32
+    after every addition."""
+    P = np.moveaxis(P, axis, -1)
+    P = P[..., rng.permutation(P.shape[-1])]
+    return np.cumsum(P, axis=-1, dtype=F)[..., -1]
+
+
+def _bf(x):
+    return M.bf16_round(np.asarray(x, dtype=F)).astype(F)
+
+
+def _emu_forward(flat, X, enc_err, rng, skip_bias=None, shift_col=False):
+    layers = M.unpack(np.asarray(flat, dtype=np.float64))
+    g = (X + rng.uniform(-1.0, 1.0, X.shape) * enc_err * 0.999).astype(F)
+    h = _bf(g)
+    xs = []
+    y = None
+    for li, (W, b) in enumerate(layers):
+        xs.append(h)
+        Wb = _bf(W)
+        if shift_col and li == 0:
+            Wb = np.roll(Wb, 1, axis=1)
+        s = _f32_sum(h[:, None, :] * Wb[None, :, :], 2, rng)
+        z = s if skip_bias == li else (s + F(b)).astype(F)
+        if li < len(layers) - 1:
+            h = _bf(np.maximum(z, F(0)))
+        else:
+            y = z
+    return xs, y
+
+
+def _emu_backward(flat, xs, y, T, valid, batch, rng, drop=None, flip=False):
+    layers = M.unpack(np.asarray(flat, dtype=np.float64))
+    diff = ((y - T.astype(F)).astype(F) * valid[:, None].astype(F)).astype(F)
+    d = _bf((diff * F(1.0 / batch)).astype(F))
+    if flip:
+        d = -d
+    if drop is not None:
+        d = d.copy()
+        d[drop] = 0
+    grads = [None] * len(layers)
+    for li in range(len(layers) - 1, -1, -1):
+        W, _ = layers[li]
+        x = xs[li]
+        gW = _f32_sum(d[:, :, None] * x[:, None, :], 0, rng)
+        gb = _f32_sum(d, 0, rng)
+        grads[li] = (gW.astype(np.float64), gb.astype(np.float64))
+        if li > 0:
+            dh = _f32_sum(d[:, :, None] * _bf(W)[None, :, :], 1, rng)
+            d = _bf(np.where(x > 0, dh, F(0)))
+    return M.pack(grads)
+
+
+def _emu_adam(flat, g, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
+    g = g.astype(F)
+    m = (F(1 - b1) * g).astype(F)
+    v = ((F(1 - b2) * g).astype(F) * g).astype(F)
+    step = (F(lr) * ((m / F(1 - b1)).astype(F) / (np.sqrt((v / F(1 - b2)).astype(F)) + F(eps))
+                     .astype(F)).astype(F)).astype(F)
+    return (np.asarray(flat, F) - step).astype(np.float64)
+
+
+def _case(n, seed):
+    rng = np.random.default_rng(seed)
+    p = rng.uniform(-30, 30, (n, 3)).astype(np.float32)
+    nn = rng.normal(size=(n, 3))
+    nn = (nn / np.linalg.norm(nn, axis=1, keepdims=True)).astype(np.float32)
+    t = rng.lognormal(-1, 1.0, (n, 3))
+    return M.encode(p, nn, (-100.0,) * 3, (100.0,) * 3), t
+
+
+def _structured_all(seed):
+    return structured_weights(seed, "all")
+
+
+@pytest.mark.parametrize("weights", [random_weights, structured_weights, _structured_all])
+@pytest.mark.parametrize("seed", [1, 2])
+def test_bounds_hold_for_fp32_evaluations_in_random_orders(weights, seed):
+    w = weights(10 + seed).astype(np.float64)
+    X, T = _case(256, seed)
+    valid = np.ones(256)
+    valid[[3, 100, 255]] = 0
+    enc = M.encoding_error()
+    fb = M.forward_bounds(w, X, enc)
+    g, eg = M.backward_bounds(w, fb, T, valid, 256)
+    w1, ew = M.adam_first_step_bounds(w, g, eg)
+    for trial in range(3):
+        rng = np.random.default_rng(100 * seed + trial)
+        xs, y = _emu_forward(w, X, enc, rng)
+        assert np.all(np.abs(y - fb.acts.y) <= fb.ey)
+        ge = _emu_backward(w, xs, y, T, valid, 256, rng)
+        assert np.all(np.abs(ge - g) <= eg)
+        assert np.all(np.abs(_emu_adam(w, ge) - w1) <= ew)
+
+
+def test_structured_network_bounds_are_tight():
+    """With pass-through hidden layers the bounds shrink to FP32 size almost
+    everywhere: the output within 1e-4 of its scale, weight gradients within
+    1e-3 of their magnitude (a sum over 256 samples), and the first Adam step
+    (about lr times the gradient's sign) certain for almost every weight."""
+    w = structured_weights(3).astype(np.float64)
+    X, T = _case(256, 3)
+    valid = np.ones(256)
+    fb = M.forward_bounds(w, X, M.encoding_error())
+    scale = np.sqrt((fb.acts.y ** 2).mean())
+    assert np.median(fb.ey) <= 1e-4 * scale
+    g, eg = M.backward_bounds(w, fb, T, valid, 256)
+    nz = np.abs(g) > 1e-6
+    assert np.median(eg[nz] / np.abs(g[nz])) <= 1e-3
+    _, ew = M.adam_first_step_bounds(w, g, eg)
+    assert np.mean(ew < 1e-5) > 0.95
+
+
+def test_bounds_catch_planted_mistakes():
+    """An FP32 evaluation with a mistake in it -- a sample left out of the
+    gradient, a bias not added, the first layer reading the next input
+    column, the output delta's sign flipped -- leaves the bounds somewhere."""
+    w = structured_weights(4).astype(np.float64)
+    X, T = _case(256, 4)
+    valid = np.ones(256)
+    enc = M.encoding_error()
+    fb = M.forward_bounds(w, X, enc)
+    g, eg = M.backward_bounds(w, fb, T, valid, 256)
+    rng = np.random.default_rng(5)
+    xs, y = _emu_forward(w, X, enc, rng, skip_bias=3)
+    assert np.any(np.abs(y - fb.acts.y) > fb.ey)
+    xs, y = _emu_forward(w, X, enc, rng, shift_col=True)
+    assert np.any(np.abs(y - fb.acts.y) > fb.ey)
+    xs, y = _emu_forward(w, X, enc, rng)
+    for kw in (dict(drop=17), dict(flip=True)):
+        ge = _emu_backward(w, xs, y, T, valid, 256, rng, **kw)
+        assert np.any(np.abs(ge - g) > eg), kw
+    # the random network catches them too
+    w = random_weights(6).astype(np.float64)
+    fb = M.forward_bounds(w, X, enc)
+    g, eg = M.backward_bounds(w, fb, T, valid, 256)
+    xs, y = _emu_forward(w, X, enc, rng)
+    ge = _emu_backward(w, xs, y, T, valid, 256, rng, drop=17)
+    assert np.any(np.abs(ge - g) > eg)
+    for li in (0, 3):
+        xs, y = _emu_forward(w, X, enc, rng, skip_bias=li)
+        assert np.any(np.abs(y - fb.acts.y) > fb.ey), li

@@ -459,3 +459,20 @@ def test_fixed_point_mean_of_dyadic_values_is_exact():
         for n in (1, 3, 1000, 12345):
             s = np.array([[round(c * 2 ** 24) * n] * 3], dtype=np.int64)
             assert np.all(O.fixed_mean_f32(s, np.array([n])) == np.float32(c)), (c, n)
+
+
+def test_pixel_angle_closed_forms():
+    """theta_px = 2 tan(fov_y / 2) / height: tan 30 deg = 1 / sqrt 3 and
+    tan 45 deg = 1 give closed forms; the vertical field of view pairs with
+    the image height (a width, or a slip between degrees and radians, moves
+    the value by a large factor)."""
+    assert math.isclose(O.pixel_angle(60.0, 1080), 2.0 / (math.sqrt(3.0) * 1080), rel_tol=1e-15)
+    assert math.isclose(O.pixel_angle(90.0, 512), 2.0 / 512, rel_tol=1e-15)
+    assert math.isclose(O.pixel_angle(60.0, 256), 2.0 / (math.sqrt(3.0) * 256), rel_tol=1e-15)
+    # the angle between the rays through the top and bottom edges of the
+    # central pixel row, 2 atan(tan(fov / 2) / H), is theta_px up to the
+    # small-angle term theta^2 / 12
+    for fov, h in [(60.0, 1080), (60.0, 720), (45.0, 2160)]:
+        th = O.pixel_angle(fov, h)
+        edge = 2.0 * math.atan(math.tan(math.radians(fov) / 2.0) / h)
+        assert abs(edge - th) <= th ** 3 / 12 * 1.01 + 1e-18
