@@ -243,14 +243,29 @@ typedef struct pps_stats_t {
 } pps_stats_t;
 
 /*
- * Launch shape of a table's kernels (no effect on results).
- *  batch     vertices each thread carries through one insert step together
- *            (their probes and atomics overlap): 2 or 4; 0 = library default (2).
- *  reserved  must be zero.
+ * Launch shape of a table's kernels (no effect on results up to the order of
+ * FP32 additions; fixed-point results are identical).
+ *  batch      per-thread insert: vertices each thread carries through one
+ *             insert step together (their probes and atomics overlap): 2 or 4;
+ *             0 = library default (2).  Also used by the split kernels and the
+ *             batched launch.
+ *  insert     how pps_filter's persistent launch inserts: 0 = library default
+ *             (pipelined), 1 = per thread (each thread builds its vertices'
+ *             keys, then probes and accumulates them), 2 = pipelined (key
+ *             warps build keys, merge equal ones within the warp and queue one
+ *             entry per distinct key in shared memory; probe warps run the
+ *             table operations of four queued keys per thread at once).  Frames
+ *             with an evicting history or the neighborhood fallback always
+ *             insert per thread.
+ *  key_warps  pipelined insert: key warps of the 16 warps of a CTA (the rest
+ *             probe): 4, 8 or 12; 0 = library default (8).
+ *  reserved   must be zero.
  */
 typedef struct pps_tuning {
   uint32_t batch;
-  uint32_t reserved[7];
+  uint32_t insert;
+  uint32_t key_warps;
+  uint32_t reserved[5];
 } pps_tuning;
 
 typedef struct pps_table pps_table;

@@ -192,6 +192,13 @@ bool temporal(const pps_table* t) { return t->p.hist_mode != PPS_HIST_NONE; }
 
 int batch_of(const pps_table* t) { return t->tune.batch == 4 ? 4 : 2; }
 
+pps::InsertShape insert_shape(const pps_table* t) {
+  pps::InsertShape s;
+  s.pipelined = t->tune.insert == 1 ? 0 : 1;
+  s.key_warps = t->tune.key_warps ? static_cast<int>(t->tune.key_warps) : 8;
+  return s;
+}
+
 // Empty the cells of the split path's frame (the fused path leaves none behind)
 // and reset the frame counters.
 int reset_frame(pps_table* t, cudaStream_t st) {
@@ -510,7 +517,7 @@ int filter_one(pps_table* t, const pps_camera* cam, uint32_t frame, const pps_ve
   if (n == 0) return PPS_OK;
   pps::FusedPlan plan;
   PPS_CUDA(pps::plan_fused(n, temporal(t), batch_of(t), &plan, t->dev.hist_evict != 0,
-                           t->dev.neighbors != 0));
+                           t->dev.neighbors != 0, insert_shape(t), t->dev.fixed != 0));
   // cell ids and (off-chip) stash words cover whole tiles: [0, ntiles * tile)
   const size_t ftile = static_cast<size_t>(pps::fused_tile_size());
   const size_t stash_need = (n + ftile - 1) / ftile * ftile;
@@ -774,6 +781,9 @@ int pps_set_tuning(pps_table* t, const pps_tuning* tune) {
   if (!tune) return fail(PPS_EINVAL, "tuning is NULL");
   if (tune->batch != 0 && tune->batch != 2 && tune->batch != 4)
     return fail(PPS_EINVAL, "batch must be 0, 2 or 4");
+  if (tune->insert > 2) return fail(PPS_EINVAL, "insert must be 0, 1 or 2");
+  if (tune->key_warps != 0 && tune->key_warps != 4 && tune->key_warps != 8 && tune->key_warps != 12)
+    return fail(PPS_EINVAL, "key_warps must be 0, 4, 8 or 12");
   for (uint32_t r : tune->reserved)
     if (r) return fail(PPS_EINVAL, "reserved fields must be zero");
   t->tune = *tune;
@@ -786,6 +796,8 @@ int pps_get_tuning(pps_table* t, pps_tuning* tune) {
   if (!tune) return fail(PPS_EINVAL, "tuning is NULL");
   *tune = t->tune;
   tune->batch = static_cast<uint32_t>(batch_of(t));
+  tune->insert = t->tune.insert == 1 ? 1u : 2u;
+  tune->key_warps = t->tune.key_warps ? t->tune.key_warps : 8u;
   return PPS_OK;
 }
 

@@ -323,6 +323,51 @@ __device__ __forceinline__ unsigned long long l2_evict_last() {
   return pol;
 }
 
+// L2 eviction priority "evict first" for data a frame touches once and the
+// next frame does not need in L2 (cell records, history cells, the stash):
+// they should not push the slot index and the accumulators out.  Loads of such
+// data written by other CTAs of the same launch bypass L1 (.cg).
+__device__ __forceinline__ unsigned long long l2_evict_first() {
+  unsigned long long pol;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+
+__device__ __forceinline__ uint4 ld_once_u4(const void* p) {
+  uint4 v;
+  asm volatile("ld.global.cg.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+               : "l"(p), "l"(l2_evict_first())
+               : "memory");
+  return v;
+}
+
+__device__ __forceinline__ uint2 ld_once_u2(const void* p) {
+  uint2 v;
+  asm volatile("ld.global.cg.L2::cache_hint.v2.u32 {%0, %1}, [%2], %3;"
+               : "=r"(v.x), "=r"(v.y)
+               : "l"(p), "l"(l2_evict_first())
+               : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_once_u4(void* p, uint4 v) {
+  asm volatile("st.global.L2::cache_hint.v4.u32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(p), "r"(v.x),
+               "r"(v.y), "r"(v.z), "r"(v.w), "l"(l2_evict_first())
+               : "memory");
+}
+
+__device__ __forceinline__ void st_once_u2(void* p, uint2 v) {
+  asm volatile("st.global.L2::cache_hint.v2.u32 [%0], {%1, %2}, %3;" ::"l"(p), "r"(v.x), "r"(v.y),
+               "l"(l2_evict_first())
+               : "memory");
+}
+
+__device__ __forceinline__ void st_once_u32(void* p, uint32_t v) {
+  asm volatile("st.global.L2::cache_hint.u32 [%0], %1, %2;" ::"l"(p), "r"(v), "l"(l2_evict_first())
+               : "memory");
+}
+
 __device__ __forceinline__ unsigned long long ld_relaxed_u64_keep(const unsigned long long* p) {
   unsigned long long v;
   asm volatile("ld.relaxed.gpu.global.L2::cache_hint.u64 %0, [%1], %2;"
@@ -567,13 +612,13 @@ __device__ __forceinline__ HistRaw load_hist(const TableDev& t, uint32_t h) {
   HistRaw o;
   const unsigned char* c = t.hcells + static_cast<size_t>(h) * t.hstride;
   if (t.hist_mode == 1) {
-    const float4 v = __ldcg(reinterpret_cast<const float4*>(c));
-    o.r = v.x;
-    o.g = v.y;
-    o.b = v.z;
-    o.n = __float_as_uint(v.w);
+    const uint4 v = ld_once_u4(c);
+    o.r = __uint_as_float(v.x);
+    o.g = __uint_as_float(v.y);
+    o.b = __uint_as_float(v.z);
+    o.n = v.w;
   } else {
-    const uint2 v = __ldcg(reinterpret_cast<const uint2*>(c));
+    const uint2 v = ld_once_u2(c);
     const float2 rg = __half22float2(*reinterpret_cast<const __half2*>(&v.x));
     o.r = rg.x;
     o.g = rg.y;
@@ -606,14 +651,14 @@ __device__ __forceinline__ void blend_store(const TableDev& t, uint32_t id, uint
     unsigned char* c = t.hcells + static_cast<size_t>(h) * t.hstride;
     if (t.hist_mode == 1) {
       N = old.n + m.n;
-      __stcg(reinterpret_cast<float4*>(c), make_float4(cr, cg, cb, __uint_as_float(N)));
+      st_once_u4(c, make_uint4(__float_as_uint(cr), __float_as_uint(cg), __float_as_uint(cb), N));
     } else {
       N = min(old.n + m.n, 65535u);
       const __half2 rg = __floats2half2_rn(cr, cg);
       const __half hb = __float2half_rn(cb);
       const uint32_t lo = *reinterpret_cast<const uint32_t*>(&rg);
       const uint32_t hi = static_cast<uint32_t>(__half_as_ushort(hb)) | (N << 16);
-      __stcg(reinterpret_cast<uint2*>(c), make_uint2(lo, hi));
+      st_once_u2(c, make_uint2(lo, hi));
       // lookups see what the history stores
       const float2 back = __half22float2(rg);
       cr = back.x;

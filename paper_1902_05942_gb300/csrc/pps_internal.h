@@ -22,6 +22,13 @@ struct FusedPlan {
   bool global_stash = false;
   bool evict = false;      // the kernel variant for an evicting history
   bool neigh = false;      // the kernel variant with the neighborhood search
+  int key_warps = 0;       // > 0: the pipelined insert (k_fused_ws) with this many key warps
+};
+
+// How a table's persistent launch inserts (pps_tuning.insert / key_warps).
+struct InsertShape {
+  int pipelined = 1;  // 1: key warps and probe warps on alternate chunks; 0: per thread
+  int key_warps = 8;  // of the 16 warps of a CTA (4, 8 or 12)
 };
 
 // One view of a batched launch: its table, key constants, vertices and
@@ -78,7 +85,7 @@ cudaError_t launch_combine_coarse(size_t n, const uint8_t* fine_status, const Ou
 cudaError_t launch_count_nonzero(const void* base, uint32_t stride, uint32_t off, uint32_t width,
                                  uint64_t n, unsigned long long* out, cudaStream_t st);
 cudaError_t plan_fused(size_t n, bool temporal, int batch, FusedPlan* plan, bool evict = false,
-                       bool neigh = false);
+                       bool neigh = false, InsertShape shape = InsertShape{}, bool fixed = false);
 cudaError_t launch_fused(const KeyConst& kc, const TableDev& t, const VertexPtrs& v, size_t n,
                          const OutPtrs& o, bool temporal, bool blend, float alpha,
                          const FusedPlan& plan, uint32_t* gstash, uint32_t* nq, cudaStream_t st);

@@ -12,6 +12,10 @@
 //                  cell id stays in shared memory between the phases; the
 //                  blend's tiles come from a second counter, and each CTA
 //                  clears the cells its own tiles created.
+//  k_fused_ws      the same frame with a pipelined insert: key warps build
+//                  and merge keys into a shared-memory queue while probe warps
+//                  run the table operations of the previous chunk (the default
+//                  for frames without eviction or neighborhood search).
 //  k_fused<NEIGH>, k_neighbors, k_clear_fused
 //                  neighborhood-search frames: the persistent kernel queues
 //                  its low-count vertices after the lookups, a separate launch
@@ -275,8 +279,8 @@ __device__ __forceinline__ Batch<W> insert_batch(const KeyConst& kc, const Table
     }
     // record the cell, or mark a reserved id that ended up unused
     if (rec && my[q] != kOverflowSlot)
-      __stcg(t.info + my[q], claimed[q] ? make_uint4(slot[q], h1[q], f[q], kOverflowSlot)
-                                        : make_uint4(kNoSlot, 0u, 0u, kOverflowSlot));
+      st_once_u4(t.info + my[q], claimed[q] ? make_uint4(slot[q], h1[q], f[q], kOverflowSlot)
+                                            : make_uint4(kNoSlot, 0u, 0u, kOverflowSlot));
     if constexpr (KREC)
       if (claimed[q]) __stcg(t.kw + my[q], kr[q]);
   }
@@ -561,7 +565,7 @@ __device__ __forceinline__ void blend_range(const TableDev& t, uint32_t base, ui
       home[q] = 0u;
       f[q] = 0u;
       if (k < count) {
-        const uint4 in = __ldcg(t.info + d[q]);
+        const uint4 in = ld_once_u4(t.info + d[q]);
         use[q] = in.x != kNoSlot;
         home[q] = in.y & t.hmask;
         f[q] = in.z;
@@ -583,7 +587,7 @@ __device__ __forceinline__ void blend_range(const TableDev& t, uint32_t base, ui
 __device__ __forceinline__ void clear_range(const TableDev& t, uint32_t base, uint32_t count,
                                             uint32_t first, uint32_t stride, bool slots_swept) {
   for (uint32_t k = first; k < count; k += stride) {
-    const uint32_t slot = slots_swept ? kNoSlot : __ldcg(t.info + base + k).x;
+    const uint32_t slot = slots_swept ? kNoSlot : ld_once_u4(t.info + base + k).x;
     clear_cell(t, base + k, slot);
   }
 }
@@ -1046,6 +1050,435 @@ __global__ void __launch_bounds__(kFusedBlock, W == 4 ? 1 : 2) k_fused(FusedArgs
                 static_cast<size_t>(gridDim.x) * blockDim.x);
 }
 
+// ------------------------------------------------------------------ pipelined insert
+// k_fused_ws: the persistent kernel with its insert (phase A) split between
+// two groups of warps that work on different chunks of vertices at once.
+//
+//  key warps    read a chunk's vertex streams (coalesced; two vertices per
+//               thread at a time, whose keys are built together so that their
+//               chains of Philox rounds and hash steps overlap), build each
+//               vertex's key (Algorithm 1), merge equal keys within the
+//               warp (__match_any_sync: the lowest lane of each group of equal
+//               keys becomes its leader and the members add their
+//               contributions to the leader's entry with shared-memory
+//               atomics), and append one queue entry per distinct key:
+//               {home hash, fingerprint, member lanes, first vertex of the
+//               warp} and the group's sums and count.
+//  probe warps  take a full chunk's entries, four per thread at a time, and
+//               run the table operations of Sec. 3.2 for all four together
+//               (first probes, id claims, compare-and-swaps, the rare longer
+//               probes, then the accumulating reductions); each entry's cell id
+//               goes to the stash word of every member vertex.
+//
+// Two queue buffers alternate, so the key warps fill one chunk while the
+// probe warps drain the other.  The handover uses two mbarriers per buffer
+// (full: every key thread arrives after writing its entries; empty: every
+// probe thread arrives after reading them), waited with a bounded
+// try_wait loop (about two seconds of wall time, then kErrBarrierTimeout and
+// the launch ends like a timed-out grid barrier).  The key warps decide
+// together whether to go on (a named-barrier AND vote), so none of them is
+// left waiting at a barrier.  The stash is the global one (indexed by
+// vertex); phases B, C and D are those of k_fused.  Cell records, stash words
+// and history cells are written and read with an evict-first L2 policy, so
+// that the slot index and the accumulators stay in L2.
+constexpr int kWsChunk = 1024;  // vertices per queue chunk: half a tile
+constexpr int kWsChunksPerTile = kFusedTile / kWsChunk;
+constexpr uint32_t kWsEnd = 0xFFFFFFFFu;  // chunk header: no more tiles
+
+struct WsHeader {
+  uint32_t count;  // entries in the chunk
+  uint32_t k;      // the tile's place in this CTA's tile list
+  uint32_t tile;   // the tile, or kWsEnd
+};
+
+__device__ __forceinline__ void mbar_init(uint64_t* m, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(
+                   static_cast<uint32_t>(__cvta_generic_to_shared(m))),
+               "r"(count)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* m) {
+  unsigned long long state;
+  asm volatile("mbarrier.arrive.shared::cta.b64 %0, [%1];"
+               : "=l"(state)
+               : "r"(static_cast<uint32_t>(__cvta_generic_to_shared(m)))
+               : "memory");
+  (void)state;
+}
+
+// Wait for the phase of parity `parity` of mbarrier m to complete, for about
+// `limit_ns` of wall time at most; false when the wait gave up.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* m, uint32_t parity,
+                                                  unsigned long long limit_ns = 2000000000ull) {
+  const uint32_t a = static_cast<uint32_t>(__cvta_generic_to_shared(m));
+  const unsigned long long t0 = globaltimer_ns();
+  for (;;) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (globaltimer_ns() - t0 > limit_ns) return false;
+  }
+}
+
+// AND of `pred` over the `nthreads` threads that use named barrier `id`.
+__device__ __forceinline__ bool bar_and(int id, int nthreads, bool pred) {
+  uint32_t r;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n"
+      " bar.red.and.pred q, %2, %3, p;\n selp.u32 %0, 1, 0, q;\n}"
+      : "=r"(r)
+      : "r"(pred ? 1u : 0u), "r"(id), "r"(nthreads)
+      : "memory");
+  return r != 0;
+}
+
+// Shared-memory layout of k_fused_ws (dynamic part), for `fixed` accumulation.
+struct WsLayout {
+  static constexpr size_t kHeaders = 64;  // 2 headers + 4 mbarriers (full[2], empty[2])
+  __host__ __device__ static constexpr size_t keys_off() { return kHeaders; }
+  __host__ __device__ static constexpr size_t sums_off() {
+    return kHeaders + 2 * kWsChunk * sizeof(uint4);
+  }
+  // float4 words per entry: {r, g, b, count} FP32, or int64 r, g, b, count
+  __host__ __device__ static constexpr size_t sum_words(bool fixed) { return fixed ? 2 : 1; }
+  __host__ __device__ static constexpr size_t bytes(bool fixed) {
+    return sums_off() + 2 * kWsChunk * sum_words(fixed) * sizeof(float4);
+  }
+};
+
+// Append the queue entry of vertex j (valid) of this warp's lanes `vm`:
+// merge equal keys among the warp's lanes (the lowest lane of a group leads,
+// the others add their contributions to its entry), one entry per group.
+__device__ __forceinline__ void ws_enqueue(const TableDev& t, uint4* keys, float4* sums, WsHeader* h,
+                                           unsigned vm, const Key& k, size_t j, float r, float g,
+                                           float b) {
+  const uint32_t lane = threadIdx.x & 31;
+  const unsigned long long kk = (static_cast<unsigned long long>(k.h1) << 32) | k.fp;
+  const unsigned grp = __match_any_sync(vm, kk);
+  const uint32_t leader = __ffs(grp) - 1;
+  const bool lead = leader == lane;
+  const unsigned lm = __ballot_sync(vm, lead);
+  const uint32_t first = __ffs(vm) - 1;
+  uint32_t e = 0;
+  if (lane == first) e = atomicAdd(&h->count, static_cast<uint32_t>(__popc(lm)));
+  e = __shfl_sync(vm, e, first) + __popc(lm & ((1u << lane) - 1u));
+  e = __shfl_sync(vm, e, leader);
+  if (lead) {
+    keys[e] = make_uint4(k.h1, k.fp, grp, static_cast<uint32_t>(j - lane));
+    if (!t.fixed) {
+      sums[e] = make_float4(r, g, b, __uint_as_float(static_cast<uint32_t>(__popc(grp))));
+    } else {
+      long long* s = reinterpret_cast<long long*>(sums + 2 * e);
+      s[0] = to_fixed(r);
+      s[1] = to_fixed(g);
+      s[2] = to_fixed(b);
+      s[3] = __popc(grp);
+    }
+  }
+  __syncwarp(vm);
+  if (!lead) {
+    if (!t.fixed) {
+      atomicAdd(&sums[e].x, r);
+      atomicAdd(&sums[e].y, g);
+      atomicAdd(&sums[e].z, b);
+    } else {
+      unsigned long long* s = reinterpret_cast<unsigned long long*>(sums + 2 * e);
+      atomicAdd(s + 0, static_cast<unsigned long long>(to_fixed(r)));
+      atomicAdd(s + 1, static_cast<unsigned long long>(to_fixed(g)));
+      atomicAdd(s + 2, static_cast<unsigned long long>(to_fixed(b)));
+    }
+  }
+}
+
+// The key warps' work on one chunk [c0, c0 + kWsChunk) of the vertices below
+// `end`: KV vertices per thread at a time (KT apart, so that each warp's loads
+// of a stream are one coalesced run), their keys built together so that the
+// independent chains of Philox rounds and hash steps overlap.
+template <int KEYW, int KV>
+__device__ __forceinline__ void ws_key_chunk(const FusedArgs& a, uint4* keys, float4* sums,
+                                             WsHeader* h, size_t c0, size_t end) {
+  const TableDev& t = a.t;
+  const VertexPtrs& v = a.v;
+  constexpr int KT = KEYW * 32;
+  const size_t cend = min(end, c0 + kWsChunk);
+#pragma unroll 1
+  for (size_t base = c0 + threadIdx.x; base < c0 + kWsChunk; base += KV * KT) {
+    float px[KV], py[KV], pz[KV], nx[KV], ny[KV], nz[KV], r[KV], g[KV], b[KV];
+#pragma unroll
+    for (int q = 0; q < KV; ++q) {
+      const size_t j = base + q * KT;
+      const bool ok = j < cend;
+      px[q] = ok ? __ldcs(v.px + j) : 0.f;
+      py[q] = ok ? __ldcs(v.py + j) : 0.f;
+      pz[q] = ok ? __ldcs(v.pz + j) : 0.f;
+      nx[q] = ok ? __ldcs(v.nx + j) : 0.f;
+      ny[q] = ok ? __ldcs(v.ny + j) : 0.f;
+      nz[q] = ok ? __ldcs(v.nz + j) : 1.f;
+      r[q] = ok ? __ldcs(v.r + j) : 0.f;
+      g[q] = ok ? __ldcs(v.g + j) : 0.f;
+      b[q] = ok ? __ldcs(v.b + j) : 0.f;
+    }
+    Key k[KV];
+#pragma unroll
+    for (int q = 0; q < KV; ++q) {
+      const size_t j = base + q * KT;
+      k[q] = vertex_key(a.kc, px[q], py[q], pz[q], nx[q], ny[q], nz[q],
+                        j < cend ? vertex_id(v, j) : 0u, v.stream_id);
+    }
+#pragma unroll
+    for (int q = 0; q < KV; ++q) {
+      const size_t j = base + q * KT;
+      const bool valid = j < cend;
+      const unsigned vm = __ballot_sync(0xFFFFFFFFu, valid);
+      if (valid) ws_enqueue(t, keys, sums, h, vm, k[q], j, r[q], g[q], b[q]);
+    }
+  }
+}
+
+// One probe thread's entries e0, e0 + stride, ... (at most 4) of a chunk:
+// the table operations of all of them together.
+template <int PB>
+__device__ __forceinline__ void ws_probe_group(const TableDev& t, const uint4* keys,
+                                               const float4* sums, uint32_t q, uint32_t e0,
+                                               uint32_t stride, uint32_t id_base,
+                                               uint32_t* claims, uint32_t* gstash, bool rec,
+                                               Counters& cnt) {
+  uint32_t h1[PB], f[PB], mask[PB], vb[PB];
+  bool use[PB];
+#pragma unroll
+  for (int i = 0; i < PB; ++i) {
+    const uint32_t e = e0 + i * stride;
+    use[i] = e < q;
+    const uint4 kq = use[i] ? keys[e] : make_uint4(0u, 0u, 0u, 0u);
+    h1[i] = kq.x;
+    f[i] = kq.y;
+    mask[i] = kq.z;
+    vb[i] = kq.w;
+  }
+  unsigned long long w[PB];
+#pragma unroll
+  for (int i = 0; i < PB; ++i) w[i] = use[i] ? ld_relaxed_u64_keep(t.slots + (h1[i] & t.mask)) : 1ull;
+  uint32_t my[PB];
+#pragma unroll
+  for (int i = 0; i < PB; ++i)
+    my[i] = use[i] && w[i] == 0ull ? id_base + atomicAdd(claims, 1u) : kOverflowSlot;
+  unsigned long long old[PB];
+#pragma unroll
+  for (int i = 0; i < PB; ++i)
+    old[i] = my[i] != kOverflowSlot
+                 ? atomicCAS(t.slots + (h1[i] & t.mask), 0ull, slot_word(f[i], my[i]))
+                 : w[i];
+  uint32_t id[PB];
+#pragma unroll
+  for (int i = 0; i < PB; ++i) {
+    id[i] = kOverflowSlot;
+    if (!use[i]) continue;
+    const uint32_t home = h1[i] & t.mask;
+    uint32_t slot = home;
+    bool claimed = false;
+    if (my[i] != kOverflowSlot && old[i] == 0ull) {
+      id[i] = my[i];
+      claimed = true;
+    } else if (slot_fp(old[i]) == f[i]) {
+      id[i] = slot_id(old[i]);
+    } else {
+      const MoreProbe m = probe_more(t.slots, t.mask, t.max_probes, home, f[i], my[i], id_base,
+                                     claims);
+      slot = m.slot;
+      id[i] = m.id;
+      my[i] = m.my;
+      claimed = m.claimed;
+    }
+    if (rec && my[i] != kOverflowSlot)
+      st_once_u4(t.info + my[i], claimed ? make_uint4(slot, h1[i], f[i], kOverflowSlot)
+                                         : make_uint4(kNoSlot, 0u, 0u, kOverflowSlot));
+    cnt.cells += claimed ? 1u : 0u;
+  }
+#pragma unroll
+  for (int i = 0; i < PB; ++i) {
+    if (!use[i]) continue;
+    const uint32_t e = e0 + i * stride;
+    if (id[i] != kOverflowSlot) {
+      if (!t.fixed) {
+        const float4 s = sums[e];
+        red_add_v4_keep(t.acc + id[i], s.x, s.y, s.z, static_cast<float>(__float_as_uint(s.w)));
+      } else {
+        const long long* s = reinterpret_cast<const long long*>(sums + 2 * e);
+        accumulate(t, id[i], 0.f, 0.f, 0.f, s[0], s[1], s[2], static_cast<uint32_t>(s[3]));
+      }
+    } else {
+      cnt.ovf += __popc(mask[i]);
+    }
+    for (uint32_t m = mask[i]; m; m &= m - 1u) st_once_u32(gstash + vb[i] + __ffs(m) - 1, id[i]);
+  }
+}
+
+template <bool TEMPORAL, int KEYW, int PRW, int KV>
+__global__ void __launch_bounds__((KEYW + PRW) * 32, 2) k_fused_ws(FusedArgs a) {
+  extern __shared__ __align__(16) unsigned char s_dyn[];
+  __shared__ uint32_t s_tile[kMaxTilesPerCta];
+  __shared__ uint32_t s_claims[kMaxTilesPerCta];
+  __shared__ uint32_t s_cur, s_taken;
+  constexpr int KT = KEYW * 32, PT = PRW * 32;
+  const TableDev& t = a.t;
+  const uint32_t ntiles = static_cast<uint32_t>((a.n + kFusedTile - 1) / kFusedTile);
+  WsHeader* hdr = reinterpret_cast<WsHeader*>(s_dyn);
+  uint64_t* full = reinterpret_cast<uint64_t*>(s_dyn + 32);
+  uint64_t* empty = full + 2;
+  uint4* keys = reinterpret_cast<uint4*>(s_dyn + WsLayout::keys_off());
+  float4* sums = reinterpret_cast<float4*>(s_dyn + WsLayout::sums_off());
+  const size_t sw = WsLayout::sum_words(t.fixed != 0);
+  if (threadIdx.x == 0) {
+    s_taken = 0;
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(full + b, KT);
+      mbar_init(empty + b, PT);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+
+  // Phase A: key warps and probe warps on alternate chunks.
+  Counters c;
+  unsigned long long nv = 0;  // vertices of this CTA's tiles (key thread 0)
+  bool ok = true;
+  if (threadIdx.x < KT) {
+    uint32_t tile = 0, k = 0;
+    for (uint32_t ch = 0;; ++ch) {
+      const uint32_t bsel = ch & 1u;
+      bool go = true;
+      if (ch >= 2) go = mbar_wait_bounded(empty + bsel, ((ch >> 1) + 1u) & 1u);
+      if (threadIdx.x == 0 && go) {
+        if (ch % kWsChunksPerTile == 0) {
+          tile = s_taken < a.cap_tiles ? claim_tile(t.ctrl, ntiles) : ntiles;
+          if (tile < ntiles) {
+            k = s_taken;
+            s_tile[k] = tile;
+            s_claims[k] = 0;
+            s_taken = k + 1;
+            nv += min(a.n, static_cast<size_t>(tile) * kFusedTile + kFusedTile) -
+                  static_cast<size_t>(tile) * kFusedTile;
+          }
+        }
+        hdr[bsel].count = 0;
+        hdr[bsel].k = k;
+        hdr[bsel].tile = tile < ntiles ? tile : kWsEnd;
+      }
+      go = bar_and(1, KT, go);  // also publishes the header to the key warps
+      if (!go) {
+        ok = false;
+        break;
+      }
+      // this buffer's header is rewritten only after the probe warps have
+      // released it, which needs every key thread's arrival for this chunk
+      const uint32_t cur = hdr[bsel].tile;
+      if (cur != kWsEnd) {
+        const size_t t0 = static_cast<size_t>(cur) * kFusedTile;
+        ws_key_chunk<KEYW, KV>(a, keys + bsel * kWsChunk, sums + bsel * kWsChunk * sw, hdr + bsel,
+                           t0 + (ch % kWsChunksPerTile) * kWsChunk, min(a.n, t0 + kFusedTile));
+      }
+      mbar_arrive(full + bsel);
+      if (cur == kWsEnd) break;
+    }
+  } else {
+    const uint32_t pt = threadIdx.x - KT;
+    const bool rec = (TEMPORAL && a.blend) || !a.sweep;
+    for (uint32_t ch = 0;; ++ch) {
+      const uint32_t bsel = ch & 1u;
+      if (!mbar_wait_bounded(full + bsel, (ch >> 1) & 1u)) {
+        ok = false;
+        break;
+      }
+      const WsHeader hh = hdr[bsel];
+      if (hh.tile == kWsEnd) break;
+      const uint32_t id_base = hh.tile * static_cast<uint32_t>(kFusedTile);
+      const uint4* kq = keys + bsel * kWsChunk;
+      const float4* sq = sums + bsel * kWsChunk * sw;
+#pragma unroll 1
+      for (uint32_t e0 = pt; e0 < hh.count; e0 += 4 * PT)
+        ws_probe_group<4>(t, kq, sq, hh.count, e0, PT, id_base, &s_claims[hh.k], a.gstash, rec,
+                          c);
+      mbar_arrive(empty + bsel);
+    }
+  }
+  if (!ok) atomicOr(&t.ctrl->error, kErrBarrierTimeout);
+  __syncthreads();
+  const uint32_t taken = s_taken;
+  {
+    const unsigned long long o = block_sum(static_cast<unsigned long long>(c.ovf));
+    const unsigned long long kk = block_sum(static_cast<unsigned long long>(c.cells));
+    if (threadIdx.x == 0) {
+      if (o) atomicAdd(&t.ctrl->overflow_vertices, o);
+      if (kk) atomicAdd(&t.ctrl->frame_cells, kk);
+      if (nv) atomicAdd(&t.ctrl->vertices, nv);
+      if (TEMPORAL && a.blend)
+        for (uint32_t i = 0; i < taken; ++i) __stcg(t.bcount + s_tile[i], s_claims[i]);
+    }
+  }
+  if (!grid_barrier(t.ctrl, gridDim.x)) return;
+
+  // Phase B: temporal blend, tiles from the second counter (as k_fused).
+  const bool blended = TEMPORAL && a.blend;
+  if (blended) {
+    unsigned long long n_hovf = 0;
+    for (;;) {
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        const unsigned long long bb = atomicAdd(&t.ctrl->blend_next, 1ull);
+        s_cur = bb < ntiles ? static_cast<uint32_t>(bb) : ntiles;
+      }
+      __syncthreads();
+      const uint32_t tile = s_cur;
+      if (tile >= ntiles) break;
+      blend_range<2, false>(t, tile * static_cast<uint32_t>(kFusedTile), __ldcg(t.bcount + tile),
+                            threadIdx.x, blockDim.x, a.alpha, n_hovf);
+    }
+    const unsigned long long hs = block_sum(n_hovf);
+    if (threadIdx.x == 0 && hs) atomicAdd(&t.ctrl->hist_overflow, hs);
+    if (!grid_barrier(t.ctrl, gridDim.x)) return;
+  }
+
+  // Phase C: one lookup per vertex of this CTA's tiles (cell ids from the stash).
+  const bool ovec = a.ovec != 0;
+  for (uint32_t k = 0; k < taken; ++k) {
+    const size_t t0 = static_cast<size_t>(s_tile[k]) * kFusedTile;
+    const size_t end = min(a.n, t0 + kFusedTile);
+#pragma unroll 1
+    for (int sub = 0; sub < 4; sub += 2) {
+      const size_t j = t0 + fused_offset<2>(sub);
+      if (j < end) {
+        uint32_t id[2];
+        if (j + 2 <= end) {  // j is even and the stash 8-byte aligned
+          const uint2 w2 = __ldcs(reinterpret_cast<const uint2*>(a.gstash + j));
+          id[0] = w2.x;
+          id[1] = w2.y;
+        } else {
+          id[0] = __ldcs(a.gstash + j);
+          id[1] = kOverflowSlot;
+        }
+        Result res[2];
+        resolve_batch<2>(t, a.v, j, end, id, blended, res);
+        store_batch<2>(a.o, j, end, ovec, res);
+      }
+    }
+  }
+  if (!grid_barrier(t.ctrl, gridDim.x)) return;
+
+  // Phase D: empty the cells this CTA's tiles created.
+  for (uint32_t k = 0; k < taken; ++k)
+    clear_range(t, s_tile[k] * static_cast<uint32_t>(kFusedTile), s_claims[k], threadIdx.x,
+                blockDim.x, a.sweep != 0);
+  if (a.sweep)
+    sweep_slots(t, blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x,
+                static_cast<size_t>(gridDim.x) * blockDim.x);
+}
+
 // The batched persistent kernel: the same phases as k_fused over the tiles of
 // several views, each with its own table.  Tiles are numbered across views
 // (view v owns tiles [tile_base, tile_base + ntiles)) and handed out from one
@@ -1359,9 +1792,9 @@ static const void* fused_kernel(bool temporal, int batch, bool evict, bool neigh
 // Largest dynamic shared memory a k_fused CTA may request: the opt-in limit
 // per block minus the kernel's static shared memory (set once per kernel).
 static cudaError_t fused_dyn_smem_limit(const void* fn, size_t* limit) {
-  static const void* done[16] = {nullptr};
-  static size_t lims[16] = {0};
-  for (int i = 0; i < 16; ++i)
+  static const void* done[32] = {nullptr};
+  static size_t lims[32] = {0};
+  for (int i = 0; i < 32; ++i)
     if (done[i] == fn) {
       *limit = lims[i];
       return cudaSuccess;
@@ -1375,7 +1808,7 @@ static cudaError_t fused_dyn_smem_limit(const void* fn, size_t* limit) {
   const size_t lim = static_cast<size_t>(maxopt) - fa.sharedSizeBytes;
   e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(lim));
   if (e != cudaSuccess) return e;
-  for (int i = 0; i < 16; ++i)
+  for (int i = 0; i < 32; ++i)
     if (!done[i]) {
       done[i] = fn;
       lims[i] = lim;
@@ -1385,8 +1818,51 @@ static cudaError_t fused_dyn_smem_limit(const void* fn, size_t* limit) {
   return cudaSuccess;
 }
 
+template <bool TEMPORAL>
+static const void* ws_fn(int key_warps) {
+  if (key_warps == 4) return reinterpret_cast<const void*>(k_fused_ws<TEMPORAL, 4, 12, 2>);
+  if (key_warps == 12) return reinterpret_cast<const void*>(k_fused_ws<TEMPORAL, 12, 4, 2>);
+  return reinterpret_cast<const void*>(k_fused_ws<TEMPORAL, 8, 8, 2>);
+}
+
+static const void* ws_kernel(bool temporal, int key_warps) {
+  return temporal ? ws_fn<true>(key_warps) : ws_fn<false>(key_warps);
+}
+
+// The pipelined insert: two CTAs of 512 threads per SM when their queues fit
+// (one otherwise); the stash is the global one.
+static cudaError_t plan_ws(size_t n, bool temporal, int key_warps, bool fixed, FusedPlan* plan) {
+  const void* fn = ws_kernel(temporal, key_warps);
+  size_t maxdyn = 0;
+  cudaError_t e = fused_dyn_smem_limit(fn, &maxdyn);
+  if (e != cudaSuccess) return e;
+  const size_t smem = WsLayout::bytes(fixed);
+  if (smem > maxdyn) return cudaErrorInvalidConfiguration;
+  int nb = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, kFusedBlock, smem);
+  if (e != cudaSuccess) return e;
+  if (nb < 1) return cudaErrorInvalidConfiguration;
+  plan->grid = sm_count() * std::min(nb, 2);
+  plan->block = kFusedBlock;
+  plan->batch = 2;
+  plan->cap_tiles = kMaxTilesPerCta;
+  plan->smem = smem;
+  plan->global_stash = true;
+  plan->evict = false;
+  plan->neigh = false;
+  plan->key_warps = key_warps;
+  const size_t ntiles = (n + kFusedTile - 1) / kFusedTile;
+  if (static_cast<size_t>(plan->grid) * kMaxTilesPerCta < ntiles) return cudaErrorInvalidValue;
+  return cudaSuccess;
+}
+
 cudaError_t plan_fused(size_t n, bool temporal, int batch, FusedPlan* plan, bool evict,
-                       bool neigh) {
+                       bool neigh, InsertShape shape, bool fixed) {
+  plan->key_warps = 0;
+  if (shape.pipelined && !evict && !neigh) {
+    const int kw = shape.key_warps == 4 || shape.key_warps == 12 ? shape.key_warps : 8;
+    return plan_ws(n, temporal, kw, fixed, plan);
+  }
   const void* fn = fused_kernel(temporal, batch, evict, neigh);
   plan->evict = temporal && evict;
   plan->neigh = neigh;
@@ -1452,6 +1928,9 @@ cudaError_t launch_fused(const KeyConst& kc, const TableDev& t, const VertexPtrs
   a.sweep = sweep_pays(t, n) ? 1 : 0;
   a.nq = nq;
   void* args[] = {&a};
+  if (plan.key_warps > 0)
+    return cudaLaunchCooperativeKernel(ws_kernel(temporal, plan.key_warps), dim3(plan.grid),
+                                       dim3(plan.block), args, plan.smem, st);
   cudaError_t e = cudaLaunchCooperativeKernel(
       fused_kernel(temporal, plan.batch, plan.evict, plan.neigh), dim3(plan.grid), dim3(plan.block),
       args, plan.smem, st);
