@@ -34,6 +34,9 @@ What it computes, and from which passage
   fingerprint words carry a priority (the frame of last use) in their top
   bits, so that a cell without room replaces the least recently used entry
   of its probe window.
+* Searching similar normals by linear probing (Sec. 3.2.2): with the normal
+  only in the fingerprint, a lookup pools the cells of its voxel whose
+  quantized normal lies within a given number of steps of its own.
 * Fallbacks for cells with few vertices (Sec. 3.3.1 neighborhood search,
   Sec. 3.3.2 multi-level accumulation): the pooled average of the 3x3x3
   block of cells around a vertex's cell, and the average of the next coarser
@@ -740,6 +743,54 @@ def neighborhood(fr: FrameResult, threshold: int, cell_value=None, cell_weight=N
         s64 = np.where(ok[:, :, None], cv[nbc] * wn[:, :, None], 0.0).sum(axis=1)
         value64[idx] = s64 / tot[:, None]
     return value64, value_fx, count, status
+
+
+def similar_normals(fr: FrameResult, radius: int, cell_value=None, cell_weight=None):
+    """Searching similar normals by linear probing (Sec. 3.2.2).  With the
+    normal in the fingerprint only, all cells of one voxel share their home
+    slot, so a lookup can walk the probe window past mismatching fingerprints
+    and pool, besides its own cell, the cells of the same voxel whose normal
+    is similar.  Reading: the cells pooled for a vertex are those with the
+    same x~ and l' (and the same extra key word, if any) whose quantized
+    normal lies within `radius` quantization steps of the vertex's own on
+    every axis (max_a |q_a - q'_a| <= radius: an integer test, so every
+    implementation decides membership identically).  radius 0 is the plain
+    lookup; radius 255 pools the whole voxel whatever the normal.
+
+    Without `cell_value`: the pooled sums over the pooled counts, in FP64 and
+    in the fixed-point reading fl32(fl32(sum of fixed sums) * 2^-24) /
+    fl32(count).  With per-cell `cell_value` (C, 3) and `cell_weight` (C,) --
+    blended values and their counts N after a temporal blend -- sum(N c) /
+    sum(N) in FP64.  Returns (value64 (N, 3), value_fixed (N, 3) or None,
+    count (N,))."""
+    T = fr.tuples
+    C = T.shape[0]
+    w = fr.cell_count if cell_value is None else np.asarray(cell_weight, dtype=np.int64)
+    cv = None if cell_value is None else np.asarray(cell_value, dtype=np.float64)
+    vox = np.concatenate([T[:, :4], T[:, 7:]], axis=1)  # x~, l' and any extra word
+    _, vinv = np.unique(vox, axis=0, return_inverse=True)
+    vinv = vinv.reshape(-1)
+    order = np.argsort(vinv, kind="stable")
+    starts = np.r_[0, np.nonzero(np.diff(vinv[order]))[0] + 1, C]
+    pw = np.zeros(C, dtype=np.int64)
+    p64 = np.zeros((C, 3))
+    pfx = np.zeros((C, 3), dtype=np.int64)
+    for a, b in zip(starts[:-1], starts[1:]):
+        cells = order[a:b]
+        q = T[cells, 4:7]
+        near = np.abs(q[:, None, :] - q[None, :, :]).max(axis=2) <= radius  # (k, k)
+        pw[cells] = near.astype(np.int64) @ w[cells]
+        if cv is None:
+            p64[cells] = near.astype(np.float64) @ fr.cell_sum64[cells]
+            pfx[cells] = near.astype(np.int64) @ fr.cell_fixed[cells]
+        else:
+            p64[cells] = near.astype(np.float64) @ (cv[cells] * w[cells][:, None])
+    count = pw[fr.cell]
+    value64 = p64[fr.cell] / count[:, None]
+    value_fx = None
+    if cv is None:
+        value_fx = fixed_mean_f32(pfx, pw)[fr.cell]
+    return value64, value_fx, count
 
 
 # ----------------------------------------------------------------------------
