@@ -154,7 +154,22 @@ extern "C" {
  *                     keep each cell's quantized key (16 B per cell); no extra
  *                     key word (pps_vertices.extra) is accepted; pps_batch_create
  *                     and pps_filter_noalloc reject such tables.
- *  reserved           must be zero.
+ *  normal_search      searching similar normals by linear probing (Sec. 3.2.2):
+ *                     0 = off; r + 1 (r = 0 .. 255) = every lookup returns the
+ *                     pooled average of the cells of its voxel (same x~ and
+ *                     l') whose quantized normal lies within r steps of its
+ *                     own on every axis (max over axes |q - q'| <= r): the
+ *                     pooled sums over the pooled counts (fixed point: exact
+ *                     int64 sums), or after a blend the blended values
+ *                     weighted by their N; count = the pooled count, status
+ *                     OK or LOWCOUNT by it.  Needs normal_in_home_hash = 0
+ *                     (so a voxel's normals share a home slot and lie within
+ *                     its P-slot window, which the lookup walks past
+ *                     mismatching entries) and fallback NONE; no extra key
+ *                     word.  Frames run through the split kernels, which keep
+ *                     each cell's quantized key (16 B per cell) for the test;
+ *                     pps_batch_create and pps_filter_noalloc reject such
+ *                     tables.  r = 0 gives the plain lookup.
  */
 typedef struct pps_params {
   uint32_t log2_slots;
@@ -175,7 +190,7 @@ typedef struct pps_params {
   uint32_t fallback;
   uint32_t hist_evict;
   uint32_t hist_migrate;
-  uint32_t reserved[1];
+  uint32_t normal_search;
 } pps_params;
 
 /* Camera position p_cam of Algorithm 1 (world space). */

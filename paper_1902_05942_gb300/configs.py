@@ -63,6 +63,9 @@ class FilterConfig:
     fallback: str = "none"  # low-count vertices: "none", "coarse" (Sec. 3.3.2), "neighbors" (3.3.1)
     hist_evict: bool = False  # history evicts its least recently used entries (Sec. 3.4.3)
     hist_migrate: bool = False  # history follows changes of resolution (Sec. 3.4.2)
+    # searching similar normals by linear probing (Sec. 3.2.2): 0 off, r + 1 =
+    # lookups pool the voxel's cells whose quantized normal is within r steps
+    normal_search: int = 0
 
     def oracle_kwargs(self) -> dict:
         """Plain keyword arguments for the oracle's key parameters."""

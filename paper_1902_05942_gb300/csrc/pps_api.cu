@@ -125,8 +125,10 @@ int check_params(const pps_params* p) {
     return fail(PPS_EINVAL, "hist_migrate needs a history without eviction");
   if (p->fallback == PPS_FALLBACK_COARSE && !std::isfinite(2.0f * p->voxel_scale))
     return fail(PPS_EINVAL, "voxel_scale too large for a coarser level");
-  for (uint32_t r : p->reserved)
-    if (r) return fail(PPS_EINVAL, "reserved fields must be zero");
+  if (p->normal_search > 256) return fail(PPS_EINVAL, "normal_search must be 0 .. 256");
+  if (p->normal_search && (p->normal_in_home_hash || p->fallback != PPS_FALLBACK_NONE))
+    return fail(PPS_EINVAL,
+                "normal_search needs normal_in_home_hash = 0 and no low-count fallback");
   return PPS_OK;
 }
 
@@ -226,7 +228,8 @@ int ensure_dense(pps_table* t, size_t need, size_t keep, cudaStream_t st) {
   cudaError_t e = cudaMalloc(&acc, cap * acc_b);
   if (e == cudaSuccess) e = cudaMalloc(&info, cap * sizeof(uint4));
   if (e == cudaSuccess) e = cudaMalloc(&bc, nb * sizeof(uint32_t));
-  if (e == cudaSuccess && t->dev.hist_migrate) e = cudaMalloc(&kw, cap * sizeof(uint4));
+  if (e == cudaSuccess && (t->dev.hist_migrate || t->dev.normal_search))
+    e = cudaMalloc(&kw, cap * sizeof(uint4));
   if (e == cudaSuccess && t->dev.hist_migrate) e = cudaMalloc(&hold, cap * sizeof(float4));
   if (e == cudaSuccess) e = cudaMemsetAsync(acc, 0, cap * acc_b, st);
   void* old_acc = t->dev.fixed ? static_cast<void*>(t->dev.acc64) : static_cast<void*>(t->dev.acc);
@@ -374,6 +377,7 @@ int pps_create(pps_table** out, const pps_params* p) {
   const bool fixed = p->accum_mode == PPS_ACCUM_FIXED;
   t->dev.fixed = fixed;
   t->dev.hist_migrate = p->hist_migrate ? 1 : 0;  // before the dense arrays are made
+  t->dev.normal_search = p->normal_search;
   t->dev.hstride = p->hist_mode == PPS_HIST_FP16 ? 16u : 32u;
   t->dev.hfp_off = p->hist_mode == PPS_HIST_FP16 ? 8u : 16u;
   cudaError_t e = alloc(reinterpret_cast<void**>(&t->dev.slots), T * sizeof(unsigned long long));
@@ -451,8 +455,8 @@ int pps_insert(pps_table* t, const pps_vertices* v, size_t n, uint32_t* slot_out
   if (int rc = check_table(t)) return rc;
   if (int rc = check_vertices(v, n)) return rc;
   if (t->state != kOpen) return fail(PPS_ESTATE, "pps_insert needs pps_build first (and no pps_blend since)");
-  if (t->dev.hist_migrate && v->extra)
-    return fail(PPS_EINVAL, "a table with hist_migrate takes no extra key word");
+  if ((t->dev.hist_migrate || t->dev.normal_search) && v->extra)
+    return fail(PPS_EINVAL, "a table with hist_migrate or normal_search takes no extra key word");
   const cudaStream_t st = static_cast<cudaStream_t>(stream);
   const size_t tile = static_cast<size_t>(pps::tile_size());
   const size_t tiles = (n + tile - 1) / tile;
@@ -565,7 +569,7 @@ int pps_filter(pps_table* t, const pps_camera* cam, uint32_t frame, const pps_ve
   if (blend && (!std::isfinite(alpha) || alpha > 1.0f))
     return fail(PPS_EINVAL, "alpha must be finite and <= 1");
   const cudaStream_t st = static_cast<cudaStream_t>(stream);
-  if (v->dist || v->extra || t->dev.hist_migrate) {
+  if (v->dist || v->extra || t->dev.hist_migrate || t->dev.normal_search) {
     // key variants and history migration: the split kernels (the persistent
     // ones are built without them); the insert's cell ids spare the lookup
     // its keys and probes
@@ -761,9 +765,10 @@ int table_for_batch(pps_table* t, size_t n, ViewDesc* vd, int* batch, bool* temp
                     cudaStream_t st) {
   if (int rc = check_table(t)) return rc;
   if (t->state != kClean) return fail(PPS_ESTATE, "a table of a batch is in the middle of a frame");
-  if (t->p.fallback != PPS_FALLBACK_NONE || t->p.hist_evict || t->p.hist_migrate)
-    return fail(PPS_EINVAL,
-                "batched views take tables without a low-count fallback, eviction or migration");
+  if (t->p.fallback != PPS_FALLBACK_NONE || t->p.hist_evict || t->p.hist_migrate ||
+      t->p.normal_search)
+    return fail(PPS_EINVAL, "batched views take tables without a low-count fallback, eviction, "
+                            "migration or normal search");
   const size_t ftile = static_cast<size_t>(fused_tile_size());
   if (int rc = ensure_dense(t, (n + ftile - 1) / ftile * ftile, 0, st)) return rc;
   vd->kc = t->kc;

@@ -106,6 +106,7 @@ struct TableDev {
   int hist_evict;             // history fingerprints carry a priority (evicting table)
   int hist_migrate;           // history follows changes of resolution (Sec. 3.4.2)
   uint32_t hist_rank;         // evicting table: this frame's priority (blend epoch)
+  uint32_t normal_search;     // 0 off; r + 1: lookups pool the voxel's normals within r steps
 };
 
 constexpr uint32_t kNoSlot = 0xFFFFFFFFu;  // info.x of an id reserved but not used

@@ -405,6 +405,75 @@ __device__ __noinline__ Result neighbor_pool(const KeyConst& kc, const TableDev&
   return neighbor_pool_inl(kc, t, v, j, blended, own);
 }
 
+// Searching similar normals by linear probing (Sec. 3.2.2) for a vertex whose
+// cell is `id`: with the normal only in the fingerprint, every cell of the
+// voxel has the voxel's home slot and lies within P slots of it, so the walk
+// from the home slot to the first empty slot (at most P slots) passes all of
+// them, between the entries of other voxels.  Each entry's cell record (its
+// quantized key) says whether it is the same voxel (x~, l') with a quantized
+// normal within r steps on every axis; those cells are pooled: FP32 sums, or
+// exact int64 sums in fixed-point mode, or after a blend the blended values
+// weighted by their N.  Kept out of line: only tables with the search pay.
+__device__ __noinline__ Result similar_pool(const TableDev& t, uint32_t id, bool blended) {
+  const uint4 rec = __ldcg(t.kw + id);
+  const uint32_t home = __ldcg(&t.info[id].y) & t.mask;
+  const int r = static_cast<int>(t.normal_search) - 1;
+  const int qx = static_cast<int>((rec.w >> 8) & 0xFFu);
+  const int qy = static_cast<int>((rec.w >> 16) & 0xFFu);
+  const int qz = static_cast<int>(rec.w >> 24);
+  float sr = 0.f, sg = 0.f, sb = 0.f;
+  long long fr = 0, fg = 0, fb = 0;
+  unsigned long long n = 0;
+#pragma unroll 1
+  for (uint32_t p = 0; p < t.max_probes; ++p) {
+    const unsigned long long w = __ldcg(t.slots + ((home + p) & t.mask));
+    if (w == 0ull) break;
+    const uint32_t c = slot_id(w);
+    const uint4 o = __ldcg(t.kw + c);
+    if (o.x != rec.x || o.y != rec.y || o.z != rec.z || ((o.w ^ rec.w) & 0xFFu)) continue;
+    const int dx = abs(static_cast<int>((o.w >> 8) & 0xFFu) - qx);
+    const int dy = abs(static_cast<int>((o.w >> 16) & 0xFFu) - qy);
+    const int dz = abs(static_cast<int>(o.w >> 24) - qz);
+    if (max(dx, max(dy, dz)) > r) continue;
+    if (blended) {
+      const float4 v = __ldcg(value_ptr(t, c));
+      const uint32_t N = __float_as_uint(v.w);
+      const float fN = __uint2float_rn(N);
+      sr = __fadd_rn(sr, __fmul_rn(fN, v.x));
+      sg = __fadd_rn(sg, __fmul_rn(fN, v.y));
+      sb = __fadd_rn(sb, __fmul_rn(fN, v.z));
+      n += N;
+    } else if (!t.fixed) {
+      const float4 v = __ldcg(t.acc + c);
+      if (v.w >= kExactCountLimit) atomicOr(&t.ctrl->error, kErrCountSaturated);
+      sr = __fadd_rn(sr, v.x);
+      sg = __fadd_rn(sg, v.y);
+      sb = __fadd_rn(sb, v.z);
+      n += static_cast<unsigned long long>(v.w);
+    } else {
+      const unsigned long long* a = t.acc64 + 4 * static_cast<size_t>(c);
+      fr += static_cast<long long>(__ldcg(a + 0));
+      fg += static_cast<long long>(__ldcg(a + 1));
+      fb += static_cast<long long>(__ldcg(a + 2));
+      n += __ldcg(a + 3);
+    }
+  }
+  Result res;
+  const float fn = __ull2float_rn(n);
+  if (t.fixed && !blended) {
+    res.r = __fdiv_rn(__fmul_rn(__ll2float_rn(fr), 0x1p-24f), fn);
+    res.g = __fdiv_rn(__fmul_rn(__ll2float_rn(fg), 0x1p-24f), fn);
+    res.b = __fdiv_rn(__fmul_rn(__ll2float_rn(fb), 0x1p-24f), fn);
+  } else {
+    res.r = __fdiv_rn(sr, fn);
+    res.g = __fdiv_rn(sg, fn);
+    res.b = __fdiv_rn(sb, fn);
+  }
+  res.n = static_cast<uint32_t>(min(n, 0xFFFFFFFFull));
+  res.status = res.n < t.lowcount ? 1 : 0;
+  return res;
+}
+
 // Vertex j with cell `id`: if its cell is low-count, replace its outputs by
 // the neighborhood-search result.
 __device__ __forceinline__ void neighbors_of_vertex(const KeyConst& kc, const TableDev& t,
@@ -674,6 +743,11 @@ __global__ void __launch_bounds__(kBlock) k_query(KeyConst kc, TableDev t, Verte
     }
     Result res[4];
     resolve_batch<4>(t, v, j, n, id, blended != 0, res);
+    if (t.normal_search) {
+#pragma unroll 1
+      for (int q = 0; q < 4; ++q)
+        if (j + q < n && id[q] != kOverflowSlot) res[q] = similar_pool(t, id[q], blended != 0);
+    }
     store_batch<4>(o, j, n, ovec != 0, res);
     if (t.neighbors) {
 #pragma unroll
@@ -1668,7 +1742,7 @@ cudaError_t launch_insert(const KeyConst& kc, const TableDev& t, const VertexPtr
   if (n == 0) return cudaSuccess;
   const int grid = split_grid((n + 3) / 4);
   const int vec = vec_inputs(v) ? 1 : 0;
-  if (t.hist_migrate) {
+  if (t.hist_migrate || t.normal_search) {  // keep each new cell's quantized key
     if (batch == 2)
       k_insert<2, true><<<grid, kBlock, 0, st>>>(kc, t, v, n, id_out, vec, tile_base);
     else

@@ -146,9 +146,10 @@ extern "C" int pps_filter_noalloc(const pps_params* p, const pps_camera* cam, ui
   if (n > kNoAllocMaxVertices)
     return noalloc_fail(PPS_EINVAL, "pps_filter_noalloc: at most 524288 vertices per call");
   if (p->accum_mode != PPS_ACCUM_FP32 || p->hist_mode != PPS_HIST_NONE ||
-      p->fallback != PPS_FALLBACK_NONE || p->hist_evict != 0 || p->hist_migrate != 0)
-    return noalloc_fail(PPS_EINVAL,
-                        "pps_filter_noalloc: FP32 accumulation without history or fallback only");
+      p->fallback != PPS_FALLBACK_NONE || p->hist_evict != 0 || p->hist_migrate != 0 ||
+      p->normal_search != 0)
+    return noalloc_fail(PPS_EINVAL, "pps_filter_noalloc: FP32 accumulation without history, "
+                                    "fallback or normal search only");
   if (v->dist || v->extra)
     return noalloc_fail(PPS_EINVAL, "pps_filter_noalloc: no dist or extra arrays");
   if (n && (!v->px || !v->py || !v->pz || !v->nx || !v->ny || !v->nz || !v->r || !v->g ||

@@ -41,7 +41,7 @@ class pps_params(ctypes.Structure):
                 ("normal_in_home_hash", _u32), ("lod_min", _i32), ("lod_max", _i32),
                 ("accum_mode", _u32), ("hist_mode", _u32), ("lowcount_threshold", _u32),
                 ("log2_hist_slots", _u32), ("fallback", _u32), ("hist_evict", _u32),
-                ("hist_migrate", _u32), ("reserved", _u32 * 1)]
+                ("hist_migrate", _u32), ("normal_search", _u32)]
 
 
 class pps_camera(ctypes.Structure):
@@ -225,7 +225,7 @@ def make_params(cfg, hist_mode: Optional[int] = None, accum_fixed: Optional[bool
                       cfg.hash_seed_fp & 0xFFFFFFFF, int(cfg.normal_in_home_hash), cfg.lod_min,
                       cfg.lod_max, ACCUM_FIXED if fx else ACCUM_FP32, hm,
                       cfg.lowcount_threshold, lh, FALLBACKS[fb], int(bool(ev)), int(bool(mg)),
-                      (_u32 * 1)(0))
+                      int(getattr(cfg, "normal_search", 0)))
 
 
 def camera(pos: Sequence[float]) -> pps_camera:

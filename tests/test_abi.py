@@ -89,13 +89,23 @@ def test_create_rejects_bad_parameters_without_touching_the_gpu(field, value):
     assert pps.last_error()
 
 
-def test_reserved_fields_must_be_zero():
+@pytest.mark.parametrize("bad", [dict(normal_search=257), dict(normal_search=3, normal_in_home_hash=1),
+                                 dict(normal_search=1, normal_in_home_hash=0, fallback=2)])
+def test_normal_search_checks(bad):
     pps, L = _lib()
     p = _params(pps)
-    p.reserved[0] = 7
+    for k, v in bad.items():
+        setattr(p, k, v)
     h = ctypes.c_void_p()
     assert L.pps_create(ctypes.byref(h), ctypes.byref(p)) == pps.PPS_EINVAL
-    assert "reserved" in pps.last_error()
+    assert "normal_search" in pps.last_error()
+
+
+def test_set_tuning_needs_a_table():
+    pps, L = _lib()
+    t = pps.pps_tuning()
+    assert L.pps_set_tuning(None, ctypes.byref(t)) == pps.PPS_EINVAL
+    assert "table" in pps.last_error()
 
 
 def test_null_arguments_are_rejected():
