@@ -193,11 +193,76 @@ def make_frames(rank: int, device):
     return w, frames
 
 
-def algorithmic_bytes(n: int, cells: int) -> int:
+def algorithmic_bytes(n: int, cells: int, hist_bytes: int = 32) -> int:
     """Per frame: 36 B of vertex input + 12 B of output + 1 B status per vertex;
     per occupied cell 20 B (accumulator and fingerprint written back once) and
-    32 B for the FP32 history cell read and written by the blend."""
-    return 49 * n + 52 * cells
+    `hist_bytes` for its history value read and written by the blend (FP32
+    history: 16 B read + 16 B written; FP16: 8 + 8; none: 0)."""
+    return 49 * n + (20 + hist_bytes) * cells
+
+
+def subframe_error(frames, cfg, nsub=1_000_000, blended_frames=0, **table_kw):
+    """Precision of a table variant against the FP64 oracle, off the timed
+    path: the first `nsub` vertices of the leading frames filtered as frames of
+    their own (`blended_frames` > 0: that many frames with the temporal blend,
+    the oracle blending in FP64 without any storage rounding), then the last
+    frame's max relative error and RMSE per channel."""
+    import numpy as np
+    import torch
+    from oracle import pps_oracle as O
+    from paper_1902_05942_gb300 import pps, scene
+    tab = pps.Table(cfg, **table_kw)
+    fixed = tab.fixed
+    hist = O.History.empty()
+    nf = max(1, blended_frames)
+    for f in range(nf):
+        v, eye = frames[f % len(frames)]
+        sub = {k: v[k][:nsub].contiguous() for k in scene.STREAMS}
+        out = tab.filter(sub, eye, f, blend=blended_frames > 0, alpha=cfg.alpha)
+        torch.cuda.synchronize()
+        v_np = {k: t.cpu().numpy() for k, t in sub.items()}
+        fr = O.filter_frame(O.KeyParams(**cfg.oracle_kwargs()), eye, f, v_np)
+        if blended_frames:
+            hist, ref, cnt = O.blend(hist, fr, cfg.alpha)
+        else:
+            ref, cnt = fr.mean64, fr.count
+    o = {k: t.cpu().numpy() for k, t in out.items()}
+    tab.close()
+    ok = o["status"] != 2
+    got = np.column_stack([o[c] for c in "rgb"]).astype(np.float64)[ok]
+    rel = np.abs(got - ref[ok]) / np.abs(ref[ok])
+    res = {"vertices": int(ok.sum()), "frames": nf, "max_rel": float(rel.max()),
+           "rmse_rgb": [float(x) for x in np.sqrt(((got - ref[ok]) ** 2).mean(axis=0))],
+           "counts_equal": bool(np.array_equal(o["count"].astype(np.int64)[ok], cnt[ok]))}
+    if fixed and not blended_frames:
+        res["bit_exact_vs_oracle_fixed"] = bool(np.array_equal(
+            np.column_stack([o[c] for c in "rgb"])[ok], fr.mean_fixed[ok]))
+    return res
+
+
+def oracle_error(v_np, cfg, eye, frame, out_np, view=None, fixed=False):
+    """Error of one plain frame's results against the FP64 oracle over the
+    same vertices (the GPU's `out_np` from filtering exactly `v_np` as frame
+    `frame`): max relative error and RMSE per channel over the vertices that
+    kept a cell (status != OVERFLOW); with `fixed`, whether the results equal
+    the oracle's fixed-point averages bit for bit."""
+    import numpy as np
+    from oracle import pps_oracle as O
+    kw = cfg.oracle_kwargs()
+    if view is not None:
+        kw["pixel_angle"] = O.pixel_angle(view.fov_y_deg, view.height)
+    fr = O.filter_frame(O.KeyParams(**kw), eye, frame, v_np)
+    ok = out_np["status"] != 2
+    got = np.column_stack([out_np[c] for c in "rgb"]).astype(np.float64)[ok]
+    ref = fr.mean64[ok]
+    rel = np.abs(got - ref) / np.abs(ref)
+    res = {"vertices": int(ok.sum()), "max_rel": float(rel.max()),
+           "rmse_rgb": [float(x) for x in np.sqrt(((got - ref) ** 2).mean(axis=0))],
+           "counts_equal": bool(np.array_equal(out_np["count"].astype(np.int64)[ok], fr.count[ok]))}
+    if fixed:
+        res["bit_exact_vs_oracle_fixed"] = bool(np.array_equal(
+            np.column_stack([out_np[c] for c in "rgb"])[ok], fr.mean_fixed[ok]))
+    return res
 
 
 def run_ours(args):
@@ -273,8 +338,16 @@ def run_ours(args):
     if not args.no_fallbacks:
         precision["fixed_point_plain"] = history_leg(frames, cfg, calls, fsteps, args.warmup,
                                                      blend=0, hist_mode=0, accum_fixed=True)
+        precision["fixed_point_plain"]["error_vs_fp64_oracle"] = subframe_error(
+            frames, cfg, hist_mode=0, accum_fixed=True)
         precision["fp16_history"] = history_leg(frames, cfg, calls, fsteps, args.warmup,
                                                 hist_mode=2)
+        precision["fp16_history"]["error_vs_fp64_oracle"] = subframe_error(
+            frames, cfg, blended_frames=3, hist_mode=2)
+        precision["fp32_headline"] = {"error_vs_fp64_oracle": subframe_error(
+            frames, cfg, blended_frames=3)}
+        precision["error_sample"] = ("first 1,000,000 vertices of the leading HD frames "
+                                     "filtered as frames of their own, off the timed path")
     ms, job_n = reduce_ranks(ms, float(total_n), dev)
     value = job_n / (ms / 1e3)
     ms_step = ms / args.steps
@@ -579,21 +652,21 @@ def batched_leg(steps_timed=8, tune=True):
         tuned.append({"view": f"{w.streams[i].view.width}x{w.streams[i].view.height}",
                       "vertices": v["px"].numel(), "log2_slots": cfg.log2_slots,
                       "max_probes": cfg.max_probes})
-    outs = [pps.empty_output(v["px"].numel(), "cuda", count=False) for v, _ in views]
+    outs = [pps.empty_output(v["px"].numel(), "cuda", count=True) for v, _ in views]
     cams = [eye for _, eye in views]
 
-    def make(width):
+    def make(width, block):
         tabs = []
         for cfg in cfgs:
             t = pps.Table(cfg)
-            t.tune(width)
+            t.tune(width, block=block)
             tabs.append(t)
         b = pps.Batch([(tabs[i], views[i][0], outs[i]) for i in range(len(views))])
         b._tables = tabs
         return b
 
-    width, wt = autotune.tune_batch_width(make, cams) if tune else (2, {})
-    batch = make(width)
+    (width, block), wt = autotune.tune_batch_shape(make, cams) if tune else ((2, 512), {})
+    batch = make(width, block)
     total = sum(v["px"].numel() for v, _ in views)
     for i in range(3):
         batch.run(cams, i)
@@ -605,10 +678,20 @@ def batched_leg(steps_timed=8, tune=True):
     e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / steps_timed
+    cells = [t.stats()["frame_cells"] for t in batch._tables]
+    last = 3 + steps_timed - 1
+    # precision of the last batched frame against the FP64 oracle: the two
+    # smallest views in full (their vertices are the oracle's whole input)
+    errs = []
+    for i in range(2):
+        v, eye = views[i]
+        errs.append(oracle_error({k: v[k].cpu().numpy() for k in scene.STREAMS}, cfgs[i], eye,
+                                 last, {k: t.cpu().numpy() for k, t in outs[i].items()},
+                                 w.streams[i].view))
     # the same views, one call per view
     tabs = [pps.Table(c) for c in cfgs]
     for t in tabs:
-        t.tune(width)
+        t.tune(width, block=block)
     def seq(f):
         for i, (v, eye) in enumerate(views):
             tabs[i].filter(v, eye, f, out=outs[i])
@@ -623,12 +706,20 @@ def batched_leg(steps_timed=8, tune=True):
     batch.close()
     for t in tabs + batch._tables:
         t.close()
+    alg = sum(algorithmic_bytes(v["px"].numel(), c, hist_bytes=0) for (v, _), c in zip(views, cells))
+    peak, peak_kind = _peaks()
     return {"workload": "8 views (2x 720p/1080p/1440p/2160p), 2 bounces, one persistent launch "
                         "replayed from a CUDA graph",
             "vertices_per_frame": total, "ms_per_frame": ms,
             "vertices_per_s": total / (ms * 1e-3),
             "ms_per_frame_one_call_per_view": ms_seq,
-            "batch_width": width, "batch_width_trials_ms": wt, "views": tuned}
+            "batch_width": width, "block": block, "launch_shape_trials_ms": wt, "views": tuned,
+            "roofline": {"bound": "hbm", "achieved": alg / (ms * 1e-3) / 1e9, "peak": peak,
+                         "unit": "GB/s", "frac": alg / (ms * 1e-3) / 1e9 / peak,
+                         "peak_source": peak_kind, "kernel": "k_fused_multi",
+                         "algorithmic_bytes_per_launch": alg},
+            "error_vs_fp64_oracle": {"views": "the two 1280x720 views of the last timed frame, "
+                                              "every vertex", "per_view": errs}}
 
 
 def stress_leg(steps_timed=6):
@@ -650,6 +741,14 @@ def stress_leg(steps_timed=6):
         del v
     torch.cuda.synchronize()
     n = frames[0][0]["px"].numel()
+    # probe limit by the autotuner at the workload's table size: the fastest
+    # limit whose overflowing share stays within 0.1 % (the paper wants probe
+    # failures rare, Sec. 3.2)
+    from paper_1902_05942_gb300 import autotune
+    tuned, trials = autotune.tune_view(cfg, frames[0][0], frames[0][1],
+                                       log2_range=(cfg.log2_slots, cfg.log2_slots),
+                                       probes=(16, 32), max_overflow=1e-3)
+    cfg = tuned
     tab = pps.Table(cfg)
     net = pps.MLP(pps.mlp_params())
     out = pps.empty_output(max(fr[0]["px"].numel() for fr in frames), "cuda")
@@ -674,15 +773,28 @@ def stress_leg(steps_timed=6):
     st = tab.stats()
     tab.close()
     net.close()
+    k = steps_timed
+    err = subframe_error(frames, cfg, blended_frames=2)
     del frames, out
     torch.cuda.empty_cache()
-    k = steps_timed
-    return {"workload": "3840x2160 x2 paths x6 bounces, 80% of vertices in 5% of the box, "
-                        "T=2^26, P=16, FP16 history 2^28, alpha=0.2, learned fallback",
+    alg = algorithmic_bytes(int(nv / k), st["frame_cells"], hist_bytes=16)
+    peak, peak_kind = _peaks()
+    bw = alg / (t_f / k * 1e-3) / 1e9
+    return {"workload": f"3840x2160 x2 paths x6 bounces, 80% of vertices in 5% of the box, "
+                        f"T=2^26, P={cfg.max_probes} (tuned), FP16 history 2^28, alpha=0.2, "
+                        f"learned fallback",
             "vertices_per_frame": nv / k, "ms_filter": t_f / k, "ms_frame_with_mlp": t_all / k,
             "filter_vertices_per_s": nv / (t_f * 1e-3),
+            "max_probes": cfg.max_probes, "probe_trials": trials,
             "overflow_vertices_last_frame": st["overflow_vertices"],
-            "frame_cells_last_frame": st["frame_cells"]}
+            "overflow_share_last_frame": st["overflow_vertices"] / (nv / k),
+            "frame_cells_last_frame": st["frame_cells"],
+            "roofline": {"bound": "hbm", "achieved": bw, "peak": peak, "unit": "GB/s",
+                         "frac": bw / peak, "peak_source": peak_kind, "kernel": "k_fused",
+                         "algorithmic_bytes_per_launch": alg},
+            "error_vs_fp64_oracle": dict(err, sample="first 1,000,000 vertices of the two "
+                                                     "stress frames, two blended frames with "
+                                                     "the tuned table, off the timed path")}
 
 
 def _oracle_step(v_np, w, frame, eye, hist):
@@ -693,17 +805,85 @@ def _oracle_step(v_np, w, frame, eye, hist):
     return hist
 
 
+def _shard_cells(task):
+    """One worker of the all-core oracle (a spawned process): the oracle's keys
+    of one shard of vertices (global vertex ids, so the jitter is the same) and
+    the shard's cells -- sorted tuples, FP64 sums, fixed-point sums, counts --
+    with each vertex's cell within the shard."""
+    import numpy as np
+    from oracle import pps_oracle as O
+    v_np, kw, frame, eye, ids = task
+    keys = O.vertex_keys(O.KeyParams(**kw), eye, frame, v_np["px"], v_np["py"], v_np["pz"],
+                         v_np["nx"], v_np["ny"], v_np["nz"], ids=ids)
+    uniq, inv, cnt = O.group_cells(keys.tuples())
+    rgb = np.column_stack([v_np[c].astype(np.float32) for c in "rgb"])
+    s64 = np.column_stack([np.bincount(inv, weights=rgb[:, j].astype(np.float64),
+                                       minlength=uniq.shape[0]) for j in range(3)])
+    sfx = np.zeros((uniq.shape[0], 3), dtype=np.int64)
+    np.add.at(sfx, inv, O.to_fixed(rgb))
+    return uniq, s64, sfx, cnt, inv
+
+
+def _oracle_step_sharded(pool, nshards, v_np, w, frame, eye, hist):
+    """The oracle's filter + blend with the key construction and per-shard
+    group-by spread over worker processes, then the partial cells merged (an
+    ordered group-by of the shards' tuples, sums and counts added) and the
+    blend run on the merged cells."""
+    import numpy as np
+    from oracle import pps_oracle as O
+    cfg = w.filters[0]
+    n = v_np["px"].shape[0]
+    bounds = np.linspace(0, n, nshards + 1).astype(np.int64)
+    tasks = [({k: a[lo:hi] for k, a in v_np.items()}, cfg.oracle_kwargs(), frame, eye,
+              np.arange(lo, hi, dtype=np.uint32)) for lo, hi in zip(bounds[:-1], bounds[1:])]
+    parts = pool.map(_shard_cells, tasks)
+    allt = np.concatenate([p[0] for p in parts])
+    uniq, minv = np.unique(allt, axis=0, return_inverse=True)
+    minv = minv.reshape(-1)
+    C = uniq.shape[0]
+    s64 = np.zeros((C, 3))
+    sfx = np.zeros((C, 3), dtype=np.int64)
+    cnt = np.zeros(C, dtype=np.int64)
+    np.add.at(s64, minv, np.concatenate([p[1] for p in parts]))
+    np.add.at(sfx, minv, np.concatenate([p[2] for p in parts]))
+    np.add.at(cnt, minv, np.concatenate([p[3] for p in parts]))
+    off = np.cumsum([0] + [p[0].shape[0] for p in parts[:-1]])
+    cell = np.concatenate([minv[o + p[4]] for o, p in zip(off, parts)])
+    fr = O.FrameResult(None, cell, uniq, cnt[cell], s64[cell] / cnt[cell][:, None],
+                       O.fixed_mean_f32(sfx, cnt)[cell], cnt, s64, sfx, None, None)
+    hist, _, _ = O.blend(hist, fr, cfg.alpha)
+    return hist
+
+
 def cpu_baseline(frame, w, sample):
     """The CPU oracle as it stands, single-threaded numpy, on the first `sample`
-    vertices of one HD frame (a bounded sample: the full frame takes ~15 s)."""
+    vertices of one HD frame (a bounded sample: the full frame takes ~15 s);
+    beside it the same step spread over all host cores (the key construction
+    and group-by per shard in spawned worker processes, then the merge and the
+    blend in this process)."""
+    import multiprocessing as mp
     from oracle import pps_oracle as O
     v, eye = frame
     v_np = {k: t[:sample].cpu().numpy() for k, t in v.items()}
     t0 = time.perf_counter()
     _oracle_step(v_np, w, 0, eye, O.History.empty())
     dt = time.perf_counter() - t0
-    return {"value": sample / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"first {sample} vertices of HD frame 0, filter + blend, numpy FP64"}
+    res = {"value": sample / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": f"first {sample} vertices of HD frame 0, filter + blend, numpy FP64"}
+    try:
+        cores = len(os.sched_getaffinity(0))
+    except AttributeError:
+        cores = os.cpu_count() or 1
+    with mp.get_context("spawn").Pool(cores) as pool:
+        small = {k: a[:4096] for k, a in v_np.items()}
+        _oracle_step_sharded(pool, cores, small, w, 0, eye, O.History.empty())  # start-up
+        t0 = time.perf_counter()
+        _oracle_step_sharded(pool, cores, v_np, w, 0, eye, O.History.empty())
+        dta = time.perf_counter() - t0
+    res["all_cores"] = {"value": sample / dta, "unit": UNIT, "cores": cores, "kind": "oracle",
+                        "sample": res["sample"] + "; keys and per-shard group-by in one "
+                                  "spawned process per core, merge and blend in the parent"}
+    return res
 
 
 def run_reference(args):

@@ -265,7 +265,8 @@ typedef struct pps_stats_t {
  *             0 = library default (2).  Also used by the split kernels and the
  *             batched launch.
  *  insert     how pps_filter's persistent launch inserts: 0 = library default
- *             (pipelined), 1 = per thread (each thread builds its vertices'
+ *             (pipelined while the slot index fits in L2, T <= 2^23; per
+ *             thread for larger tables), 1 = per thread (each thread builds its vertices'
  *             keys, then probes and accumulates them), 2 = pipelined (key
  *             warps build keys, merge equal ones within the warp and queue one
  *             entry per distinct key in shared memory; probe warps run the
@@ -274,13 +275,17 @@ typedef struct pps_stats_t {
  *             insert per thread.
  *  key_warps  pipelined insert: key warps of the 16 warps of a CTA (the rest
  *             probe): 4, 8 or 12; 0 = library default (8).
+ *  block      batched launch (taken from the first view's table): threads
+ *             per CTA, 256 or 512; 0 = library default (512).  Each CTA
+ *             takes tiles of 2,048 vertices, 2048 / block per thread.
  *  reserved   must be zero.
  */
 typedef struct pps_tuning {
   uint32_t batch;
   uint32_t insert;
   uint32_t key_warps;
-  uint32_t reserved[5];
+  uint32_t block;
+  uint32_t reserved[4];
 } pps_tuning;
 
 typedef struct pps_table pps_table;

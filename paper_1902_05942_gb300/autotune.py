@@ -4,9 +4,11 @@ Off the timed path, on a sample frame of each view: for every candidate table
 size (2^lo .. 2^hi slots) and probe limit, filter the view a few times with the
 library's fused launch, time it with CUDA events and read the overflow count;
 keep the fastest candidate whose overflowing share of vertices stays below
-`max_overflow` (if none does, the one with the least overflow).  Then choose
-the batch width (vertices per thread per insert step) of a batched launch by
-timing the whole batch with each width.  The paper sizes the table in
+`max_overflow` (if none does, the one with the least overflow), candidates
+within 3 % of the fastest counting as ties that the smaller table and probe
+limit win.  Then choose the launch shape of a batched launch -- batch width
+(vertices per thread per insert step) and block shape (threads per CTA) -- by
+timing the whole batch with each.  The paper sizes the table in
 proportion to the image (Sec. 4); the candidate range brackets that choice.
 """
 from __future__ import annotations
@@ -31,15 +33,22 @@ def _time(fn, reps: int) -> float:
     return e0.elapsed_time(e1) / reps
 
 
-def choose(trials: List[dict], max_overflow: float) -> dict:
-    """The fastest trial whose overflowing share of vertices is at most
-    `max_overflow`; if none qualifies, the one with the least overflow (ties:
-    the fastest)."""
+def choose(trials: List[dict], max_overflow: float, tie: float = 0.03) -> dict:
+    """Among the trials whose overflowing share of vertices is at most
+    `max_overflow`, those within `tie` (relative) of the fastest count as equally
+    fast -- timing noise of a few per cent must not decide -- and of those the
+    one with the smallest table, then the smallest probe limit, then the
+    smallest launch-shape key wins, so that identical views get identical
+    choices.  If no trial qualifies, the one with the least overflow (ties: the
+    fastest)."""
     if not trials:
         raise ValueError("no trials")
     ok = [t for t in trials if t["overflow"] <= max_overflow]
     if ok:
-        return min(ok, key=lambda t: t["ms"])
+        best = min(t["ms"] for t in ok)
+        near = [t for t in ok if t["ms"] <= best * (1.0 + tie)]
+        return min(near, key=lambda t: (t.get("log2_slots", 0), t.get("max_probes", 0),
+                                        t.get("shape", 0), t["ms"]))
     return min(trials, key=lambda t: (t["overflow"], t["ms"]))
 
 
@@ -61,11 +70,18 @@ def tune_view(cfg, v: Dict[str, torch.Tensor], eye, log2_range=(21, 24),
     return dataclasses.replace(cfg, log2_slots=best["log2_slots"], max_probes=best["max_probes"]), trials
 
 
-def tune_batch_width(make_batch, cams, reps: int = 3, widths: Sequence[int] = (2, 4)) -> Tuple[int, Dict[int, float]]:
-    """Fastest batch width for a batched launch; `make_batch(width)` builds it."""
+def tune_batch_shape(make_batch, cams, reps: int = 3,
+                     shapes: Sequence[Tuple[int, int]] = ((2, 512), (4, 512), (2, 256), (4, 256))
+                     ) -> Tuple[Tuple[int, int], Dict[str, float]]:
+    """Launch shape of a batched launch: batch width (vertices per thread per
+    insert step) and block shape (threads per CTA), timed on the whole batch;
+    `make_batch(width, block)` builds it.  Shapes within 3 % of the fastest
+    count as equally fast and the first of them in `shapes` wins."""
     times = {}
-    for w in widths:
-        b = make_batch(w)
-        times[w] = _time(lambda: b.run(cams, 0), reps)
+    for w, blk in shapes:
+        b = make_batch(w, blk)
+        times[(w, blk)] = _time(lambda: b.run(cams, 0), reps)
         b.close()
-    return min(times, key=times.get), times
+    trials = [{"ms": times[s], "overflow": 0.0, "shape": i} for i, s in enumerate(shapes)]
+    best = choose(trials, 1.0)
+    return shapes[best["shape"]], {f"{w}x{blk}": ms for (w, blk), ms in times.items()}

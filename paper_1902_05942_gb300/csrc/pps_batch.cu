@@ -57,7 +57,7 @@ int pps_batch_create(pps_batch** out, const pps_view* views, uint32_t nviews, in
   if (!b) return bfail(PPS_ENOMEM, "host allocation failed");
   cudaGetDevice(&b->device);
   b->alpha = alpha;
-  int batch = 2;
+  int batch = 2, block = 512;
   const size_t ftile = static_cast<size_t>(pps::fused_tile_size());
   for (uint32_t i = 0; i < nviews; ++i) {
     const pps_view& v = views[i];
@@ -72,12 +72,15 @@ int pps_batch_create(pps_batch** out, const pps_view* views, uint32_t nviews, in
     }
     pps::ViewDesc vd{};
     bool tmp = false;
-    int bw = 2;
-    if (int rc = pps::table_for_batch(v.table, v.n, &vd, &bw, &tmp, nullptr)) {
+    int bw = 2, blk = 512;
+    if (int rc = pps::table_for_batch(v.table, v.n, &vd, &bw, &blk, &tmp, nullptr)) {
       delete b;
       return rc;
     }
-    if (i == 0) batch = bw;
+    if (i == 0) {
+      batch = bw;
+      block = blk;
+    }
     vd.v = pps::VertexPtrs{v.v.px, v.v.py, v.v.pz, v.v.nx, v.v.ny, v.v.nz, v.v.r, v.v.g, v.v.b,
                            v.v.id, v.v.id_base, v.v.stream_id, v.v.dist, v.v.extra};
     vd.o = pps::OutPtrs{v.out.r, v.out.g, v.out.b, v.out.count, v.out.status};
@@ -97,7 +100,7 @@ int pps_batch_create(pps_batch** out, const pps_view* views, uint32_t nviews, in
     delete b;
     return bfail(PPS_EINVAL, "alpha must be finite and <= 1");
   }
-  cudaError_t e = pps::plan_multi(b->total_tiles, b->temporal, batch, &b->plan);
+  cudaError_t e = pps::plan_multi(b->total_tiles, b->temporal, batch, block, &b->plan);
   const size_t bytes = nviews * sizeof(pps::ViewDesc);
   for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
     e = cudaMalloc(&b->dviews[k], bytes);

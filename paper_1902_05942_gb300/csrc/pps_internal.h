@@ -57,7 +57,7 @@ struct MultiPlan {
 // views in device memory (`views`, nviews entries); `ctrl` carries the grid
 // barrier and the tile counter; `gstash` (total_tiles tiles) is used when the
 // stash does not fit on chip.
-cudaError_t plan_multi(size_t total_tiles, bool temporal, int batch, MultiPlan* plan);
+cudaError_t plan_multi(size_t total_tiles, bool temporal, int batch, int block, MultiPlan* plan);
 cudaError_t launch_multi(const ViewDesc* views, uint32_t nviews, uint32_t total_tiles, Ctrl* ctrl,
                          bool temporal, float alpha, const MultiPlan& plan, uint32_t* gstash,
                          cudaStream_t st);
@@ -109,7 +109,7 @@ cudaError_t launch_selftest_mbar(unsigned long long limit_ns, unsigned int* err,
 struct pps_table;
 
 namespace pps {
-int table_for_batch(pps_table* t, size_t n, ViewDesc* vd, int* batch, bool* temporal,
+int table_for_batch(pps_table* t, size_t n, ViewDesc* vd, int* batch, int* block, bool* temporal,
                     cudaStream_t st);
 
 }  // namespace pps

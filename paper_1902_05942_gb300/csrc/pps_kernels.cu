@@ -942,9 +942,9 @@ __global__ void __launch_bounds__(kBlock) k_clear_fused(TableDev t, uint32_t nti
 // sub-batch `sub` (0, W, ..): sub-batch k covers the k-th run of
 // kFusedBlock * W vertices, W consecutive ones per thread, so that each
 // warp's loads and stores of a stream are one contiguous run.
-template <int W>
+template <int W, int BLOCK = kFusedBlock>
 __device__ __forceinline__ uint32_t fused_offset(int sub) {
-  return static_cast<uint32_t>(sub / W) * (kFusedBlock * W) + threadIdx.x * W;
+  return static_cast<uint32_t>(sub / W) * (BLOCK * W) + threadIdx.x * W;
 }
 
 // Next tile of the frame's tile counter (ntiles once all are taken).
@@ -1572,8 +1572,9 @@ __device__ __forceinline__ void copy_view(ViewDesc* dst, const ViewDesc* src) {
     reinterpret_cast<uint32_t*>(dst)[i] = reinterpret_cast<const uint32_t*>(src)[i];
 }
 
-template <bool TEMPORAL, int W>
-__global__ void __launch_bounds__(kFusedBlock, W == 4 ? 1 : 2) k_fused_multi(MultiArgs a) {
+template <bool TEMPORAL, int W, int BLOCK>
+__global__ void __launch_bounds__(BLOCK, (W == 4 ? 1 : 2) * (kFusedBlock / BLOCK)) k_fused_multi(MultiArgs a) {
+  constexpr int kPer = kFusedTile / BLOCK;  // vertices per thread per tile
   extern __shared__ __align__(16) uint32_t s_stash[];
   __shared__ uint32_t s_tile[kMaxTilesPerCta];
   __shared__ uint32_t s_claims[kMaxTilesPerCta];
@@ -1612,8 +1613,8 @@ __global__ void __launch_bounds__(kFusedBlock, W == 4 ? 1 : 2) k_fused_multi(Mul
                                : s_stash + static_cast<size_t>(k) * kFusedTile;
     Counters c;
 #pragma unroll 1
-    for (int sub = 0; sub < 4; sub += W) {
-      const size_t j = t0 + fused_offset<W>(sub);
+    for (int sub = 0; sub < kPer; sub += W) {
+      const size_t j = t0 + fused_offset<W, BLOCK>(sub);
       if (j < end) {
         const Batch<W> b = insert_batch<W>(s_vd.kc, s_vd.t, s_vd.v, j, end, s_vd.vec != 0,
                                            static_cast<uint32_t>(t0), &s_claims[k], c);
@@ -1669,8 +1670,8 @@ __global__ void __launch_bounds__(kFusedBlock, W == 4 ? 1 : 2) k_fused_multi(Mul
                                      : s_stash + static_cast<size_t>(k) * kFusedTile;
     const bool blended = TEMPORAL && s_vd.blended;
 #pragma unroll 1
-    for (int sub = 0; sub < 4; sub += W) {
-      const size_t j = t0 + fused_offset<W>(sub);
+    for (int sub = 0; sub < kPer; sub += W) {
+      const size_t j = t0 + fused_offset<W, BLOCK>(sub);
       if (j < end) {
         uint32_t id[W];
 #pragma unroll
@@ -2023,37 +2024,39 @@ bool vec_outputs_host(const OutPtrs& o) { return vec_outputs(o); }
 bool sweep_pays_host(const TableDev& t, size_t vertices) { return sweep_pays(t, vertices); }
 
 template <bool TEMPORAL, int W>
-static const void* multi_fn() {
-  return reinterpret_cast<const void*>(k_fused_multi<TEMPORAL, W>);
+static const void* multi_fn(int block) {
+  return block == 256 ? reinterpret_cast<const void*>(k_fused_multi<TEMPORAL, W, 256>)
+                      : reinterpret_cast<const void*>(k_fused_multi<TEMPORAL, W, 512>);
 }
 
-static const void* multi_kernel(bool temporal, int batch) {
-  if (temporal) return batch == 2 ? multi_fn<true, 2>() : multi_fn<true, 4>();
-  return batch == 2 ? multi_fn<false, 2>() : multi_fn<false, 4>();
+static const void* multi_kernel(bool temporal, int batch, int block) {
+  if (temporal) return batch == 2 ? multi_fn<true, 2>(block) : multi_fn<true, 4>(block);
+  return batch == 2 ? multi_fn<false, 2>(block) : multi_fn<false, 4>(block);
 }
 
-cudaError_t plan_multi(size_t total_tiles, bool temporal, int batch, MultiPlan* plan) {
-  const void* fn = multi_kernel(temporal, batch);
+cudaError_t plan_multi(size_t total_tiles, bool temporal, int batch, int block, MultiPlan* plan) {
+  block = block == 256 ? 256 : kFusedBlock;
+  const void* fn = multi_kernel(temporal, batch, block);
   const int sms = sm_count();
   size_t maxdyn = 0;
   cudaError_t e = fused_dyn_smem_limit(fn, &maxdyn);
   if (e != cudaSuccess) return e;
   int b0 = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b0, fn, kFusedBlock, 0);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b0, fn, block, 0);
   if (e != cudaSuccess) return e;
   if (b0 < 1) return cudaErrorInvalidConfiguration;
   int dev = 0, smem_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
   const size_t tile_bytes = kFusedTile * sizeof(uint32_t);
-  plan->block = kFusedBlock;
+  plan->block = block;
   plan->batch = batch;
   for (int b = b0; b >= 1; --b) {
     const size_t per = std::min(maxdyn, static_cast<size_t>(smem_sm) / b - 12 * 1024);
     const size_t cap = std::min<size_t>(per / tile_bytes, kMaxTilesPerCta);
     if (cap == 0 || cap * static_cast<size_t>(sms) * b < total_tiles) continue;
     int nb = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, kFusedBlock, cap * tile_bytes);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, block, cap * tile_bytes);
     if (e != cudaSuccess) return e;
     if (nb >= b) {
       plan->grid = sms * b;
@@ -2083,7 +2086,7 @@ cudaError_t launch_multi(const ViewDesc* views, uint32_t nviews, uint32_t total_
   a.cap_tiles = plan.cap_tiles;
   a.alpha = alpha;
   void* args[] = {&a};
-  return cudaLaunchCooperativeKernel(multi_kernel(temporal, plan.batch), dim3(plan.grid),
+  return cudaLaunchCooperativeKernel(multi_kernel(temporal, plan.batch, plan.block), dim3(plan.grid),
                                      dim3(plan.block), args, plan.smem, st);
 }
 
