@@ -1212,15 +1212,17 @@ __device__ __forceinline__ bool bar_and(int id, int nthreads, bool pred) {
   return r != 0;
 }
 
-// Shared-memory layout of k_fused_ws (dynamic part), for `fixed` accumulation.
+// Shared-memory layout of k_fused_ws (dynamic part): 2 headers, 4 mbarriers
+// (full[2], empty[2]), two queue buffers of kWsChunk entries and their FP32
+// group sums {r, g, b, count} (fixed-point tables leave the sums to the probe
+// warps, which add the members' contributions exactly in int64).
 struct WsLayout {
-  static constexpr size_t kHeaders = 64;  // 2 headers + 4 mbarriers (full[2], empty[2])
+  static constexpr size_t kHeaders = 64;
   __host__ __device__ static constexpr size_t keys_off() { return kHeaders; }
   __host__ __device__ static constexpr size_t sums_off() {
     return kHeaders + 2 * kWsChunk * sizeof(uint4);
   }
-  // float4 words per entry: {r, g, b, count} FP32, or int64 r, g, b, count
-  __host__ __device__ static constexpr size_t sum_words(bool fixed) { return fixed ? 2 : 1; }
+  __host__ __device__ static constexpr size_t sum_words(bool) { return 1; }
   __host__ __device__ static constexpr size_t bytes(bool fixed) {
     return sums_off() + 2 * kWsChunk * sum_words(fixed) * sizeof(float4);
   }
@@ -1245,28 +1247,15 @@ __device__ __forceinline__ void ws_enqueue(const TableDev& t, uint4* keys, float
   e = __shfl_sync(vm, e, leader);
   if (lead) {
     keys[e] = make_uint4(k.h1, k.fp, grp, static_cast<uint32_t>(j - lane));
-    if (!t.fixed) {
+    if (!t.fixed)
       sums[e] = make_float4(r, g, b, __uint_as_float(static_cast<uint32_t>(__popc(grp))));
-    } else {
-      long long* s = reinterpret_cast<long long*>(sums + 2 * e);
-      s[0] = to_fixed(r);
-      s[1] = to_fixed(g);
-      s[2] = to_fixed(b);
-      s[3] = __popc(grp);
-    }
   }
+  if (t.fixed) return;  // the probe warps sum the members exactly
   __syncwarp(vm);
   if (!lead) {
-    if (!t.fixed) {
-      atomicAdd(&sums[e].x, r);
-      atomicAdd(&sums[e].y, g);
-      atomicAdd(&sums[e].z, b);
-    } else {
-      unsigned long long* s = reinterpret_cast<unsigned long long*>(sums + 2 * e);
-      atomicAdd(s + 0, static_cast<unsigned long long>(to_fixed(r)));
-      atomicAdd(s + 1, static_cast<unsigned long long>(to_fixed(g)));
-      atomicAdd(s + 2, static_cast<unsigned long long>(to_fixed(b)));
-    }
+    atomicAdd(&sums[e].x, r);
+    atomicAdd(&sums[e].y, g);
+    atomicAdd(&sums[e].z, b);
   }
 }
 
@@ -1294,9 +1283,10 @@ __device__ __forceinline__ void ws_key_chunk(const FusedArgs& a, uint4* keys, fl
       nx[q] = ok ? __ldcs(v.nx + j) : 0.f;
       ny[q] = ok ? __ldcs(v.ny + j) : 0.f;
       nz[q] = ok ? __ldcs(v.nz + j) : 1.f;
-      r[q] = ok ? __ldcs(v.r + j) : 0.f;
-      g[q] = ok ? __ldcs(v.g + j) : 0.f;
-      b[q] = ok ? __ldcs(v.b + j) : 0.f;
+      const bool rgb = ok && !t.fixed;  // fixed point: summed by the probe warps
+      r[q] = rgb ? __ldcs(v.r + j) : 0.f;
+      g[q] = rgb ? __ldcs(v.g + j) : 0.f;
+      b[q] = rgb ? __ldcs(v.b + j) : 0.f;
     }
     Key k[KV];
 #pragma unroll
@@ -1318,7 +1308,8 @@ __device__ __forceinline__ void ws_key_chunk(const FusedArgs& a, uint4* keys, fl
 // One probe thread's entries e0, e0 + stride, ... (at most 4) of a chunk:
 // the table operations of all of them together.
 template <int PB>
-__device__ __forceinline__ void ws_probe_group(const TableDev& t, const uint4* keys,
+__device__ __forceinline__ void ws_probe_group(const TableDev& t, const VertexPtrs& v,
+                                               const uint4* keys,
                                                const float4* sums, uint32_t q, uint32_t e0,
                                                uint32_t stride, uint32_t id_base,
                                                uint32_t* claims, uint32_t* gstash, bool rec,
@@ -1383,8 +1374,15 @@ __device__ __forceinline__ void ws_probe_group(const TableDev& t, const uint4* k
         const float4 s = sums[e];
         red_add_v4_keep(t.acc + id[i], s.x, s.y, s.z, static_cast<float>(__float_as_uint(s.w)));
       } else {
-        const long long* s = reinterpret_cast<const long long*>(sums + 2 * e);
-        accumulate(t, id[i], 0.f, 0.f, 0.f, s[0], s[1], s[2], static_cast<uint32_t>(s[3]));
+        // exact int64 sums of the members' fixed-point contributions
+        long long fr = 0, fg = 0, fb = 0;
+        for (uint32_t m = mask[i]; m; m &= m - 1u) {
+          const uint32_t j = vb[i] + __ffs(m) - 1;
+          fr += to_fixed(__ldg(v.r + j));
+          fg += to_fixed(__ldg(v.g + j));
+          fb += to_fixed(__ldg(v.b + j));
+        }
+        accumulate(t, id[i], 0.f, 0.f, 0.f, fr, fg, fb, __popc(mask[i]));
       }
     } else {
       cnt.ovf += __popc(mask[i]);
@@ -1476,7 +1474,7 @@ __global__ void __launch_bounds__((KEYW + PRW) * 32, 2) k_fused_ws(FusedArgs a) 
       const float4* sq = sums + bsel * kWsChunk * sw;
 #pragma unroll 1
       for (uint32_t e0 = pt; e0 < hh.count; e0 += 4 * PT)
-        ws_probe_group<4>(t, kq, sq, hh.count, e0, PT, id_base, &s_claims[hh.k], a.gstash, rec,
+        ws_probe_group<4>(t, a.v, kq, sq, hh.count, e0, PT, id_base, &s_claims[hh.k], a.gstash, rec,
                           c);
       mbar_arrive(empty + bsel);
     }
