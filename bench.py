@@ -55,7 +55,7 @@ def _peaks():
         return 6800.0, "fallback"
 
 
-# the sources that define k_fused; its DRAM counters stay valid while they do
+# the sources that define the headline kernel; its DRAM counters stay valid while they do
 KERNEL_SOURCES = ("pps_device.cuh", "pps_internal.h", "pps_kernels.cu")
 
 
@@ -85,7 +85,7 @@ def _strip_comments(src: str) -> str:
 
 def _source_hash(texts=None) -> str:
     """Hash of the code (comments and blank space at line ends left out) of
-    the sources that define k_fused."""
+    the sources that define the persistent kernels."""
     h = hashlib.sha256()
     for f in KERNEL_SOURCES:
         if texts is None:
@@ -100,7 +100,7 @@ def _source_hash(texts=None) -> str:
 
 
 def _traffic_per_launch():
-    """DRAM bytes of one k_fused launch from the committed ncu summary, or None
+    """DRAM bytes of one headline launch from the committed ncu summary, or None
     when the kernel sources changed since those counters were taken."""
     try:
         with open(TRAFFIC_FILE) as fh:
@@ -351,7 +351,8 @@ def run_ours(args):
     ms, job_n = reduce_ranks(ms, float(total_n), dev)
     value = job_n / (ms / 1e3)
     ms_step = ms / args.steps
-    # roofline of the dominant (only) kernel: k_fused, one launch per step
+    # roofline of the dominant (only) kernel: k_fused_ws (the pipelined
+    # insert, the default at this table size), one launch per step
     mean_n = total_n / args.steps
     mean_c = sum(cells) / len(cells)
     alg = algorithmic_bytes(int(mean_n), int(mean_c))
@@ -412,7 +413,7 @@ def run_ours(args):
                        "parallelism": f"replicas x{ws} (independent frame streams)"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
-                         "peak_source": peak_kind, "kernel": "k_fused",
+                         "peak_source": peak_kind, "kernel": "k_fused_ws",
                          "algorithmic_bytes_per_launch": alg},
             "gpu_launches": args.steps,
             "clocks": clk.summary(),
@@ -451,7 +452,7 @@ def run_ours(args):
 
 def plain_leg(frames, cfg, calls, steps, warmup):
     """The same resident HD frames through the plain filter (no history, no
-    blend): one k_fused launch per frame, timed with CUDA events like the
+    blend): one persistent launch per frame, timed with CUDA events like the
     headline."""
     import ctypes
     import torch
