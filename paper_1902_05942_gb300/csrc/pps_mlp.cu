@@ -9,11 +9,15 @@
 // shared-memory tiles in the canonical no-swizzle layout into tensor memory,
 // tcgen05.ld back to registers for the bias / ReLU / rounding epilogues.
 // Inference: a CTA of 128 threads evaluates 128 vertices per tile.
-// Training: a CTA of 128 threads draws 128 samples and takes them through the
-// forward pass, the delta chain and the weight and bias gradients dZ^T X and
-// dZ^T 1 (products over the samples, reading the row-per-sample tiles as
-// MN-major operands), added to an FP32 gradient with vector reductions; Adam
-// updates FP32 master weights and refreshes the BF16 copies.
+// Training: one cooperative launch per call takes all its Adam steps.  A CTA
+// of 256 threads draws 128 samples and takes them through the forward pass,
+// the delta chain and the weight and bias gradients dZ^T X and dZ^T 1
+// (products over the samples, reading the row-per-sample tiles as MN-major
+// operands); two warps share each 32-lane quarter of tensor memory and split
+// every epilogue by columns.  The gradients are added to an FP32 accumulator
+// with vector reductions; after a grid barrier every thread applies Adam to its
+// share of the FP32 master weights and refreshes their BF16 copies, and a
+// second barrier starts the next step.
 //
 // Parameter vector (FP32, this order): W1 [64][80], b1 [64], W2 [64][64], b2,
 // W3 [64][64], b3, W4 [3][64], b4 [3]  (W as [out][in]).
@@ -60,6 +64,13 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) {
 __device__ __forceinline__ uint32_t pack2(float x, float y) {
   const __nv_bfloat162 h = __floats2bfloat162_rn(x, y);  // x in the low half
   return *reinterpret_cast<const uint32_t*>(&h);
+}
+// ReLU and BF16 rounding of two values in one conversion (x in the low half):
+// rounding is monotonic and keeps 0, so max(round(v), 0) = round(max(v, 0)).
+__device__ __forceinline__ uint32_t pack2_relu(float x, float y) {
+  uint32_t d;
+  asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(y), "f"(x));
+  return d;
 }
 __device__ __forceinline__ float lo_f(uint32_t w) { return __uint_as_float(w << 16); }
 __device__ __forceinline__ float hi_f(uint32_t w) { return __uint_as_float(w & 0xFFFF0000u); }
@@ -243,9 +254,11 @@ __device__ __forceinline__ void st16(unsigned char* base, uint32_t off, uint4 v)
 // kb < 9 holds (sin, cos)(pi 2^k p_a) for axis a = kb / 3 and k = 4 (kb % 3)
 // .. + 3 -- one sincospif, then three double-angle steps (error at most 8x
 // the FP32 rounding, far below BF16's); block 9 holds n_x, n_y, n_z, 0...
-__device__ __forceinline__ void encode_row(unsigned char* x, int r, const VertexIn& vi, bool valid) {
+// encode_blocks writes blocks KB0 .. KB1 - 1 and, with NORMAL, block 9.
+template <int KB0, int KB1, bool NORMAL>
+__device__ __forceinline__ void encode_blocks(unsigned char* x, int r, const VertexIn& vi, bool valid) {
 #pragma unroll
-  for (int kb = 0; kb < 9; ++kb) {
+  for (int kb = KB0; kb < KB1; ++kb) {
     float sn, cs;
     sincospif(vi.pn[kb / 3] * static_cast<float>(1 << (4 * (kb % 3))), &sn, &cs);
     uint32_t w[4];
@@ -258,9 +271,14 @@ __device__ __forceinline__ void encode_row(unsigned char* x, int r, const Vertex
     }
     st16(x, cm(r, 8 * kb, 80), make_uint4(w[0], w[1], w[2], w[3]));
   }
-  const uint4 nv = valid ? make_uint4(pack2(vi.nr[0], vi.nr[1]), pack2(vi.nr[2], 0.f), 0u, 0u)
-                         : make_uint4(0u, 0u, 0u, 0u);
-  st16(x, cm(r, 72, 80), nv);
+  if (NORMAL) {
+    const uint4 nv = valid ? make_uint4(pack2(vi.nr[0], vi.nr[1]), pack2(vi.nr[2], 0.f), 0u, 0u)
+                           : make_uint4(0u, 0u, 0u, 0u);
+    st16(x, cm(r, 72, 80), nv);
+  }
+}
+__device__ __forceinline__ void encode_row(unsigned char* x, int r, const VertexIn& vi, bool valid) {
+  encode_blocks<0, 9, true>(x, r, vi, valid);
 }
 
 // bias + ReLU + BF16 of 64 accumulator columns of row r, into the A tile h
@@ -272,8 +290,7 @@ __device__ __forceinline__ void hidden_row(unsigned char* h, int r, const uint32
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int c = 8 * kb + 2 * q;
-      w[q] = pack2(fmaxf(__uint_as_float(acc[c]) + bias[c], 0.f),
-                   fmaxf(__uint_as_float(acc[c + 1]) + bias[c + 1], 0.f));
+      w[q] = pack2_relu(__uint_as_float(acc[c]) + bias[c], __uint_as_float(acc[c + 1]) + bias[c + 1]);
     }
     st16(h, cm(r, 8 * kb, 64), make_uint4(w[0], w[1], w[2], w[3]));
   }
@@ -338,11 +355,14 @@ __global__ void __launch_bounds__(128) k_mlp_infer_tc(Dev d, VertexPtrs v, const
   };
   int64_t j = row_of(blockIdx.x);
   VertexIn vi = load_vertex(d, v, j);
+  int64_t jn = row_of(blockIdx.x + gridDim.x);
   for (uint32_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
     tc::encode_row(s.act, tid, vi, j >= 0);
-    // the next tile's vertex, loaded while this tile goes through the layers
-    const int64_t jn = row_of(tile + gridDim.x);
+    // while this tile goes through the layers: the next tile's vertex (its list
+    // entry was read one tile ago, so the loads do not wait for it) and the
+    // list entry of the tile after
     const VertexIn vn = load_vertex(d, v, jn);
+    const int64_t jnn = row_of(tile + 2 * gridDim.x);
     tc::fence_smem_async();
     tc::fence_before();
     __syncthreads();
@@ -390,6 +410,7 @@ __global__ void __launch_bounds__(128) k_mlp_infer_tc(Dev d, VertexPtrs v, const
     }
     j = jn;
     vi = vn;
+    jn = jnn;
   }
   if (!ok && tid == 0) atomicOr(d.err, 1u);
   tc::fence_before();
@@ -481,11 +502,12 @@ struct Smem {
   alignas(128) unsigned char w1[64 * 80 * 2];
   alignas(128) unsigned char w2[64 * 64 * 2];
   alignas(128) unsigned char w3[64 * 64 * 2];
-  alignas(128) unsigned char x0[128 * 80 * 2];  // X_0 [sample][in]
+  alignas(128) unsigned char x0[2][128 * 80 * 2];  // X_0 [sample][in] of two work items
   alignas(128) unsigned char h[3][128 * 64 * 2];  // X_1..X_3 (hidden outputs) [sample][feature]
   alignas(128) unsigned char ones[128 * 16 * 2];
   alignas(128) unsigned char dz[128 * 64 * 2];  // dY (16 wide), then dZ_2, dZ_1, dZ_0 [sample][out]
   alignas(128) unsigned char pad[kPad];
+  float4 tgt[2][128];  // the two work items' targets (w: the sample is valid)
   float bias[3 * 64 + 16];
   alignas(8) unsigned long long mbar;
   uint32_t tmem;
@@ -539,39 +561,194 @@ __device__ __forceinline__ void sync_tc() {
 }
 }  // namespace tct
 
-// Samples: idx[] when given, else drawn with select_sample.  The gradient
-// d.grad must be 16-byte aligned (vector reductions).
-__global__ void __launch_bounds__(128, 1) k_mlp_grad_tc(Dev d, VertexPtrs v, const float* tr,
-                                                        const float* tg, const float* tb,
-                                                        const int32_t* idx, SampleSel sel,
-                                                        uint32_t batch) {
+// ---- the training launch
+// One launch takes `steps` Adam steps (or computes one gradient, without
+// Adam).  A CTA of 384 threads works through 128-sample tiles (the MMA's M),
+// one work item (step, tile) at a time:
+//  warps 0..7   the chain of products (forward, output delta, backward with
+//               the weight and bias gradients) and their epilogues.  Warps w
+//               and w + 4 may read the same 32 tensor-memory lanes (samples,
+//               or outputs for the gradients), so they split every 64-column
+//               product between them, half the columns each.
+//  warps 8..11  draw, gather and encode the NEXT work item's samples (thread
+//               t: sample t) into the other of two input buffers, so that the
+//               samples' memory latency and the encoding overlap the chain.
+// With Adam, the CTAs meet at the end of each step; the last to arrive applies
+// Adam to all parameters and releases the others, which then stage the new
+// weights.
+constexpr int kMaxSteps = 8;        // Adam steps per launch
+constexpr int kTrainThreads = 384;  // 8 chain warps + 4 sampling warps
+
+struct AdamStep {
+  float lr, b1, b2, eps, bc1, bc2;
+};
+
+struct TrainArgs {
+  Dev d;
+  VertexPtrs v;
+  const float* tr;
+  const float* tg;
+  const float* tb;
+  const int32_t* idx;  // the samples when given (then one step, no Adam)
+  SampleSel sel;       // sel.step: the index of the launch's first step
+  float* grad;         // FP32 gradient accumulator, 16-byte aligned
+  Ctrl* ctrl;          // grid barrier of the launch (Adam only)
+  unsigned int bar_base;  // arrivals counted in ctrl->bar_count before this launch
+  uint32_t batch, steps;
+  int adam;
+  float lr, beta1, beta2, eps;
+  float bc1[kMaxSteps], bc2[kMaxSteps];  // Adam's bias corrections, per step
+};
+
+// Index of parameter i's BF16 copy, or -1 (biases have none).
+__device__ __forceinline__ int bf16_index(int i) {
+  if (i < oB1) return bW1 + i;
+  if (i >= oW2 && i < oB2) return bW2 + (i - oW2);
+  if (i >= oW3 && i < oB3) return bW3 + (i - oW3);
+  if (i >= oW4 && i < oB4) return bW4 + (i - oW4);
+  return -1;
+}
+
+// One Adam update of parameter i from the accumulated gradient, which it
+// then clears; refreshes the BF16 copy.  Reads go through L2: the gradient
+// was accumulated by other multiprocessors' reductions.
+__device__ __forceinline__ void adam_apply(const Dev& d, float* grad, int i, const AdamStep& s) {
+  const float gr = __ldcg(grad + i);
+  float w = __ldcg(d.master + i);
+  const float m = s.b1 * __ldcg(d.m + i) + (1.f - s.b1) * gr;
+  const float vv = s.b2 * __ldcg(d.v + i) + (1.f - s.b2) * gr * gr;
+  d.m[i] = m;
+  d.v[i] = vv;
+  w -= s.lr * (m / s.bc1) / (sqrtf(vv / s.bc2) + s.eps);
+  d.master[i] = w;
+  grad[i] = 0.f;
+  const int dst = bf16_index(i);
+  if (dst >= 0) d.wb[dst] = __float2bfloat16_rn(w);
+}
+
+namespace tct {
+__device__ __forceinline__ void tmem_ld_x32(uint32_t taddr, uint32_t (&v)[32]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+               : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+               : "r"(taddr));
+}
+
+// bias + ReLU + BF16 of 32 accumulator columns (c0 .. c0 + 31) of row r, into
+// the A tile h; `bias` points at column c0's bias
+__device__ __forceinline__ void hidden_half(unsigned char* h, int r, int c0, const uint32_t (&acc)[32],
+                                            const float* bias) {
+#pragma unroll
+  for (int kb = 0; kb < 4; ++kb) {
+    uint32_t w[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int c = 8 * kb + 2 * q;
+      w[q] = pack2_relu(__uint_as_float(acc[c]) + bias[c], __uint_as_float(acc[c + 1]) + bias[c + 1]);
+    }
+    tc::st16(h, tc::cm(r, c0 + 8 * kb, 64), make_uint4(w[0], w[1], w[2], w[3]));
+  }
+}
+
+// The step's weights in shared memory: BF16 copies in the canonical layout
+// and the biases (FP32 masters).  Read through L2: the previous step's Adam
+// wrote them during this launch.  The BF16 copies are one contiguous run of
+// 16-byte chunks (W1, W2, W3, W4); a thread loads all of its chunks before it
+// stores any, so their latencies overlap.
+constexpr int kWbChunks = kWb / 8;  // 1792
+__device__ __forceinline__ void stage_chunk(Smem& s, int c, uint4 v) {
+  if (c < bW2 / 8) tc::st16(s.w1, tc::cm(c / 10, 8 * (c % 10), kIn), v);
+  else if (c < bW3 / 8) tc::st16(s.w2, tc::cm((c - bW2 / 8) / 8, 8 * (c % 8), kHid), v);
+  else if (c < bW4 / 8) tc::st16(s.w3, tc::cm((c - bW3 / 8) / 8, 8 * (c % 8), kHid), v);
+  else tc::st16(s.w4, tc::cm((c - bW4 / 8) / 8, 8 * (c % 8), kHid), v);
+}
+template <int NT>
+__device__ __forceinline__ void stage_weights(Smem& s, const Dev& d, int tid) {
+  constexpr int kPer = (kWbChunks + NT - 1) / NT;
+  const uint4* wb4 = reinterpret_cast<const uint4*>(d.wb);
+  uint4 v[kPer];
+#pragma unroll
+  for (int q = 0; q < kPer; ++q) {
+    const int c = tid + q * NT;
+    v[q] = c < kWbChunks ? __ldcg(wb4 + c) : make_uint4(0u, 0u, 0u, 0u);
+  }
+  float b = 0.f;
+  const int i = tid;
+  if (i < 64) b = __ldcg(d.master + oB1 + i);
+  else if (i < 128) b = __ldcg(d.master + oB2 + i - 64);
+  else if (i < 192) b = __ldcg(d.master + oB3 + i - 128);
+  else if (i < 192 + kOut) b = __ldcg(d.master + oB4 + i - 192);
+#pragma unroll
+  for (int q = 0; q < kPer; ++q) {
+    const int c = tid + q * NT;
+    if (c < kWbChunks) stage_chunk(s, c, v[q]);
+  }
+  if (i < 3 * 64 + 16) s.bias[i] = b;
+}
+}  // namespace tct
+
+// Named barrier 1 over the 256 threads of the product chain (warps 0..7); the
+// sampling warps are not held by it.
+__device__ __forceinline__ void chain_bar() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+__device__ __forceinline__ bool chain_bar_and(bool pred) {
+  uint32_t r;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n"
+      " bar.red.and.pred q, 1, 256, p;\n selp.u32 %0, 1, 0, q;\n}"
+      : "=r"(r)
+      : "r"(pred ? 1u : 0u)
+      : "memory");
+  return r != 0;
+}
+__device__ __forceinline__ void chain_sync_tc() {
+  tc::fence_smem_async();
+  tc::fence_before();
+  chain_bar();
+  tc::fence_after();
+}
+
+// Grid barrier of the training launch on a counter that only grows: each CTA
+// adds one arrival and waits until `target` arrivals (this barrier's place in
+// the sequence since the counter was last cleared) have been counted, so
+// nobody resets anything on the way out.  Bounded like the filter's grid
+// barrier (about two seconds, then kErrBarrierTimeout); false when it gave up.
+__device__ __forceinline__ bool grid_sync(Ctrl* c, unsigned int target) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    __threadfence();
+    atomicAdd(&c->bar_count, 1u);
+    const unsigned long long t0 = globaltimer_ns();
+    while (static_cast<int>(ld_acquire_u32(&c->bar_count) - target) < 0) {
+      if ((ld_acquire_u32(&c->error) & kErrBarrierTimeout) || globaltimer_ns() - t0 > 2000000000ull) {
+        atomicOr(&c->error, kErrBarrierTimeout);
+        ok = 0;
+        break;
+      }
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+__global__ void __launch_bounds__(kTrainThreads, 1) k_mlp_train_tc(TrainArgs a) {
   extern __shared__ unsigned char smem_raw[];
   tct::Smem& s = *reinterpret_cast<tct::Smem*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~static_cast<uintptr_t>(127));
+  const Dev& d = a.d;
   const int tid = threadIdx.x, warp = tid >> 5;
-  // this thread's sample first (its loads overlap the weight staging)
-  const uint32_t si = blockIdx.x * 128u + tid;
-  const int64_t j = si >= batch ? -1 : idx ? idx[si] : select_sample(sel, si);
-  const VertexIn vi = load_vertex(d, v, j);
-  const uint4* wb4 = reinterpret_cast<const uint4*>(d.wb);
-  for (int c = tid; c < 64 * kIn / 8; c += blockDim.x)
-    tc::st16(s.w1, tc::cm(c / 10, 8 * (c % 10), kIn), __ldg(wb4 + bW1 / 8 + c));
-  for (int c = tid; c < 64 * kHid / 8; c += blockDim.x) {
-    tc::st16(s.w2, tc::cm(c / 8, 8 * (c % 8), kHid), __ldg(wb4 + bW2 / 8 + c));
-    tc::st16(s.w3, tc::cm(c / 8, 8 * (c % 8), kHid), __ldg(wb4 + bW3 / 8 + c));
-  }
-  for (int c = tid; c < 16 * kHid / 8; c += blockDim.x)
-    tc::st16(s.w4, tc::cm(c / 8, 8 * (c % 8), kHid), __ldg(wb4 + bW4 / 8 + c));
+  const bool chain = warp < 8;               // warps 0..7: products and epilogues
+  const bool lower = tid < 128;              // chain warps 0..3
+  const int row = tid & 127;                 // sample (or output) row: lane (warp & 3) * 32 + lane
+  const uint32_t hc = 32u * ((warp >> 2) & 1);  // a chain warp's 32 columns of a 64-wide product
+  const uint32_t ntile = a.batch / kSamples;
+  // tiles of this CTA per step, and the work items (step, tile) in order
+  const uint32_t mine = blockIdx.x < ntile ? (ntile - 1u - blockIdx.x) / gridDim.x + 1u : 0u;
+  const uint32_t items = mine * a.steps;
   for (int c = tid; c < 128 * 16 / 8; c += blockDim.x)  // BF16 1.0 pairs
     tc::st16(s.ones, 16u * c, make_uint4(0x3F803F80u, 0x3F803F80u, 0x3F803F80u, 0x3F803F80u));
-  for (int i = tid; i < 3 * 64 + 16; i += blockDim.x) {
-    float b = 0.f;
-    if (i < 64) b = d.master[oB1 + i];
-    else if (i < 128) b = d.master[oB2 + i - 64];
-    else if (i < 192) b = d.master[oB3 + i - 128];
-    else if (i < 192 + kOut) b = d.master[oB4 + i - 192];
-    s.bias[i] = b;
-  }
   const uint32_t mbar = smem_u32(&s.mbar);
   if (tid == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar) : "memory");
@@ -585,135 +762,196 @@ __global__ void __launch_bounds__(128, 1) k_mlp_grad_tc(Dev d, VertexPtrs v, con
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
-  tc::encode_row(s.x0, tid, vi, j >= 0);
+  // sampling warps: draw, gather and encode work item `it` into buffer it & 1
+  // (encoded inputs X_0, targets and validity)
+  auto prepare = [&](uint32_t it) {
+    const uint32_t st = it / mine, tile = blockIdx.x + (it % mine) * gridDim.x;
+    SampleSel q = a.sel;
+    q.step = a.sel.step + st;
+    const uint32_t si = tile * static_cast<uint32_t>(kSamples) + row;
+    const int64_t j = si >= a.batch ? -1 : a.idx ? a.idx[si] : select_sample(q, si);
+    const VertexIn vi = load_vertex(d, a.v, j);
+    float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (j >= 0) t = make_float4(__ldg(a.tr + j), __ldg(a.tg + j), __ldg(a.tb + j), 1.f);
+    tc::encode_row(s.x0[it & 1u], row, vi, j >= 0);
+    s.tgt[it & 1u][row] = t;
+  };
+  if (!chain && items > 0) prepare(0);
   tct::sync_tc();
   const uint32_t tmem = s.tmem;
-  const uint32_t trow = tmem + (static_cast<uint32_t>(warp * 32) << 16);
+  const uint32_t tq = tmem + (static_cast<uint32_t>((warp & 3) * 32) << 16);  // this warp's lanes
   uint32_t parity = 0;
   bool ok = true;
   auto wait = [&]() {
-    ok = ok && __syncthreads_and(tc::mbar_wait(mbar, parity)) != 0;
+    ok = ok && chain_bar_and(tc::mbar_wait(mbar, parity));
     parity ^= 1u;
     tc::fence_after();
   };
-  // layer l's input X_l and weight W_l
-  auto X = [&](int l) -> const unsigned char* { return l == 0 ? s.x0 : s.h[l - 1]; };
-  auto W = [&](int l) -> const unsigned char* {
-    return l == 0 ? s.w1 : l == 1 ? s.w2 : l == 2 ? s.w3 : s.w4;
-  };
-  uint32_t acc[64];
-  // ---- forward: X_{l+1} = ReLU(X_l W_l^T + b_l), l = 0..2
-  for (int l = 0; l < 3 && ok; ++l) {
-    const uint32_t C = l == 0 ? kIn : kHid;
-    if (tid == 0) {
-      tct::issue(tmem, 0, tct::kmajor(X(l), C), tct::kmajor(W(l), C), 64, C / 16, false, false);
-      tc::commit(mbar);
+  const float invb = 1.0f / static_cast<float>(a.batch);
+
+  for (uint32_t it = 0; it < items && ok; ++it) {
+    const uint32_t st = it / mine;
+    const bool step_end = it % mine == mine - 1u;
+    if (chain) {
+      if (it % mine == 0) {  // the step's weights, written by the previous step's Adam
+        tct::stage_weights<256>(s, d, tid);
+        chain_sync_tc();
+      }
+      const unsigned char* x0 = s.x0[it & 1u];
+      // layer l's input X_l and weight W_l
+      auto X = [&](int l) -> const unsigned char* { return l == 0 ? x0 : s.h[l - 1]; };
+      auto W = [&](int l) -> const unsigned char* {
+        return l == 0 ? s.w1 : l == 1 ? s.w2 : l == 2 ? s.w3 : s.w4;
+      };
+      // gradient of layer l: gW_l = dZ_l^T X_l and gb_l = dZ_l^T 1 from the delta in s.dz
+      auto grad_issue = [&](int l) {
+        const uint32_t co = l == 3 ? 16u : 64u, ci = l == 0 ? kIn : kHid;
+        tct::issue(tmem, tct::gcol(l), tct::mnmajor(s.dz, co), tct::mnmajor(X(l), ci), ci, 8, true, true);
+        tct::issue(tmem, tct::bcol(l), tct::mnmajor(s.dz, co), tct::mnmajor(s.ones, 16), 16, 8, true, true);
+      };
+      // this warp's half of row `row` of gW_l, and (lower) gb_l[row] or (upper,
+      // layer 0) the row's inputs 64..79, into the global gradient
+      auto grad_out = [&](int l) {
+        const int out_dim = l == 3 ? kOut : kHid, in_dim = l == 0 ? kIn : kHid;
+        if ((warp & 3) * 32 >= out_dim) return;  // warp-uniform: rows past the outputs are not read
+        const int off = l == 0 ? oW1 : l == 1 ? oW2 : l == 2 ? oW3 : oW4;
+        const int boff = l == 0 ? oB1 : l == 1 ? oB2 : l == 2 ? oB3 : oB4;
+        uint32_t g[32], e[16];
+        tct::tmem_ld_x32(tq + tct::gcol(l) + hc, g);
+        if (lower) tc::tmem_ld_x16(tq + tct::bcol(l), e);
+        else if (l == 0) tc::tmem_ld_x16(tq + tct::gcol(0) + 64, e);
+        tc::tmem_wait_ld();
+        if (row < out_dim) {
+          float* rp = a.grad + off + row * in_dim;
+#pragma unroll
+          for (int q = 0; q < 8; ++q)
+            tct::red_v4(rp + hc + 4 * q, g[4 * q], g[4 * q + 1], g[4 * q + 2], g[4 * q + 3]);
+          if (lower) {
+            atomicAdd(a.grad + boff + row, __uint_as_float(e[0]));
+          } else if (l == 0) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+              tct::red_v4(rp + 64 + 4 * q, e[4 * q], e[4 * q + 1], e[4 * q + 2], e[4 * q + 3]);
+          }
+        }
+      };
+      uint32_t acc[32];
+      // ---- forward: X_{l+1} = ReLU(X_l W_l^T + b_l), l = 0..2
+      for (int l = 0; l < 3 && ok; ++l) {
+        const uint32_t C = l == 0 ? kIn : kHid;
+        if (tid == 0) {
+          tct::issue(tmem, 0, tct::kmajor(X(l), C), tct::kmajor(W(l), C), 64, C / 16, false, false);
+          tc::commit(mbar);
+        }
+        wait();
+        if (!ok) break;
+        tct::tmem_ld_x32(tq + hc, acc);
+        tc::tmem_wait_ld();
+        tct::hidden_half(s.h[l], row, static_cast<int>(hc), acc, s.bias + 64 * l + hc);
+        chain_sync_tc();
+      }
+      if (ok) {
+        if (tid == 0) {
+          tct::issue(tmem, 0, tct::kmajor(s.h[2], kHid), tct::kmajor(s.w4, kHid), 16, 4, false, false);
+          tc::commit(mbar);
+        }
+        wait();
+      }
+      if (ok) {
+        if (lower) {
+          uint32_t y[16];
+          tc::tmem_ld_x16(tq, y);
+          tc::tmem_wait_ld();
+          // output delta (y - target) / batch, rounded to BF16, as a 16-wide tile
+          const float4 t = s.tgt[it & 1u][row];
+          float dy[3] = {0.f, 0.f, 0.f};
+          if (t.w != 0.f) {
+            const float t3[3] = {t.x, t.y, t.z};
+#pragma unroll
+            for (int o = 0; o < 3; ++o)
+              dy[o] = __bfloat162float(__float2bfloat16_rn(
+                  (__uint_as_float(y[o]) + s.bias[192 + o] - t3[o]) * invb));
+          }
+          tc::st16(s.dz, tc::cm(row, 0, 16), make_uint4(pack2(dy[0], dy[1]), pack2(dy[2], 0.f), 0u, 0u));
+        } else {
+          tc::st16(s.dz, tc::cm(row, 8, 16), make_uint4(0u, 0u, 0u, 0u));
+        }
+        chain_sync_tc();
+      }
+      // ---- backward: for l = 3, 2, 1 the delta dZ_l in s.dz gives dX_l = dZ_l W_l
+      // and the gradients of layer l in one commit; then dZ_{l-1} = dX_l masked
+      // by X_l > 0 and rounded replaces it
+      for (int l = 3; l >= 1 && ok; --l) {
+        if (tid == 0) {
+          const uint32_t co = l == 3 ? 16u : 64u;
+          tct::issue(tmem, 0, tct::kmajor(s.dz, co), tct::mnmajor(W(l), kHid), 64, co / 16, false, true);
+          grad_issue(l);
+          tc::commit(mbar);
+        }
+        wait();
+        if (!ok) break;
+        tct::tmem_ld_x32(tq + hc, acc);
+        const unsigned char* xl = X(l);
+        uint4 hq[4];
+#pragma unroll
+        for (int kb = 0; kb < 4; ++kb)
+          hq[kb] = *reinterpret_cast<const uint4*>(xl + tc::cm(row, static_cast<int>(hc) + 8 * kb, 64));
+        tc::tmem_wait_ld();
+#pragma unroll
+        for (int kb = 0; kb < 4; ++kb) {
+          const uint32_t hw[4] = {hq[kb].x, hq[kb].y, hq[kb].z, hq[kb].w};
+          uint32_t zw[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int c = 8 * kb + 2 * q;
+            zw[q] = pack2(lo_f(hw[q]) > 0.f ? __uint_as_float(acc[c]) : 0.f,
+                          hi_f(hw[q]) > 0.f ? __uint_as_float(acc[c + 1]) : 0.f);
+          }
+          tc::st16(s.dz, tc::cm(row, static_cast<int>(hc) + 8 * kb, 64), make_uint4(zw[0], zw[1], zw[2], zw[3]));
+        }
+        grad_out(l);
+        chain_sync_tc();
+      }
+      if (ok) {
+        if (tid == 0) {
+          grad_issue(0);
+          tc::commit(mbar);
+        }
+        wait();
+        if (ok) grad_out(0);
+      }
+    } else if (it + 1 < items) {
+      prepare(it + 1);  // the next work item, while the chain runs this one
     }
-    wait();
+    // the chain is done with X_0 of this item and the sampling warps with the
+    // next item's buffers (made visible to the tensor cores); the chain's
+    // outcome reaches every thread
+    tc::fence_smem_async();
+    tc::fence_before();
+    ok = __syncthreads_and(ok) != 0;
+    tc::fence_after();
     if (!ok) break;
-    tc::tmem_ld_x64(trow, acc);
-    tc::tmem_wait_ld();
-    tc::hidden_row(s.h[l], tid, acc, s.bias + 64 * l);
-    tct::sync_tc();
-  }
-  float dy[3] = {0.f, 0.f, 0.f};
-  if (ok) {
-    if (tid == 0) {
-      tct::issue(tmem, 0, tct::kmajor(s.h[2], kHid), tct::kmajor(s.w4, kHid), 16, 4, false, false);
-      tc::commit(mbar);
-    }
-    wait();
-  }
-  if (ok) {
-    uint32_t y[16];
-    tc::tmem_ld_x16(trow, y);
-    tc::tmem_wait_ld();
-    // output delta (y - target) / batch, rounded to BF16, as a 16-wide tile
-    const float invb = 1.0f / static_cast<float>(batch);
-    if (j >= 0) {
-      const float t3[3] = {__ldg(tr + j), __ldg(tg + j), __ldg(tb + j)};
-#pragma unroll
-      for (int o = 0; o < 3; ++o)
-        dy[o] = __bfloat162float(__float2bfloat16_rn(
-            (__uint_as_float(y[o]) + s.bias[192 + o] - t3[o]) * invb));
-    }
-    tc::st16(s.dz, tc::cm(tid, 0, 16), make_uint4(pack2(dy[0], dy[1]), pack2(dy[2], 0.f), 0u, 0u));
-    tc::st16(s.dz, tc::cm(tid, 8, 16), make_uint4(0u, 0u, 0u, 0u));
-    tct::sync_tc();
-  }
-  // gradient of layer l: gW_l = dZ_l^T X_l and gb_l = dZ_l^T 1 from the delta in s.dz
-  auto grad_issue = [&](int l) {
-    const uint32_t co = l == 3 ? 16u : 64u, ci = l == 0 ? kIn : kHid;
-    tct::issue(tmem, tct::gcol(l), tct::mnmajor(s.dz, co), tct::mnmajor(X(l), ci), ci, 8, true, true);
-    tct::issue(tmem, tct::bcol(l), tct::mnmajor(s.dz, co), tct::mnmajor(s.ones, 16), 16, 8, true, true);
-  };
-  // row o of gW_l (thread o) and gb_l[o] into the global gradient
-  auto grad_out = [&](int l) {
-    const int out_dim = l == 3 ? kOut : kHid, in_dim = l == 0 ? kIn : kHid;
-    if (warp * 32 >= out_dim) return;  // warp-uniform: rows past the outputs are not read
-    const int off = l == 0 ? oW1 : l == 1 ? oW2 : l == 2 ? oW3 : oW4;
-    const int boff = l == 0 ? oB1 : l == 1 ? oB2 : l == 2 ? oB3 : oB4;
-    uint32_t g[64], e[16], bq[16];
-    tc::tmem_ld_x64(trow + tct::gcol(l), g);
-    tc::tmem_ld_x16(trow + tct::gcol(l) + 64, e);  // layer 0: inputs 64..79, else the bias block
-    if (l == 0) tc::tmem_ld_x16(trow + tct::bcol(0), bq);
-    tc::tmem_wait_ld();
-    if (tid < out_dim) {
-      float* row = d.grad + off + tid * in_dim;
-#pragma unroll
-      for (int q = 0; q < 16; ++q) tct::red_v4(row + 4 * q, g[4 * q], g[4 * q + 1], g[4 * q + 2], g[4 * q + 3]);
-      if (l == 0) {
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-          tct::red_v4(row + 64 + 4 * q, e[4 * q], e[4 * q + 1], e[4 * q + 2], e[4 * q + 3]);
-        atomicAdd(d.grad + boff + tid, __uint_as_float(bq[0]));
-      } else {
-        atomicAdd(d.grad + boff + tid, __uint_as_float(e[0]));
+    if (a.adam && step_end) {
+      // every gradient reduction in; Adam, one parameter per thread of the
+      // grid; the new weights visible before the next step stages them
+      const unsigned int base = a.bar_base + 2u * st * gridDim.x;
+      if (!grid_sync(a.ctrl, base + gridDim.x)) {
+        ok = false;
+        break;
+      }
+      const AdamStep as{a.lr, a.beta1, a.beta2, a.eps, a.bc1[st], a.bc2[st]};
+      for (int i = blockIdx.x * blockDim.x + tid; i < kP; i += gridDim.x * blockDim.x)
+        adam_apply(d, a.grad, i, as);
+      if (!grid_sync(a.ctrl, base + 2u * gridDim.x)) {
+        ok = false;
+        break;
       }
     }
-  };
-  // ---- backward: for l = 3, 2, 1 the delta dZ_l in s.dz gives dX_l = dZ_l W_l
-  // and the gradients of layer l in one commit; then dZ_{l-1} = dX_l masked
-  // by X_l > 0 and rounded replaces it
-  for (int l = 3; l >= 1 && ok; --l) {
-    if (tid == 0) {
-      const uint32_t co = l == 3 ? 16u : 64u;
-      tct::issue(tmem, 0, tct::kmajor(s.dz, co), tct::mnmajor(W(l), kHid), 64, co / 16, false, true);
-      grad_issue(l);
-      tc::commit(mbar);
-    }
-    wait();
-    if (!ok) break;
-    tc::tmem_ld_x64(trow, acc);
-    const unsigned char* xl = X(l);
-    uint4 hq[8];
-#pragma unroll
-    for (int kb = 0; kb < 8; ++kb) hq[kb] = *reinterpret_cast<const uint4*>(xl + tc::cm(tid, 8 * kb, 64));
-    tc::tmem_wait_ld();
-#pragma unroll
-    for (int kb = 0; kb < 8; ++kb) {
-      const uint32_t hw[4] = {hq[kb].x, hq[kb].y, hq[kb].z, hq[kb].w};
-      uint32_t zw[4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int c = 8 * kb + 2 * q;
-        zw[q] = pack2(lo_f(hw[q]) > 0.f ? __uint_as_float(acc[c]) : 0.f,
-                      hi_f(hw[q]) > 0.f ? __uint_as_float(acc[c + 1]) : 0.f);
-      }
-      tc::st16(s.dz, tc::cm(tid, 8 * kb, 64), make_uint4(zw[0], zw[1], zw[2], zw[3]));
-    }
-    grad_out(l);
-    tct::sync_tc();
   }
-  if (ok) {
-    if (tid == 0) {
-      grad_issue(0);
-      tc::commit(mbar);
-    }
-    wait();
-    if (ok) grad_out(0);
+  if (!ok && tid == 0) {
+    atomicOr(d.err, 1u);
+    if (a.ctrl) atomicOr(&a.ctrl->error, kErrBarrierTimeout);  // the other CTAs stop waiting
   }
-  if (!ok && tid == 0) atomicOr(d.err, 1u);
   tc::fence_before();
   __syncthreads();
   if (warp == 0)
@@ -722,28 +960,12 @@ __global__ void __launch_bounds__(128, 1) k_mlp_grad_tc(Dev d, VertexPtrs v, con
                  : "memory");
 }
 
-__global__ void k_mlp_adam(Dev d, float lr, float b1, float b2, float eps, float bc1, float bc2,
-                           int apply) {
+// BF16 copies of the master weights (after they were set from the host).
+__global__ void k_mlp_refresh_bf16(Dev d) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= kP) return;
-  float w = d.master[i];
-  if (apply) {
-    const float gr = d.grad[i];
-    const float m = b1 * d.m[i] + (1.f - b1) * gr;
-    const float vv = b2 * d.v[i] + (1.f - b2) * gr * gr;
-    d.m[i] = m;
-    d.v[i] = vv;
-    w -= lr * (m / bc1) / (sqrtf(vv / bc2) + eps);
-    d.master[i] = w;
-    d.grad[i] = 0.f;
-  }
-  // BF16 copy (biases have none)
-  int dst = -1;
-  if (i < oB1) dst = bW1 + i;
-  else if (i >= oW2 && i < oB2) dst = bW2 + (i - oW2);
-  else if (i >= oW3 && i < oB3) dst = bW3 + (i - oW3);
-  else if (i >= oW4 && i < oB4) dst = bW4 + (i - oW4);
-  if (dst >= 0) d.wb[dst] = __float2bfloat16_rn(w);
+  const int dst = bf16_index(i);
+  if (dst >= 0) d.wb[dst] = __float2bfloat16_rn(d.master[i]);
 }
 
 // Self-test of the bounded wait: an mbarrier that nothing completes; the wait
@@ -774,6 +996,8 @@ struct pps_mlp {
   pps::mlp::Dev dev{};
   uint32_t step = 0;  // Adam steps taken
   int sms = 0;                  // multiprocessors of the device
+  pps::Ctrl* ctrl = nullptr;    // training: grid barriers around Adam
+  uint32_t bar_arrivals = 0;    // training: arrivals counted in ctrl->bar_count so far
   int32_t* list = nullptr;      // inference: indices of the vertices to evaluate
   uint32_t* counter = nullptr;  // inference: their number
   size_t list_cap = 0;
@@ -818,9 +1042,52 @@ int check_mlp(pps_mlp* m) {
 
 
 int refresh_bf16(pps_mlp* m, cudaStream_t st) {
-  pps::mlp::k_mlp_adam<<<(pps::mlp::kP + 255) / 256, 256, 0, st>>>(m->dev, 0.f, 0.f, 0.f, 0.f, 1.f,
-                                                                    1.f, 0);
+  pps::mlp::k_mlp_refresh_bf16<<<(pps::mlp::kP + 255) / 256, 256, 0, st>>>(m->dev);
   MLP_CUDA(cudaGetLastError());
+  return PPS_OK;
+}
+
+// One training launch: `steps` (at most kMaxSteps) Adam steps on samples drawn
+// with `sel` (cooperative: the steps are separated by grid barriers), or, with
+// adam false, the gradient of one step over the given samples `idx`.
+int launch_train(pps_mlp* m, const pps_vertices* v, const float* tr, const float* tg,
+                 const float* tb, const int32_t* idx, const pps::mlp::SampleSel& sel,
+                 uint32_t batch, uint32_t steps, bool adam, float* grad, cudaStream_t st) {
+  pps::mlp::TrainArgs a{};
+  a.d = m->dev;
+  a.v = vptrs(v);
+  a.tr = tr;
+  a.tg = tg;
+  a.tb = tb;
+  a.idx = idx;
+  a.sel = sel;
+  a.grad = grad;
+  a.ctrl = adam ? m->ctrl : nullptr;
+  a.bar_base = m->bar_arrivals;
+  a.batch = batch;
+  a.steps = steps;
+  a.adam = adam ? 1 : 0;
+  a.lr = m->p.lr;
+  a.beta1 = m->p.beta1;
+  a.beta2 = m->p.beta2;
+  a.eps = m->p.eps;
+  for (uint32_t k = 0; adam && k < steps; ++k) {
+    ++m->step;
+    a.bc1[k] = 1.f - std::pow(m->p.beta1, static_cast<float>(m->step));
+    a.bc2[k] = 1.f - std::pow(m->p.beta2, static_cast<float>(m->step));
+  }
+  const int grid = static_cast<int>(std::min<uint32_t>(batch / pps::mlp::kSamples,
+                                                       static_cast<uint32_t>(m->sms)));
+  if (adam) {
+    m->bar_arrivals += 2u * steps * static_cast<uint32_t>(grid);
+    void* args[] = {&a};
+    MLP_CUDA(cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(pps::mlp::k_mlp_train_tc),
+                                         dim3(grid), dim3(pps::mlp::kTrainThreads), args,
+                                         pps::mlp::tct::kSmemBytes, st));
+  } else {
+    pps::mlp::k_mlp_train_tc<<<grid, pps::mlp::kTrainThreads, pps::mlp::tct::kSmemBytes, st>>>(a);
+    MLP_CUDA(cudaGetLastError());
+  }
   return PPS_OK;
 }
 
@@ -857,6 +1124,8 @@ int pps_mlp_create(pps_mlp** out, const pps_mlp_params* p, const float* init_hos
   if (e == cudaSuccess) e = cudaMalloc(&m->dev.wb, pps::mlp::kWb * sizeof(__nv_bfloat16));
   if (e == cudaSuccess) e = cudaMalloc(&m->dev.err, sizeof(unsigned int));
   if (e == cudaSuccess) e = cudaMalloc(&m->counter, sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMalloc(&m->ctrl, sizeof(pps::Ctrl));
+  if (e == cudaSuccess) e = cudaMemset(m->ctrl, 0, sizeof(pps::Ctrl));
   if (e == cudaSuccess) e = cudaMemset(m->dev.err, 0, sizeof(unsigned int));
   if (e == cudaSuccess) e = cudaMemset(m->dev.m, 0, P * sizeof(float));
   if (e == cudaSuccess) e = cudaMemset(m->dev.v, 0, P * sizeof(float));
@@ -880,7 +1149,7 @@ int pps_mlp_create(pps_mlp** out, const pps_mlp_params* p, const float* init_hos
   if (e == cudaSuccess) {
     if (cudaFuncSetAttribute(pps::mlp::k_mlp_infer_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(pps::mlp::tc::kSmemBytes)) != cudaSuccess ||
-        cudaFuncSetAttribute(pps::mlp::k_mlp_grad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(pps::mlp::k_mlp_train_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(pps::mlp::tct::kSmemBytes)) != cudaSuccess)
       e = cudaGetLastError();
   }
@@ -894,6 +1163,7 @@ int pps_mlp_create(pps_mlp** out, const pps_mlp_params* p, const float* init_hos
     cudaFree(m->dev.wb);
     cudaFree(m->dev.err);
     cudaFree(m->counter);
+    cudaFree(m->ctrl);
     delete m;
     cudaGetLastError();
     return mfail(e == cudaErrorMemoryAllocation ? PPS_ENOMEM : PPS_ECUDA,
@@ -913,6 +1183,7 @@ int pps_mlp_destroy(pps_mlp* m) {
   cudaFree(m->dev.wb);
   cudaFree(m->dev.err);
   cudaFree(m->counter);
+  cudaFree(m->ctrl);
   cudaFree(m->list);
   delete m;
   return PPS_OK;
@@ -941,7 +1212,13 @@ int pps_mlp_get_weights(pps_mlp* m, float* host, size_t count) {
   MLP_CUDA(cudaMemcpy(host, m->dev.master, count * sizeof(float), cudaMemcpyDeviceToHost));
   unsigned int err = 0;
   MLP_CUDA(cudaMemcpy(&err, m->dev.err, sizeof(err), cudaMemcpyDeviceToHost));
-  if (err) return mfail(PPS_EDEVICE, "an inference launch gave up waiting for the tensor cores");
+  if (err) {
+    // reported once: the error word and the grid barrier start afresh
+    MLP_CUDA(cudaMemset(m->dev.err, 0, sizeof(unsigned int)));
+    MLP_CUDA(cudaMemset(m->ctrl, 0, sizeof(pps::Ctrl)));
+    m->bar_arrivals = 0;
+    return mfail(PPS_EDEVICE, "a training or inference launch gave up waiting (tensor cores or grid barrier)");
+  }
   return PPS_OK;
 }
 
@@ -955,12 +1232,7 @@ int pps_mlp_gradient(pps_mlp* m, const pps_vertices* v, const float* tr, const f
     return mfail(PPS_EINVAL, "batch must be a positive multiple of 128");
   const cudaStream_t st = static_cast<cudaStream_t>(stream);
   MLP_CUDA(cudaMemsetAsync(grad_out, 0, pps::mlp::kP * sizeof(float), st));
-  pps::mlp::Dev d = m->dev;
-  d.grad = grad_out;
-  pps::mlp::k_mlp_grad_tc<<<batch / 128, 128, pps::mlp::tct::kSmemBytes, st>>>(
-      d, vptrs(v), tr, tg, tb, idx, pps::mlp::SampleSel{}, batch);
-  MLP_CUDA(cudaGetLastError());
-  return PPS_OK;
+  return launch_train(m, v, tr, tg, tb, idx, pps::mlp::SampleSel{}, batch, 1, false, grad_out, st);
 }
 
 int pps_mlp_train(pps_mlp* m, const pps_vertices* v, size_t n, const pps_output* filtered,
@@ -972,17 +1244,12 @@ int pps_mlp_train(pps_mlp* m, const pps_vertices* v, size_t n, const pps_output*
   if (n >= (1ull << 31)) return mfail(PPS_EINVAL, "n too large");
   const cudaStream_t st = static_cast<cudaStream_t>(stream);
   const uint32_t B = m->p.batch;
-  for (uint32_t s = 0; s < m->p.steps; ++s) {
-    const pps::mlp::SampleSel sel{filtered->count, n, m->p.seed, frame, s, m->p.train_min_count};
-    pps::mlp::k_mlp_grad_tc<<<B / 128, 128, pps::mlp::tct::kSmemBytes, st>>>(
-        m->dev, vptrs(v), filtered->r, filtered->g, filtered->b, nullptr, sel, B);
-    MLP_CUDA(cudaGetLastError());
-    ++m->step;
-    const float bc1 = 1.f - std::pow(m->p.beta1, static_cast<float>(m->step));
-    const float bc2 = 1.f - std::pow(m->p.beta2, static_cast<float>(m->step));
-    pps::mlp::k_mlp_adam<<<(pps::mlp::kP + 255) / 256, 256, 0, st>>>(
-        m->dev, m->p.lr, m->p.beta1, m->p.beta2, m->p.eps, bc1, bc2, 1);
-    MLP_CUDA(cudaGetLastError());
+  for (uint32_t s0 = 0; s0 < m->p.steps; s0 += pps::mlp::kMaxSteps) {
+    const uint32_t cnt = std::min<uint32_t>(m->p.steps - s0, pps::mlp::kMaxSteps);
+    const pps::mlp::SampleSel sel{filtered->count, n, m->p.seed, frame, s0, m->p.train_min_count};
+    if (int rc = launch_train(m, v, filtered->r, filtered->g, filtered->b, nullptr, sel, B, cnt, true,
+                              m->dev.grad, st))
+      return rc;
   }
   return PPS_OK;
 }
