@@ -348,6 +348,14 @@ def run_ours(args):
             frames, cfg, blended_frames=3)}
         precision["error_sample"] = ("first 1,000,000 vertices of the leading HD frames "
                                      "filtered as frames of their own, off the timed path")
+    merge = {}
+    if not args.no_fallbacks:
+        for m, name in ((1, "none"), (2, "gated"), (3, "always")):
+            merge[name] = {
+                "temporal_ms": history_leg(frames, cfg, calls, fsteps, args.warmup,
+                                           tune={"merge": m})["ms_per_frame"],
+                "plain_ms": history_leg(frames, cfg, calls, fsteps, args.warmup, blend=0,
+                                        hist_mode=0, tune={"merge": m})["ms_per_frame"]}
     ms, job_n = reduce_ranks(ms, float(total_n), dev)
     value = job_n / (ms / 1e3)
     ms_step = ms / args.steps
@@ -430,6 +438,12 @@ def run_ours(args):
                 "workload": "the headline temporal HD frames with an evicting history of "
                             "2^23 cells (evict) or a history that follows changes of "
                             "resolution (migrate)", **hvariants}
+        if merge:
+            line["merge_modes"] = {
+                "workload": "the headline HD frames (temporal and plain) with each warp "
+                            "aggregation of the pipelined insert (pps_tuning.merge): none, "
+                            "gated (__match_any_sync where neighbouring lanes repeat a key; "
+                            "the default), always", **merge}
         if precision:
             line["precision"] = {
                 "workload": "the headline HD frames: fixed-point (int64) accumulation without "
@@ -523,7 +537,7 @@ def fallback_leg(frames, cfg, calls, steps, warmup, fallback, status):
             "fallback_share": share}
 
 
-def history_leg(frames, cfg, calls, steps, warmup, blend=1, **table_kw):
+def history_leg(frames, cfg, calls, steps, warmup, blend=1, tune=None, **table_kw):
     """The headline workload with a table variant, same timing as the
     headline: "evict" = an evicting history of 2^23 cells (Sec. 3.4.3),
     "migrate" = the history following changes of resolution (Sec. 3.4.2;
@@ -533,6 +547,8 @@ def history_leg(frames, cfg, calls, steps, warmup, blend=1, **table_kw):
     import torch
     from paper_1902_05942_gb300 import pps
     tab = pps.Table(cfg, **table_kw)
+    if tune:
+        tab.tune(**tune)
     L = pps.lib()
     stream = torch.cuda.current_stream()
 

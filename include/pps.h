@@ -268,9 +268,10 @@ typedef struct pps_stats_t {
  *             (pipelined while the slot index fits in L2, T <= 2^23; per
  *             thread for larger tables), 1 = per thread (each thread builds its vertices'
  *             keys, then probes and accumulates them), 2 = pipelined (key
- *             warps build keys, merge equal ones within the warp and queue one
- *             entry per distinct key in shared memory; probe warps run the
- *             table operations of four queued keys per thread at once).  Frames
+ *             warps build keys, merge equal ones within the warp as `merge`
+ *             says and queue one entry per group in shared memory; probe
+ *             warps run the table operations of four queued keys per thread
+ *             at once).  Frames
  *             with an evicting history or the neighborhood fallback always
  *             insert per thread.
  *  key_warps  pipelined insert: key warps of the 16 warps of a CTA (the rest
@@ -278,6 +279,14 @@ typedef struct pps_stats_t {
  *  block      batched launch (taken from the first view's table): threads
  *             per CTA, 256 or 512; 0 = library default (512).  Each CTA
  *             takes tiles of 2,048 vertices, 2048 / block per thread.
+ *  merge      pipelined insert: warp aggregation of equal keys before they are
+ *             queued: 0 = library default (2); 1 = none, one queue entry per
+ *             vertex; 2 = merge with __match_any_sync (the lowest lane of each
+ *             group of equal keys leads, the others add their contributions
+ *             to its entry) in the warps where two neighbouring lanes hold
+ *             equal keys, and skip the match elsewhere (coherent primary hits
+ *             repeat keys across neighbouring pixels; secondary bounces
+ *             rarely repeat one within a warp); 3 = merge in every warp.
  *  reserved   must be zero.
  */
 typedef struct pps_tuning {
@@ -285,7 +294,8 @@ typedef struct pps_tuning {
   uint32_t insert;
   uint32_t key_warps;
   uint32_t block;
-  uint32_t reserved[4];
+  uint32_t merge;
+  uint32_t reserved[3];
 } pps_tuning;
 
 typedef struct pps_table pps_table;

@@ -203,6 +203,7 @@ pps::InsertShape insert_shape(const pps_table* t) {
   const bool big = t->T > (1u << 23);
   s.pipelined = t->tune.insert == 2 || (t->tune.insert == 0 && !big) ? 1 : 0;
   s.key_warps = t->tune.key_warps ? static_cast<int>(t->tune.key_warps) : 8;
+  s.merge = t->tune.merge ? static_cast<int>(t->tune.merge) : 2;
   return s;
 }
 
@@ -797,6 +798,7 @@ int pps_set_tuning(pps_table* t, const pps_tuning* tune) {
     return fail(PPS_EINVAL, "block must be 0, 256 or 512");
   if (tune->key_warps != 0 && tune->key_warps != 4 && tune->key_warps != 8 && tune->key_warps != 12)
     return fail(PPS_EINVAL, "key_warps must be 0, 4, 8 or 12");
+  if (tune->merge > 3) return fail(PPS_EINVAL, "merge must be 0, 1, 2 or 3");
   for (uint32_t r : tune->reserved)
     if (r) return fail(PPS_EINVAL, "reserved fields must be zero");
   t->tune = *tune;
@@ -812,6 +814,7 @@ int pps_get_tuning(pps_table* t, pps_tuning* tune) {
   tune->insert = insert_shape(t).pipelined ? 2u : 1u;
   tune->key_warps = t->tune.key_warps ? t->tune.key_warps : 8u;
   tune->block = t->tune.block ? t->tune.block : 512u;
+  tune->merge = static_cast<uint32_t>(insert_shape(t).merge);
   return PPS_OK;
 }
 

@@ -23,12 +23,14 @@ struct FusedPlan {
   bool evict = false;      // the kernel variant for an evicting history
   bool neigh = false;      // the kernel variant with the neighborhood search
   int key_warps = 0;       // > 0: the pipelined insert (k_fused_ws) with this many key warps
+  int merge = 2;           // pipelined insert: warp aggregation of equal keys (pps_tuning.merge)
 };
 
 // How a table's persistent launch inserts (pps_tuning.insert / key_warps).
 struct InsertShape {
   int pipelined = 1;  // 1: key warps and probe warps on alternate chunks; 0: per thread
   int key_warps = 8;  // of the 16 warps of a CTA (4, 8 or 12)
+  int merge = 2;      // 1 none, 2 where neighbouring lanes repeat a key, 3 always
 };
 
 // One view of a batched launch: its table, key constants, vertices and

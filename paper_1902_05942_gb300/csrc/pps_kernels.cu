@@ -965,6 +965,7 @@ struct FusedArgs {
   int vec, ovec, blend;
   int sweep;     // zero the whole slot table at the end instead of slot by slot
   uint32_t* nq;  // neighborhood search: the queue of low-count vertices
+  int merge;     // pipelined insert: 1 no warp aggregation, 2 gated, 3 always
 };
 
 // The persistent kernel.  Phase A hands out tiles of kFusedTile consecutive
@@ -1228,15 +1229,25 @@ struct WsLayout {
   }
 };
 
-// Append the queue entry of vertex j (valid) of this warp's lanes `vm`:
-// merge equal keys among the warp's lanes (the lowest lane of a group leads,
-// the others add their contributions to its entry), one entry per group.
+// Append the queue entry of vertex j (valid) of this warp's lanes `vm` (the
+// valid lanes are consecutive vertices): merge equal keys among the warp's
+// lanes (the lowest lane of a group leads, the others add their contributions
+// to its entry), one entry per group.  `merge`: 1 no merging (every lane its
+// own group); 2 merge only when two neighbouring lanes hold equal keys, which
+// one shuffle and a vote find (coherent primary hits repeat keys across
+// neighbouring pixels, secondary bounces rarely repeat one within a warp, and
+// there the match costs more than the probes it saves); 3 always merge.
 __device__ __forceinline__ void ws_enqueue(const TableDev& t, uint4* keys, float4* sums, WsHeader* h,
                                            unsigned vm, const Key& k, size_t j, float r, float g,
-                                           float b) {
+                                           float b, int merge) {
   const uint32_t lane = threadIdx.x & 31;
   const unsigned long long kk = (static_cast<unsigned long long>(k.h1) << 32) | k.fp;
-  const unsigned grp = __match_any_sync(vm, kk);
+  bool match = merge == 3;
+  if (merge == 2) {
+    const unsigned long long up = __shfl_up_sync(vm, kk, 1);
+    match = __ballot_sync(vm, lane > 0 && up == kk) != 0u;
+  }
+  const unsigned grp = match ? __match_any_sync(vm, kk) : 1u << lane;
   const uint32_t leader = __ffs(grp) - 1;
   const bool lead = leader == lane;
   const unsigned lm = __ballot_sync(vm, lead);
@@ -1250,7 +1261,8 @@ __device__ __forceinline__ void ws_enqueue(const TableDev& t, uint4* keys, float
     if (!t.fixed)
       sums[e] = make_float4(r, g, b, __uint_as_float(static_cast<uint32_t>(__popc(grp))));
   }
-  if (t.fixed) return;  // the probe warps sum the members exactly
+  // fixed point: the probe warps sum the members exactly; no match: every lane leads
+  if (t.fixed || !match) return;
   __syncwarp(vm);
   if (!lead) {
     atomicAdd(&sums[e].x, r);
@@ -1300,7 +1312,7 @@ __device__ __forceinline__ void ws_key_chunk(const FusedArgs& a, uint4* keys, fl
       const size_t j = base + q * KT;
       const bool valid = j < cend;
       const unsigned vm = __ballot_sync(0xFFFFFFFFu, valid);
-      if (valid) ws_enqueue(t, keys, sums, h, vm, k[q], j, r[q], g[q], b[q]);
+      if (valid) ws_enqueue(t, keys, sums, h, vm, k[q], j, r[q], g[q], b[q], a.merge);
     }
   }
 }
@@ -1934,6 +1946,7 @@ cudaError_t plan_fused(size_t n, bool temporal, int batch, FusedPlan* plan, bool
   plan->key_warps = 0;
   if (shape.pipelined && !evict && !neigh) {
     const int kw = shape.key_warps == 4 || shape.key_warps == 12 ? shape.key_warps : 8;
+    plan->merge = shape.merge;
     return plan_ws(n, temporal, kw, fixed, plan);
   }
   const void* fn = fused_kernel(temporal, batch, evict, neigh);
@@ -2000,6 +2013,7 @@ cudaError_t launch_fused(const KeyConst& kc, const TableDev& t, const VertexPtrs
   a.blend = blend ? 1 : 0;
   a.sweep = sweep_pays(t, n) ? 1 : 0;
   a.nq = nq;
+  a.merge = plan.merge;
   void* args[] = {&a};
   if (plan.key_warps > 0)
     return cudaLaunchCooperativeKernel(ws_kernel(temporal, plan.key_warps), dim3(plan.grid),

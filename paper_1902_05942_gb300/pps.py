@@ -60,7 +60,7 @@ class pps_output(ctypes.Structure):
 
 class pps_tuning(ctypes.Structure):
     _fields_ = [("batch", _u32), ("insert", _u32), ("key_warps", _u32), ("block", _u32),
-                ("reserved", _u32 * 4)]
+                ("merge", _u32), ("reserved", _u32 * 3)]
 
 
 class pps_stats_t(ctypes.Structure):
@@ -319,14 +319,17 @@ def pps_keys(handle, v: pps_vertices, n: int, h_out: torch.Tensor, f_out: torch.
                           _ptr(f_out, n, torch.int32, "f_out"), _stream(stream)))
 
 
-def pps_set_tuning(handle, batch: int = 0, insert: int = 0, key_warps: int = 0, block: int = 0):
-    _check(lib().pps_set_tuning(handle, ctypes.byref(pps_tuning(batch, insert, key_warps, block))))
+def pps_set_tuning(handle, batch: int = 0, insert: int = 0, key_warps: int = 0, block: int = 0,
+                   merge: int = 0):
+    _check(lib().pps_set_tuning(handle, ctypes.byref(pps_tuning(batch, insert, key_warps, block,
+                                                                merge))))
 
 
 def pps_get_tuning(handle) -> dict:
     t = pps_tuning()
     _check(lib().pps_get_tuning(handle, ctypes.byref(t)))
-    return {"batch": t.batch, "insert": t.insert, "key_warps": t.key_warps, "block": t.block}
+    return {"batch": t.batch, "insert": t.insert, "key_warps": t.key_warps, "block": t.block,
+            "merge": t.merge}
 
 
 def pps_stats(handle, stream=None) -> dict:
@@ -531,8 +534,9 @@ class Table:
     def stats(self, stream=None) -> dict:
         return pps_stats(self.handle, stream)
 
-    def tune(self, batch: int = 0, insert: int = 0, key_warps: int = 0, block: int = 0):
-        pps_set_tuning(self.handle, batch, insert, key_warps, block)
+    def tune(self, batch: int = 0, insert: int = 0, key_warps: int = 0, block: int = 0,
+             merge: int = 0):
+        pps_set_tuning(self.handle, batch, insert, key_warps, block, merge)
 
     def dump(self, stream=None):
         return pps_table_dump(self.handle, self.T, self.fixed, stream)

@@ -174,6 +174,28 @@ def test_fused_filter_matches_oracle(fixed, batch):
     tab.close()
 
 
+@pytest.mark.parametrize("fixed", [False, True])
+@pytest.mark.parametrize("merge", [1, 2, 3])
+def test_pipelined_insert_merge_modes_match_oracle(merge, fixed):
+    """The pipelined insert with each warp aggregation of equal keys (none,
+    gated by neighbouring lanes, always): counts and statuses exact, values
+    within the FP32 summation bound (fixed point: bit-exact)."""
+    spec, cfg = _small(width=160, height=120, bounces=3, accum_fixed=fixed)
+    v = _gen(spec, 4)
+    n = v["px"].numel() - 5
+    tab = pps.Table(cfg)
+    tab.tune(insert=2, merge=merge)
+    t = pps.pps_get_tuning(tab.handle)
+    assert t["merge"] == merge and t["insert"] == 2
+    out = tab.filter(_dev(v, n), spec.view.eye, 4)
+    fr = _oracle(cfg, spec.view.eye, 4, _np(v, n), view=spec.view)
+    _check_frame(out, fr, fixed)
+    st = tab.stats()
+    assert st["frame_cells"] == fr.tuples.shape[0]
+    assert st["overflow_vertices"] == 0 and st["device_error"] == 0
+    tab.close()
+
+
 def test_results_do_not_depend_on_placement():
     """Fixed point, so bit for bit: the table size, the probe limit, the hash
     seeds and the order of the vertices (ids kept) change where cells live in
@@ -465,6 +487,10 @@ def test_call_order_and_argument_errors():
     with pytest.raises(pps.PPSError) as e:
         tab.blend(0.2)  # no history in this table
     assert e.value.code == pps.PPS_EINVAL
+    with pytest.raises(pps.PPSError) as e:
+        tab.tune(merge=4)
+    assert e.value.code == pps.PPS_EINVAL
+    assert pps.pps_get_tuning(tab.handle)["merge"] == 2  # the library default
     tab.close()
 
 
