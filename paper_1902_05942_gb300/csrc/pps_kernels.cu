@@ -1341,10 +1341,33 @@ __device__ __forceinline__ void ws_probe_group(const TableDev& t, const VertexPt
   unsigned long long w[PB];
 #pragma unroll
   for (int i = 0; i < PB; ++i) w[i] = use[i] ? ld_relaxed_u64_keep(t.slots + (h1[i] & t.mask)) : 1ull;
+  // ids for the entries whose first probe found an empty slot: one
+  // shared-memory atomic per warp, the lanes' ids in (entry, lane) order
   uint32_t my[PB];
+  {
+    // the lanes of this warp in this call: those whose first entry is below q
+    const uint32_t lane = threadIdx.x & 31u, lt = (1u << lane) - 1u;
+    const uint32_t e_lane0 = e0 - lane;
+    const uint32_t nin = q > e_lane0 ? min(32u, q - e_lane0) : 0u;
+    const unsigned am = nin >= 32u ? 0xFFFFFFFFu : (1u << nin) - 1u;
+    unsigned bm[PB];
+    uint32_t tot = 0;
 #pragma unroll
-  for (int i = 0; i < PB; ++i)
-    my[i] = use[i] && w[i] == 0ull ? id_base + atomicAdd(claims, 1u) : kOverflowSlot;
+    for (int i = 0; i < PB; ++i) {
+      bm[i] = __ballot_sync(am, use[i] && w[i] == 0ull);
+      tot += __popc(bm[i]);
+    }
+    const uint32_t first = __ffs(am) - 1u;
+    uint32_t base = 0;
+    if (lane == first && tot) base = atomicAdd(claims, tot);
+    base = __shfl_sync(am, base, first);
+    uint32_t off = 0;
+#pragma unroll
+    for (int i = 0; i < PB; ++i) {
+      my[i] = (bm[i] >> lane) & 1u ? id_base + base + off + __popc(bm[i] & lt) : kOverflowSlot;
+      off += __popc(bm[i]);
+    }
+  }
   unsigned long long old[PB];
 #pragma unroll
   for (int i = 0; i < PB; ++i)

@@ -101,24 +101,44 @@ __device__ __forceinline__ VertexIn load_vertex(const Dev& d, const VertexPtrs& 
 // PPS_STATUS_MLP unless `all`).  Two kernels: k_mlp_compact lists the
 // vertices to evaluate; k_mlp_infer_tc evaluates them 128 at a time on the
 // fifth-generation tensor cores.
-// One pass: each thread looks at 4 consecutive vertices, a CTA-wide scan
-// places its CTA's candidates, and one atomic per CTA (1,024 vertices)
-// reserves their places in the list.
+// One pass: each thread looks at 4 consecutive vertices (one 16-byte load of
+// their counts and one 4-byte load of their statuses when `vec`: both arrays
+// aligned for it), a CTA-wide scan places its CTA's candidates, and one atomic
+// per CTA (1,024 vertices) reserves their places in the list.
 constexpr int kCompactPer = 4;
 __global__ void __launch_bounds__(256) k_mlp_compact(size_t n, const uint8_t* status,
                                                      const uint32_t* count, uint32_t max_count,
-                                                     int all, int32_t* list, uint32_t* counter) {
+                                                     int all, int vec, int32_t* list,
+                                                     uint32_t* counter) {
   __shared__ uint32_t s_warp[8];
   __shared__ uint32_t s_base;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const size_t j0 = (static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x) * kCompactPer;
   bool f[kCompactPer];
   uint32_t mine = 0;
+  if (vec && j0 + kCompactPer <= n) {
+    uint32_t c[4] = {0u, 0u, 0u, 0u}, sw = 0u;
+    if (!all) {
+      const uint4 c4 = __ldcs(reinterpret_cast<const uint4*>(count + j0));
+      sw = __ldcs(reinterpret_cast<const unsigned int*>(status + j0));
+      c[0] = c4.x;
+      c[1] = c4.y;
+      c[2] = c4.z;
+      c[3] = c4.w;
+    }
 #pragma unroll
-  for (int q = 0; q < kCompactPer; ++q) {
-    const size_t j = j0 + q;
-    f[q] = j < n && (all || (status[j] != PPS_STATUS_OVERFLOW && count[j] < max_count));
-    mine += f[q] ? 1u : 0u;
+    for (int q = 0; q < kCompactPer; ++q) {
+      const uint32_t stq = (sw >> (8 * q)) & 0xFFu;
+      f[q] = all || (stq != PPS_STATUS_OVERFLOW && c[q] < max_count);
+      mine += f[q] ? 1u : 0u;
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < kCompactPer; ++q) {
+      const size_t j = j0 + q;
+      f[q] = j < n && (all || (status[j] != PPS_STATUS_OVERFLOW && count[j] < max_count));
+      mine += f[q] ? 1u : 0u;
+    }
   }
   // inclusive scan of `mine` over the warp, then over the warps
   uint32_t incl = mine;
@@ -1259,20 +1279,26 @@ static int launch_infer(pps_mlp* m, const pps_vertices* v, size_t n, const pps::
   if (n == 0) return PPS_OK;
   if (n >= (1ull << 31)) return mfail(PPS_EINVAL, "n too large");
   if (m->list_cap < n) {
+    // grown to the next power of two, so that frames whose vertex counts vary
+    // a little do not reallocate (cudaFree waits for the device)
+    size_t cap = 1;
+    while (cap < n) cap *= 2;
     cudaFree(m->list);
     m->list = nullptr;
     m->list_cap = 0;
-    if (cudaMalloc(&m->list, n * sizeof(int32_t)) != cudaSuccess) {
+    if (cudaMalloc(&m->list, cap * sizeof(int32_t)) != cudaSuccess) {
       cudaGetLastError();
       return mfail(PPS_ENOMEM, "inference list allocation failed");
     }
-    m->list_cap = n;
+    m->list_cap = cap;
   }
   const int sms = m->sms;
   MLP_CUDA(cudaMemsetAsync(m->counter, 0, sizeof(uint32_t), st));
   const int cgrid = static_cast<int>((n + 256 * pps::mlp::kCompactPer - 1) / (256 * pps::mlp::kCompactPer));
+  const int vec = reinterpret_cast<uintptr_t>(o.count) % 16 == 0 &&
+                  reinterpret_cast<uintptr_t>(o.status) % 4 == 0;
   pps::mlp::k_mlp_compact<<<cgrid, 256, 0, st>>>(n, o.status, o.count, m->p.infer_max_count, all,
-                                                 m->list, m->counter);
+                                                 vec, m->list, m->counter);
   MLP_CUDA(cudaGetLastError());
   const int grid = static_cast<int>(std::min<size_t>(static_cast<size_t>(sms) * 4, (n + 127) / 128));
   pps::mlp::k_mlp_infer_tc<<<grid, 128, pps::mlp::tc::kSmemBytes, st>>>(m->dev, vptrs(v), m->list,
