@@ -113,6 +113,48 @@ def test_mlp_training_step_matches_oracle(kind):
     net.close()
 
 
+def test_mlp_training_step_with_several_tiles_per_cta():
+    """A batch of 20,480 samples (160 tiles of 128) on a GPU with fewer
+    multiprocessors: some CTAs of the training launch take two tiles.  All
+    13,699 master weights after the first Adam step within their bounds."""
+    w = WEIGHTS["random"](31)
+    params = pps.mlp_params(batch=20480, steps=1, seed=7)
+    net = pps.MLP(params, init=w)
+    d, p, nn, rgb = _verts(60000, 8)
+    count = np.random.default_rng(9).integers(1, 16, 60000).astype(np.int32)
+    filt = {"r": d["r"], "g": d["g"], "b": d["b"], "count": torch.from_numpy(count).cuda()}
+    net.train(d, filt, frame=2)
+    got = net.get_weights().astype(np.float64)
+    idx = M.select_samples(count, 7, 2, 0, 20480, 8)
+    valid = (idx >= 0).astype(np.float64)
+    sel = np.where(idx >= 0, idx, 0)
+    w64 = w.astype(np.float64)
+    fb = M.forward_bounds(w64, _x(p[sel], nn[sel]), M.encoding_error())
+    g, eg = M.backward_bounds(w64, fb, rgb[sel].astype(np.float64), valid, 20480)
+    ref, ew = M.adam_first_step_bounds(w64, g, eg)
+    _within(got, ref, ew, "Adam step, several tiles per CTA")
+    net.close()
+
+
+def test_mlp_training_steps_across_launches():
+    """Ten Adam steps per call run as two cooperative launches (at most eight
+    steps each); three calls in a row.  The grid barriers' arrival counts
+    carry over between launches: a wrong count would leave a barrier waiting
+    until its time limit and raise the device error word, which get_weights
+    reports.  The weights stay finite and move."""
+    w = WEIGHTS["random"](33)
+    net = pps.MLP(pps.mlp_params(batch=2048, steps=10, seed=3), init=w)
+    d, _, _, _ = _verts(8000, 10)
+    count = np.random.default_rng(11).integers(1, 16, 8000).astype(np.int32)
+    filt = {"r": d["r"], "g": d["g"], "b": d["b"], "count": torch.from_numpy(count).cuda()}
+    for f in range(3):
+        net.train(d, filt, frame=f)
+    got = net.get_weights()  # raises on a device error
+    assert np.all(np.isfinite(got))
+    assert np.abs(got - w).max() > 1e-3
+    net.close()
+
+
 def test_mlp_infer_replaces_only_low_count_vertices():
     w = M.he_init(24).astype(np.float32)
     net = pps.MLP(pps.mlp_params(batch=256, infer_max_count=4), init=w)
