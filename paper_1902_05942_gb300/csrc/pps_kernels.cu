@@ -947,10 +947,17 @@ __device__ __forceinline__ uint32_t fused_offset(int sub) {
   return static_cast<uint32_t>(sub / W) * (BLOCK * W) + threadIdx.x * W;
 }
 
-// Next tile of the frame's tile counter (ntiles once all are taken).
-__device__ __forceinline__ uint32_t claim_tile(Ctrl* ctrl, uint32_t ntiles) {
+// Next tile of the frame's tile counter (ntiles once all are taken), in
+// stream order or, with `backwards`, from the end of the vertex stream.  The
+// pipelined insert takes them backwards: streams are bounce-major, so the
+// secondary-bounce tiles, whose vertices nearly all create cells of their own
+// and cost the most, go first and the cheap primary-hit tiles balance the CTAs
+// at the end of the insert (HD plain frame 6 %, temporal 3 % shorter).  The
+// per-thread insert measured slower backwards (stress frame +3 %).
+__device__ __forceinline__ uint32_t claim_tile(Ctrl* ctrl, uint32_t ntiles, bool backwards = false) {
   const unsigned long long k = atomicAdd(&ctrl->tile_next, 1ull);
-  return k < ntiles ? static_cast<uint32_t>(k) : ntiles;
+  if (k >= ntiles) return ntiles;
+  return backwards ? ntiles - 1u - static_cast<uint32_t>(k) : static_cast<uint32_t>(k);
 }
 
 struct FusedArgs {
@@ -1463,7 +1470,7 @@ __global__ void __launch_bounds__((KEYW + PRW) * 32, 2) k_fused_ws(FusedArgs a) 
       if (ch >= 2) go = mbar_wait_bounded(empty + bsel, ((ch >> 1) + 1u) & 1u);
       if (threadIdx.x == 0 && go) {
         if (ch % kWsChunksPerTile == 0) {
-          tile = s_taken < a.cap_tiles ? claim_tile(t.ctrl, ntiles) : ntiles;
+          tile = s_taken < a.cap_tiles ? claim_tile(t.ctrl, ntiles, true) : ntiles;
           if (tile < ntiles) {
             k = s_taken;
             s_tile[k] = tile;
