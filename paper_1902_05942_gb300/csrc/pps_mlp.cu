@@ -1099,11 +1099,13 @@ int launch_train(pps_mlp* m, const pps_vertices* v, const float* tr, const float
   const int grid = static_cast<int>(std::min<uint32_t>(batch / pps::mlp::kSamples,
                                                        static_cast<uint32_t>(m->sms)));
   if (adam) {
-    m->bar_arrivals += 2u * steps * static_cast<uint32_t>(grid);
     void* args[] = {&a};
     MLP_CUDA(cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(pps::mlp::k_mlp_train_tc),
                                          dim3(grid), dim3(pps::mlp::kTrainThreads), args,
                                          pps::mlp::tct::kSmemBytes, st));
+    // counted only for a launch that was made: two barriers per step, one
+    // arrival per CTA each
+    m->bar_arrivals += 2u * steps * static_cast<uint32_t>(grid);
   } else {
     pps::mlp::k_mlp_train_tc<<<grid, pps::mlp::kTrainThreads, pps::mlp::tct::kSmemBytes, st>>>(a);
     MLP_CUDA(cudaGetLastError());
