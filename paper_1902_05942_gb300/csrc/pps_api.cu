@@ -281,6 +281,7 @@ void set_camera(pps_table* t, const pps_camera* cam, uint32_t frame) {
   t->kc.cam[1] = cam->pos[1];
   t->kc.cam[2] = cam->pos[2];
   t->kc.frame = frame;
+  pps::set_round_keys(t->kc);
 }
 
 void free_all(pps_table* t) {
@@ -408,6 +409,7 @@ int pps_create(pps_table** out, const pps_params* p) {
   t->dev.hist_mode = static_cast<int>(p->hist_mode);
   t->kc.k = p->voxel_scale * p->pixel_angle;  // fl32(s * theta_px)
   t->kc.seed = p->seed;
+  pps::set_round_keys(t->kc);
   t->kc.hseed_home = p->hash_seed_home;
   t->kc.hseed_fp = p->hash_seed_fp;
   t->kc.mask = t->T - 1;

@@ -160,6 +160,7 @@ int pps_batch_run(pps_batch* b, const pps_camera* cams, uint32_t frame, void* st
     vd.kc.cam[1] = cams[i].pos[1];
     vd.kc.cam[2] = cams[i].pos[2];
     vd.kc.frame = frame;
+    pps::set_round_keys(vd.kc);
     b->hviews[k][i] = vd;
   }
   const cudaStream_t st = static_cast<cudaStream_t>(stream);

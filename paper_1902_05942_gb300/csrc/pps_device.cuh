@@ -33,7 +33,22 @@ struct KeyConst {
   uint32_t max_probes;
   int32_t lod_min, lod_max;
   uint32_t jitter, nih;  // jitter on/off, normal in home hash
+  // Philox4x32-10 key of rounds 1..9 for the jitter draw (seed and frame
+  // bumped by the Weyl constants; set_round_keys): the same for every vertex
+  // of a frame, so the kernels read them from their parameters
+  uint32_t rk0[9], rk1[9];
 };
+
+// Fill kc.rk0 / kc.rk1 from kc.seed and kc.frame; call whenever either changes.
+__host__ __device__ inline void set_round_keys(KeyConst& kc) {
+  uint32_t k0 = kc.seed, k1 = kc.frame;
+  for (int r = 0; r < 9; ++r) {
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+    kc.rk0[r] = k0;
+    kc.rk1[r] = k1;
+  }
+}
 
 // Per-frame and lifetime counters plus the device error word and the state of
 // the grid barrier used by the persistent filter kernel.
@@ -129,15 +144,13 @@ struct OutPtrs {
 // ---------------------------------------------------------------- Philox4x32-10
 // Salmon et al., SC'11: ten rounds of two 32x32->64 multiplies; the key is
 // bumped by the Weyl constants between rounds.
-__device__ __forceinline__ uint2 philox_first2(uint32_t c0, uint32_t c1, uint32_t k0,
-                                               uint32_t k1) {
+// The first two output words of one draw, the round keys taken from the key
+// constants (round 0: seed and frame; rounds 1..9: kc.rk0 / kc.rk1).
+__device__ __forceinline__ uint2 philox_first2_rk(uint32_t c0, uint32_t c1, const KeyConst& kc) {
   uint32_t x0 = c0, x1 = c1, x2 = 0u, x3 = 0u;
 #pragma unroll
   for (int r = 0; r < 10; ++r) {
-    if (r) {
-      k0 += 0x9E3779B9u;
-      k1 += 0xBB67AE85u;
-    }
+    const uint32_t k0 = r ? kc.rk0[r - 1] : kc.seed, k1 = r ? kc.rk1[r - 1] : kc.frame;
     const uint32_t lo0 = 0xD2511F53u * x0, hi0 = __umulhi(0xD2511F53u, x0);
     const uint32_t lo1 = 0xCD9E8D57u * x2, hi1 = __umulhi(0xCD9E8D57u, x2);
     const uint32_t n0 = hi1 ^ x1 ^ k0, n2 = hi0 ^ x3 ^ k1;
@@ -244,7 +257,7 @@ __device__ __forceinline__ KeyWords key_words(const KeyConst& kc, float px, floa
   int l1 = l0;
   if (kc.jitter) {
     // jitter(n): a point of the tangent plane, (u, w) uniform in [-0.5, 0.5)
-    const uint2 rnd = philox_first2(id, stream_id, kc.seed, kc.frame);
+    const uint2 rnd = philox_first2_rk(id, stream_id, kc);
     const float u = __fsub_rn(__fmul_rn(__uint2float_rn(rnd.x >> 8), 0x1p-24f), 0.5f);
     const float w = __fsub_rn(__fmul_rn(__uint2float_rn(rnd.y >> 8), 0x1p-24f), 0.5f);
     // tangent frame after Duff et al. (JCGT 2017)

@@ -181,6 +181,7 @@ extern "C" int pps_filter_noalloc(const pps_params* p, const pps_camera* cam, ui
   kc.k = p->voxel_scale * p->pixel_angle;
   kc.seed = p->seed;
   kc.frame = frame;
+  pps::set_round_keys(kc);
   kc.hseed_home = p->hash_seed_home;
   kc.hseed_fp = p->hash_seed_fp;
   kc.mask = T - 1;
