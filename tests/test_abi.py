@@ -49,9 +49,11 @@ def test_struct_layouts_match_the_header(tmp_path):
     prog = tmp_path / "sizes.c"
     prog.write_text(
         '#include <stdio.h>\n#include <stddef.h>\n#include "pps.h"\n'
-        "int main(void){printf(\"%zu %zu %zu %zu %zu %zu %zu\\n\", sizeof(pps_params),"
-        " sizeof(pps_camera), sizeof(pps_vertices), sizeof(pps_output), sizeof(pps_stats_t),"
-        " offsetof(pps_params, log2_hist_slots), offsetof(pps_vertices, id_base));return 0;}\n")
+        "int main(void){printf(\"%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n\","
+        " sizeof(pps_params), sizeof(pps_camera), sizeof(pps_vertices), sizeof(pps_output),"
+        " sizeof(pps_stats_t), offsetof(pps_params, log2_hist_slots),"
+        " offsetof(pps_vertices, id_base), sizeof(pps_tuning), offsetof(pps_tuning, merge),"
+        " sizeof(pps_mlp_params), offsetof(pps_mlp_params, seed));return 0;}\n")
     exe = tmp_path / "sizes"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)],
                    check=True)
@@ -60,7 +62,9 @@ def test_struct_layouts_match_the_header(tmp_path):
     want = [ctypes.sizeof(pps.pps_params), ctypes.sizeof(pps.pps_camera),
             ctypes.sizeof(pps.pps_vertices), ctypes.sizeof(pps.pps_output),
             ctypes.sizeof(pps.pps_stats_t), pps.pps_params.log2_hist_slots.offset,
-            pps.pps_vertices.id_base.offset]
+            pps.pps_vertices.id_base.offset, ctypes.sizeof(pps.pps_tuning),
+            pps.pps_tuning.merge.offset, ctypes.sizeof(pps.pps_mlp_params),
+            pps.pps_mlp_params.seed.offset]
     assert got == want
 
 
