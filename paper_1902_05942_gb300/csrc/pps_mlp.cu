@@ -10,14 +10,15 @@
 // tcgen05.ld back to registers for the bias / ReLU / rounding epilogues.
 // Inference: a CTA of 128 threads evaluates 128 vertices per tile.
 // Training: one cooperative launch per call takes all its Adam steps.  A CTA
-// of 256 threads draws 128 samples and takes them through the forward pass,
-// the delta chain and the weight and bias gradients dZ^T X and dZ^T 1
-// (products over the samples, reading the row-per-sample tiles as MN-major
-// operands); two warps share each 32-lane quarter of tensor memory and split
-// every epilogue by columns.  The gradients are added to an FP32 accumulator
-// with vector reductions; after a grid barrier every thread applies Adam to its
-// share of the FP32 master weights and refreshes their BF16 copies, and a
-// second barrier starts the next step.
+// of 384 threads takes 128 samples at a time through the forward pass, the
+// delta chain and the weight and bias gradients dZ^T X and dZ^T 1 (products
+// over the samples, reading the row-per-sample tiles as MN-major operands):
+// eight warps run the products, two of them sharing each 32-lane quarter of
+// tensor memory and splitting every epilogue by columns, while four warps
+// draw, gather and encode the next samples.  The gradients are added to an
+// FP32 accumulator with vector reductions; after a grid barrier every thread
+// applies Adam to its share of the FP32 master weights and refreshes their
+// BF16 copies, and a second barrier starts the next step.
 //
 // Parameter vector (FP32, this order): W1 [64][80], b1 [64], W2 [64][64], b2,
 // W3 [64][64], b3, W4 [3][64], b4 [3]  (W as [out][in]).
@@ -593,9 +594,9 @@ __device__ __forceinline__ void sync_tc() {
 //  warps 8..11  draw, gather and encode the NEXT work item's samples (thread
 //               t: sample t) into the other of two input buffers, so that the
 //               samples' memory latency and the encoding overlap the chain.
-// With Adam, the CTAs meet at the end of each step; the last to arrive applies
-// Adam to all parameters and releases the others, which then stage the new
-// weights.
+// With Adam, the CTAs meet at a grid barrier at the end of each step, every
+// thread of the grid updates one parameter (Adam), and a second barrier
+// publishes the new weights, which the next step stages.
 constexpr int kMaxSteps = 8;        // Adam steps per launch
 constexpr int kTrainThreads = 384;  // 8 chain warps + 4 sampling warps
 
